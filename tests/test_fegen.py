@@ -1,0 +1,117 @@
+"""Pins for the synthetic input generator (the assembled FE systems both sides consume).
+
+The generator stands in for the paper's FE library (Sec. 2).  These checks tie its output to
+mathematics that fixes it independently of the code: the nonzero count of the tensor-product
+pattern, exact symmetry, zero row sums of the pure Laplacian, the mass matrix integrating to
+the cube's volume, and O(h^{p+1}) convergence to the manufactured solution of Sec. 3.1.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+
+import fegen
+
+
+def _nnz_formula(n, p):
+    nnz1 = n * (p + 1) ** 2 - (n - 1)
+    # drop the rows and columns of the two end nodes; they share an element when n = 1
+    inner = nnz1 - 4 * (p + 1) + 2 if n > 1 else (p - 1) ** 2
+    N1 = n * p + 1
+    return inner ** 3 + (N1 ** 3 - (N1 - 2) ** 3)
+
+
+@pytest.mark.parametrize("n,p", [(1, 2), (2, 3), (3, 4), (4, 4), (2, 6)])
+def test_pattern_size_matches_tensor_formula(n, p):
+    P = fegen.make(n, p, with_values=False, rhs="none")
+    assert P.n == (n * p + 1) ** 3
+    assert P.nnz == _nnz_formula(n, p)
+    # boundary rows keep only their diagonal
+    bnd = np.flatnonzero(P.boundary)
+    assert np.all(np.diff(P.row_ptr)[bnd] == 1)
+    assert np.all(P.col[P.row_ptr[bnd]] == bnd)
+
+
+def test_c1_nonzero_count():
+    P = fegen.make(4, 4, with_values=False, rhs="none")
+    assert (P.n, P.nnz) == (4913, 494577)
+
+
+@pytest.mark.parametrize("mesh", ["uniform", "jitter", "graded"])
+def test_exact_symmetry_and_sorted_columns(mesh):
+    P = fegen.make(3, 3, mesh=mesh, lam=2.0, kappa=1)
+    A = P.scipy()
+    assert (A - A.T).count_nonzero() == 0
+    for i in range(P.n):
+        c = P.col[P.row_ptr[i]:P.row_ptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+@pytest.mark.parametrize("mesh", ["uniform", "jitter"])
+def test_laplacian_rows_sum_to_zero(mesh):
+    P = fegen.make(3, 4, mesh=mesh, lam=0.0, dirichlet=False, rhs="none")
+    A = P.scipy()
+    rs = np.asarray(A.sum(axis=1)).ravel()
+    assert np.max(np.abs(rs)) <= 1e-12 * np.max(np.abs(P.val))
+
+
+@pytest.mark.parametrize("mesh", ["uniform", "jitter", "graded"])
+def test_mass_matrix_integrates_volume(mesh):
+    P = fegen.make(3, 3, mesh=mesh, lam=1.0, kappa=2, dirichlet=False, rhs="none")
+    assert abs(P.val.sum() - 1.0) < 1e-12
+
+
+def test_dense_solve_matches_sparse_direct():
+    P = fegen.make(2, 3, mesh="jitter", lam=1.0)
+    x = sla.spsolve(P.scipy().tocsc(), P.b)
+    xd = np.linalg.solve(P.scipy().toarray(), P.b)
+    assert np.linalg.norm(x - xd) <= 1e-12 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_convergence_rate_to_manufactured_solution(p):
+    errs, hs = [], []
+    for n in ([4, 8] if p <= 2 else [2, 4]):
+        P = fegen.make(n, p, mesh="uniform", lam=1.0)
+        x = sla.spsolve(P.scipy().tocsc(), P.b)
+        errs.append(P.l2_error(x))
+        hs.append(1.0 / n)
+    rate = np.log(errs[0] / errs[1]) / np.log(hs[0] / hs[1])
+    assert abs(rate - (p + 1)) < 0.3, (p, rate, errs)
+
+
+def test_variable_coefficient_manufactured_solution():
+    errs = []
+    for n in [2, 4]:
+        P = fegen.make(n, 3, mesh="uniform", lam=1000.0, kappa=1)
+        x = sla.spsolve(P.scipy().tocsc(), P.b)
+        errs.append(P.l2_error(x))
+    assert abs(np.log2(errs[0] / errs[1]) - 4) < 0.4
+
+
+def test_renumbering_and_element_symmetries_give_the_same_operator():
+    base = fegen.make(2, 3, mesh="jitter", lam=1.0)
+    perm = fegen.make(2, 3, mesh="jitter", lam=1.0, perm_seed=7, sym_seed=9)
+    # map base ids to permuted ids through the coordinates
+    key = lambda c: np.lexsort(np.round(c, 12).T[::-1])
+    ib, ip = key(base.coords), key(perm.coords)
+    pmap = np.empty(base.n, np.int64)
+    pmap[ib] = ip
+    Ab = base.scipy().toarray()
+    Ap = perm.scipy().toarray()
+    assert np.array_equal(Ap[np.ix_(pmap, pmap)], Ab)
+    assert np.array_equal(perm.b[pmap], base.b)
+    # element maps agree as sets per element, and differ in order for some elements
+    same_order = 0
+    for e in range(base.n_elem):
+        assert sorted(pmap[base.elem_dof[e]]) == sorted(perm.elem_dof[e])
+        same_order += np.array_equal(pmap[base.elem_dof[e]], perm.elem_dof[e])
+    assert same_order < base.n_elem
+
+
+def test_graded_mesh_aspect_ratio():
+    P = fegen.make(12, 1, mesh="graded", rhs="none", with_values=False)
+    z = np.unique(np.round(P.coords[:, 2], 12))
+    h = np.diff(z)
+    assert abs(h[0] - 1.0 / 120.0) < 1e-12
+    assert abs(h.sum() - 1.0) < 1e-12
+    assert abs(h[1] / h[0] - 1.37618) < 1e-4

@@ -1,0 +1,490 @@
+"""Pins for the CPU oracle: each part is tied to something other than itself.
+
+  GLL nodes        Fig. 1's printed positions, closed forms, numpy's Legendre roots
+  P (Alg. 2-4, 7)  partition of unity, exact reproduction of degree-q fields, coincident nodes
+  RAP (Sec. 2)     equals the order-q operator assembled directly with the fine rule;
+                   Table 1's 4 levels and 27/343 coarsest level
+  SpGEMM           scipy's product (values) and the boolean product (pattern)
+  MIS-2 (Sec. 2.5) brute-force greedy MIS of the squared graph; validity; hand-worked path
+  aggregates       cover, one root each, connected; hand-worked path
+  SPAI-0           minimiser of ||e_i - m a_i|| row by row
+  Lanczos          dense eigenvalues (numpy) within 1%
+  Chebyshev        closed-form damping T_k((theta - mu)/delta) / T_k(theta/delta)
+  Cholesky         numpy's factor and solve
+  V-cycle (Alg. 1) symmetric as an operator
+  PCG              dense direct solve; Dirichlet entries converge to zero; fewer iterations
+                   than Jacobi-preconditioned CG; thread-count independence
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
+
+import fegen
+import oracle
+from conftest import read_golden
+
+
+# ----------------------------------------------------------------------------- 1D rules
+def test_gll_nodes_match_fig1():
+    g = read_golden("fig1_gll_nodes_p4.txt")
+    for p_s, pos in g.items():
+        p = int(p_s)
+        x = (oracle.gll_nodes(p) + 1.0) / 2.0
+        assert np.allclose(x, [float(v) for v in pos], atol=5e-5)
+
+
+@pytest.mark.parametrize("p", range(1, 13))
+def test_gll_nodes_closed_forms_and_legendre_roots(p):
+    x = oracle.gll_nodes(p)
+    assert x[0] == -1.0 and x[-1] == 1.0
+    assert np.all(np.diff(x) > 0)
+    assert np.array_equal(x, -x[::-1])
+    if p >= 2:
+        roots = np.sort(np.polynomial.legendre.Legendre.basis(p).deriv().roots().real)
+        assert np.allclose(x[1:-1], roots, atol=1e-14)
+    if p == 3:
+        assert np.allclose(x[1:3], [-1 / np.sqrt(5), 1 / np.sqrt(5)], atol=1e-15)
+    if p == 4:
+        assert np.allclose(x[1:4], [-np.sqrt(3 / 7), 0.0, np.sqrt(3 / 7)], atol=1e-15)
+    if p % 2 == 0:
+        assert x[p // 2] == 0.0
+
+
+def test_p_schedule():
+    assert [oracle.next_order(p) for p in range(1, 11)] == [1, 1, 1, 2, 1, 3, 1, 4, 3, 5]
+
+
+@pytest.mark.parametrize("p,q", [(2, 1), (4, 2), (6, 3), (8, 4), (3, 1), (9, 3), (12, 6)])
+def test_p1d_interpolates_degree_q_polynomials(p, q):
+    T = oracle.p1d(p, q)
+    xp, xq = oracle.gll_nodes(p), oracle.gll_nodes(q)
+    assert np.allclose(T.sum(axis=1), 1.0, atol=1e-14)
+    for deg in range(q + 1):
+        assert np.allclose(T @ xq ** deg, xp ** deg, atol=1e-13)
+    # endpoints interpolate exactly; every other entry of the end rows is an exact zero
+    assert T[0, 0] == 1.0 and T[p, q] == 1.0
+    assert np.all(T[0, 1:] == 0.0) and np.all(T[p, :q] == 0.0)
+    if p % 2 == 0 and q % 2 == 0:
+        row = T[p // 2]
+        assert row[q // 2] == 1.0 and np.count_nonzero(row) == 1
+
+
+# ----------------------------------------------------------------------------- hierarchy
+def _coarse_coords(prob, H, level):
+    """Positions of the order-q nodes of `level` on an affine (uniform) mesh."""
+    p = prob.p
+    info = H.level_info(level)
+    q = info["order"]
+    nlc = (q + 1) ** 3
+    import ctypes
+    l2g = np.empty((prob.n_elem, nlc), np.int32)
+    oracle._lib().orc_level_extra(H._h, level, None, oracle._p(l2g))
+    xq = oracle.gll_nodes(q)
+    X = np.zeros((info["n"], 3))
+    n1 = p + 1
+    for e in range(prob.n_elem):
+        lo = prob.coords[prob.elem_dof[e, 0]]
+        hi = prob.coords[prob.elem_dof[e, n1 ** 3 - 1]]
+        for b in range(nlc):
+            i, j, k = b // (q + 1) ** 2, (b // (q + 1)) % (q + 1), b % (q + 1)
+            t = (np.array([xq[i], xq[j], xq[k]]) + 1.0) / 2.0
+            X[l2g[e, b]] = lo + t * (hi - lo)
+    return X
+
+
+@pytest.mark.parametrize("n,p", [(2, 4), (3, 6), (2, 8)])
+def test_prolongation_reproduces_degree_q_fields(n, p):
+    prob = fegen.make(n, p, mesh="uniform", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    q = H.level_info(1)["order"]
+    Xc = _coarse_coords(prob, H, 1)
+    rp, ci, v, m = H.prolongation(0)
+    P = sp.csr_matrix((v, ci, rp), shape=(prob.n, m))
+    assert np.allclose(P @ np.ones(m), 1.0, atol=1e-13)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        a, b, c = rng.integers(0, q + 1, 3)
+        f = lambda X: X[:, 0] ** a * X[:, 1] ** b * X[:, 2] ** c + 0.5 * X[:, 0] ** q
+        assert np.max(np.abs(P @ f(Xc) - f(prob.coords))) < 1e-12
+
+
+def test_prolongation_coincident_nodes_are_unit_rows():
+    prob = fegen.make(2, 4, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    rp, ci, v, m = H.prolongation(0)
+    # fine nodes at coarse node positions of the 4 -> 2 step: every second node per direction
+    N1 = 2 * 4 + 1
+    I = np.arange(prob.n)
+    coinc = ((I // (N1 * N1)) % 2 == 0) & (((I // N1) % N1) % 2 == 0) & ((I % N1) % 2 == 0)
+    for i in np.flatnonzero(coinc):
+        assert rp[i + 1] - rp[i] == 1 and v[rp[i]] == 1.0
+
+
+@pytest.mark.parametrize("mesh,p,kappa,lam", [("jitter", 4, 0, 1.0), ("jitter", 6, 1, 10.0),
+                                              ("graded", 2, 0, 1000.0), ("uniform", 8, 0, 1.0)])
+def test_rap_equals_direct_assembly_with_the_fine_rule(mesh, p, kappa, lam):
+    n = 2
+    fine = fegen.make(n, p, mesh=mesh, lam=lam, kappa=kappa, dirichlet=False, rhs="none")
+    H = oracle.Hierarchy.from_problem(fine, coarse_max=1)
+    q = H.level_info(1)["order"]
+    direct = fegen.make(n, q, mesh=mesh, lam=lam, kappa=kappa, nq=p + 2, dirichlet=False, rhs="none")
+    rp, ci, v, _ = H.level(1)
+    Ac = sp.csr_matrix((v, ci, rp), shape=(direct.n, direct.n)).toarray()
+    Ad = direct.scipy().toarray()
+    assert np.max(np.abs(Ac - Ad)) <= 1e-12 * np.max(np.abs(Ad))
+
+
+def test_rap_interior_block_with_dirichlet():
+    fine = fegen.make(3, 4, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(fine, coarse_max=1)
+    direct = fegen.make(3, 2, mesh="jitter", lam=1.0, nq=6)
+    rp, ci, v, _ = H.level(1)
+    Ac = sp.csr_matrix((v, ci, rp), shape=(direct.n, direct.n)).toarray()
+    Ad = direct.scipy().toarray()
+    inner = np.flatnonzero(direct.boundary == 0)
+    blk = np.ix_(inner, inner)
+    assert np.max(np.abs(Ac[blk] - Ad[blk])) <= 1e-12 * np.max(np.abs(Ad))
+
+
+def test_table1_hierarchy():
+    g = read_golden("table1_giamg_hierarchy.txt")
+    n, p = int(g["elements_per_direction"][0]), int(g["order"][0])
+    prob = fegen.make(n, p, lam=float(g["lambda"][0]))
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=int(g["cheb_degree"][0]))
+    assert H.num_levels == int(g["levels"][0])
+    info = H.level_info(H.num_levels - 1)
+    assert info["kind"] == oracle.KIND_COARSEST
+    assert info["n"] == int(g["coarsest_rows"][0]) and info["nnz"] == int(g["coarsest_nnz"][0])
+    assert [H.level_info(l)["order"] for l in range(H.num_levels)] == [8, 4, 2, 1]
+
+
+def test_coarse_operators_symmetric_and_hierarchy_sizes_c2_shape():
+    # a small mesh of the 16^3 p=6 workload's type, with an aggregation level
+    prob = fegen.make(6, 6, mesh="jitter", lam=10.0)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=3)
+    kinds = [H.level_info(l)["kind"] for l in range(H.num_levels)]
+    assert kinds[:2] == [oracle.KIND_P, oracle.KIND_P] and kinds[-1] == oracle.KIND_COARSEST
+    assert H.level_info(1)["n"] == (6 * 3 + 1) ** 3 and H.level_info(2)["n"] == 7 ** 3
+    for l in range(1, H.num_levels):
+        rp, ci, v, _ = H.level(l)
+        A = sp.csr_matrix((v, ci, rp))
+        assert abs(A - A.T).max() <= 1e-13 * abs(A).max()
+
+
+# ----------------------------------------------------------------------------- SpGEMM
+def _rand_csr(n, m, dens, rng):
+    A = sp.random(n, m, density=dens, random_state=rng, format="csr")
+    A.sort_indices()
+    return A
+
+
+def test_spgemm_matches_scipy_and_boolean_pattern():
+    rng = np.random.default_rng(3)
+    A, B = _rand_csr(40, 30, 0.15, rng), _rand_csr(30, 25, 0.2, rng)
+    C = oracle.spgemm((A.indptr, A.indices, A.data, A.shape[1]), (B.indptr, B.indices, B.data, B.shape[1]))
+    rp, ci, v, m = C
+    Cs = sp.csr_matrix((v, ci, rp), shape=(40, 25))
+    assert np.allclose(Cs.toarray(), (A @ B).toarray(), atol=1e-15)
+    Ab, Bb = A.copy(), B.copy()
+    Ab.data[:] = 1.0
+    Bb.data[:] = 1.0
+    pat = (Ab @ Bb).tocsr()
+    pat.sort_indices()
+    assert np.array_equal(rp, pat.indptr) and np.array_equal(ci, pat.indices)
+
+
+def test_spgemm_keeps_exact_cancellations():
+    # [1 1] x [1; -1] = [0]: the entry is structurally present and stored as 0.0
+    A = (np.array([0, 2], np.int64), np.array([0, 1], np.int32), np.array([1.0, 1.0]), 2)
+    B = (np.array([0, 1, 2], np.int64), np.array([0, 0], np.int32), np.array([1.0, -1.0]), 1)
+    rp, ci, v, m = oracle.spgemm(A, B)
+    assert rp.tolist() == [0, 1] and ci.tolist() == [0] and v.tolist() == [0.0]
+
+
+# ----------------------------------------------------------------------------- MIS-2
+def _graph_from_edges(n, edges):
+    adj = [set() for _ in range(n)]
+    for a, b in edges:
+        if a != b:
+            adj[a].add(b)
+            adj[b].add(a)
+    rp = np.zeros(n + 1, np.int64)
+    ci = []
+    for i in range(n):
+        nb = sorted(adj[i])
+        ci += nb
+        rp[i + 1] = rp[i] + len(nb)
+    return rp, np.array(ci, np.int32), adj
+
+
+def _dist(adj, n):
+    D = np.full((n, n), 99)
+    for s in range(n):
+        D[s, s] = 0
+        front = [s]
+        while front:
+            nxt = []
+            for u in front:
+                for w in adj[u]:
+                    if D[s, w] > D[s, u] + 1:
+                        D[s, w] = D[s, u] + 1
+                        nxt.append(w)
+            front = nxt
+    return D
+
+
+def _greedy_mis2(n, adj, prio):
+    D = _dist(adj, n)
+    chosen = []
+    for i in sorted(range(n), key=lambda i: prio[i], reverse=True):
+        if all(D[i, j] > 2 for j in chosen):
+            chosen.append(i)
+    return set(chosen), D
+
+
+def test_mis2_hand_worked_path():
+    g = read_golden("mis2_path7.txt")
+    n = int(g["n"][0])
+    edges = [tuple(map(int, e.split("-"))) for e in g["edges"]]
+    rp, ci, _ = _graph_from_edges(n, edges)
+    ins, _ = oracle.mis2(rp, ci, hash_kind=1)
+    assert sorted(np.flatnonzero(ins).tolist()) == [int(v) for v in g["roots"]]
+    agg, na = oracle.aggregate(rp, ci, ins)
+    assert agg.tolist() == [int(v) for v in g["aggregates"]] and na == 3
+
+
+@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("hash_kind", [0, 1])
+def test_mis2_equals_greedy_on_squared_graph(seed, hash_kind):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 13))
+    dens = rng.uniform(0.05, 0.6)
+    edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < dens]
+    rp, ci, adj = _graph_from_edges(n, edges)
+    ins, _ = oracle.mis2(rp, ci, hash_kind=hash_kind)
+    prio = [(oracle.hash32(i, hash_kind), i) for i in range(n)]
+    greedy, D = _greedy_mis2(n, adj, prio)
+    S = set(np.flatnonzero(ins).tolist())
+    assert S == greedy
+    # validity: distance >= 3 inside the set, every node within distance 2 of the set
+    for a in S:
+        for b in S:
+            assert a == b or D[a, b] >= 3
+    for i in range(n):
+        assert min(D[i, s] for s in S) <= 2
+    # aggregates
+    agg, na = oracle.aggregate(rp, ci, ins)
+    roots = sorted(S)
+    assert na == len(roots)
+    for a_id, r in enumerate(roots):
+        members = np.flatnonzero(agg == a_id)
+        assert r in members
+        assert all(D[r, m] <= 2 for m in members)
+        # connected: every member reaches the root inside the aggregate
+        seen, front = {r}, [r]
+        mem = set(members.tolist())
+        while front:
+            front = [w for u in front for w in adj[u] if w in mem and w not in seen and not seen.add(w)]
+        assert seen == mem
+    for i in range(n):
+        if i not in S and any(j in S for j in adj[i]):
+            assert agg[i] == roots.index(next(j for j in adj[i] if j in S))
+
+
+# ----------------------------------------------------------------------------- SPAI-0
+def test_sa_prolongation_spai0_and_constants():
+    prob = fegen.make(3, 1, mesh="jitter", lam=0.0, dirichlet=False, rhs="none")
+    rp, ci, v = prob.row_ptr, prob.col, prob.val
+    grp = np.zeros_like(rp)
+    gci = []
+    for i in range(prob.n):
+        nb = [c for c in ci[rp[i]:rp[i + 1]] if c != i]
+        gci += nb
+        grp[i + 1] = grp[i] + len(nb)
+    ins, _ = oracle.mis2(grp, np.array(gci, np.int32))
+    agg, na = oracle.aggregate(grp, np.array(gci, np.int32), ins)
+    Prp, Pci, Pv, m = oracle.sa_prolongation(rp, ci, v, agg, na)
+    P = sp.csr_matrix((Pv, Pci, Prp), shape=(prob.n, na))
+    A = prob.scipy()
+    # zero row sums of A: the smoothed prolongation keeps constants exactly (to rounding)
+    assert np.allclose(P @ np.ones(na), 1.0, atol=1e-13)
+    # the diagonal weights minimise ||e_i - m a_i||_2 row by row (SPAI-0)
+    AT = (A @ sp.csr_matrix((np.ones(prob.n), agg, np.arange(prob.n + 1)), shape=(prob.n, na))).toarray()
+    Pd = P.toarray()
+    checked = 0
+    for i in range(0, prob.n, 7):
+        j = int(np.argmax(np.abs(AT[i])))
+        if abs(AT[i, j]) < 1e-8:
+            continue  # the whole row lies in one aggregate: A T has no usable entry
+        m_i = ((1.0 if agg[i] == j else 0.0) - Pd[i, j]) / AT[i, j]
+        checked += 1
+        a = A.getrow(i).toarray().ravel()
+        e = np.zeros(prob.n)
+        e[i] = 1.0
+        f = lambda t: np.linalg.norm(e - t * a)
+        assert f(m_i) <= f(m_i * (1 + 1e-6)) and f(m_i) <= f(m_i * (1 - 1e-6))
+    assert checked > 3
+
+
+# ----------------------------------------------------------------------------- smoother
+def _dense_level(H, l):
+    rp, ci, v, _ = H.level(l)
+    return sp.csr_matrix((v, ci, rp)).toarray()
+
+
+def test_lanczos_estimate_within_one_percent():
+    prob = fegen.make(2, 4, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    for l in range(H.num_levels - 1):
+        A = _dense_level(H, l)
+        d = 1.0 / np.sqrt(np.diag(A))
+        lam = np.linalg.eigvalsh(d[:, None] * A * d[None, :]).max()
+        assert abs(H.rho_hat(l) - lam) <= 0.01 * lam
+
+
+def test_tridiagonal_eigenvalue_by_bisection():
+    rng = np.random.default_rng(1)
+    for m in [1, 2, 5, 20]:
+        a, b = rng.normal(size=m), rng.normal(size=max(m - 1, 1))
+        T = np.diag(a) + np.diag(b[:m - 1], 1) + np.diag(b[:m - 1], -1)
+        assert abs(oracle.tridiag_max_eig(a, b) - np.linalg.eigvalsh(T).max()) < 1e-12
+
+
+def test_chebyshev_damping_closed_form():
+    prob = fegen.make(2, 2, mesh="jitter", lam=1.0)
+    for k in [1, 2, 3, 4]:
+        H = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+        A = _dense_level(H, 0)
+        D = np.diag(A)
+        w, V = np.linalg.eig(A / D[:, None])
+        rho = H.rho_hat(0)
+        lo, hi = 0.1 * rho, 1.1 * rho
+        theta, delta = (hi + lo) / 2, (hi - lo) / 2
+        for idx in np.argsort(w.real)[:: max(1, len(w) // 6)]:
+            mu, v = w[idx].real, V[:, idx].real
+            # error equation: b = 0, x0 = v; after smoothing x = damping * v
+            x = H.cheb(0, np.zeros(prob.n), v)
+            Tk = lambda t: np.cos(k * np.arccos(t)) if abs(t) <= 1 else np.cosh(k * np.arccosh(abs(t))) * np.sign(t) ** k
+            damp = Tk((theta - mu) / delta) / Tk(theta / delta)
+            assert np.allclose(x, damp * v, atol=1e-11 * np.abs(v).max())
+
+
+# ----------------------------------------------------------------------------- coarsest
+def test_cholesky_matches_numpy():
+    rng = np.random.default_rng(5)
+    for n in [1, 3, 50, 200]:
+        M = rng.normal(size=(n, n))
+        A = M @ M.T + n * np.eye(n)
+        L = oracle.cholesky(A)
+        assert np.allclose(L, np.linalg.cholesky(A), atol=1e-12 * n)
+        b = rng.normal(size=n)
+        assert np.allclose(oracle.chol_solve(L, b), np.linalg.solve(A, b), atol=1e-12)
+    with pytest.raises(RuntimeError):
+        oracle.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
+# ----------------------------------------------------------------------------- V-cycle / PCG
+@pytest.mark.parametrize("n,p,mesh,k", [(4, 4, "uniform", 3), (8, 2, "jitter", 2), (3, 6, "jitter", 3)])
+def test_vcycle_is_symmetric(n, p, mesh, k):
+    prob = fegen.make(n, p, mesh=mesh, lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+    rng = np.random.default_rng(2)
+    u, w = rng.normal(size=prob.n), rng.normal(size=prob.n)
+    u[prob.boundary == 1] = 0
+    w[prob.boundary == 1] = 0
+    a, b = np.dot(H.vcycle(u), w), np.dot(u, H.vcycle(w))
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+
+
+@pytest.mark.parametrize("n,p,mesh,lam", [(2, 2, "uniform", 1.0), (2, 4, "jitter", 10.0), (3, 3, "graded", 1000.0),
+                                          (8, 2, "jitter", 0.0)])
+def test_pcg_matches_dense_direct_solve(n, p, mesh, lam):
+    prob = fegen.make(n, p, mesh=mesh, lam=lam, rhs="fourier", rhs_seed=1001)
+    H = oracle.Hierarchy.from_problem(prob)
+    x, it, rr, hist, st = H.solve(prob.b, rtol=1e-12)
+    assert st == "ok" and rr <= 1e-12
+    xd = np.linalg.solve(prob.scipy().toarray(), prob.b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    # Dirichlet entries are not frozen (the coarse correction reaches them through P), but
+    # they converge to the exact value 0 with the rest of the solution
+    assert np.max(np.abs(x[prob.boundary == 1])) <= 1e-10 * np.max(np.abs(xd))
+    assert np.all(np.diff(hist) < 0.5) or it < 3
+
+
+def test_pcg_beats_jacobi_cg_and_matches_discretisation_error():
+    # the paper's qualitative result (Sec. 3.1.2): far fewer iterations than diagonally
+    # preconditioned CG on a rough right-hand side
+    prob = fegen.make(4, 4, mesh="jitter", lam=1.0, rhs="fourier")
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=3)
+    x, it, rr, hist, st = H.solve(prob.b, rtol=1e-10)
+    A = prob.scipy()
+    count = [0]
+    sla.cg(A, prob.b, rtol=1e-10, M=sp.diags(1.0 / A.diagonal()), maxiter=5000,
+           callback=lambda _: count.__setitem__(0, count[0] + 1))
+    assert it * 5 < count[0]
+    # on the manufactured problem the iterate carries the discretisation error of the direct solve
+    prob = fegen.make(4, 4, mesh="uniform", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=3)
+    x = H.solve(prob.b, rtol=1e-10)[0]
+    xd = sla.spsolve(prob.scipy().tocsc(), prob.b)
+    assert abs(prob.l2_error(x) - prob.l2_error(xd)) <= 1e-6 * prob.l2_error(xd)
+
+
+def test_force_iters_and_flexible_cg():
+    prob = fegen.make(4, 4, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    x, it, rr, hist, st = H.solve(prob.b, rtol=1e-8)
+    xf, itf, rrf, _, stf = H.solve(prob.b, force_iters=it + 3)
+    assert itf == it + 3 and rrf < rr
+    # flexible CG with the same symmetric V-cycle follows PCG to rounding
+    xfl, itfl, rrfl, histfl, _ = H.solve(prob.b, rtol=1e-8, flexible=1)
+    assert abs(itfl - it) <= 1
+    # FP32 V-cycle inside FP64 flexible CG reaches the same tolerance
+    x32, it32, rr32, _, st32 = H.solve(prob.b, rtol=1e-8, precision=1)
+    assert st32 == "ok" and rr32 <= 1e-8
+    r_true = prob.b - prob.scipy() @ x32
+    assert np.linalg.norm(r_true) <= 2e-8 * np.linalg.norm(prob.b)
+
+
+def test_hierarchy_invariant_under_renumbering_and_element_symmetries():
+    base = fegen.make(6, 2, mesh="jitter", lam=1.0)
+    perm = fegen.make(6, 2, mesh="jitter", lam=1.0, perm_seed=11, sym_seed=13)
+    Hb = oracle.Hierarchy.from_problem(base)
+    Hp = oracle.Hierarchy.from_problem(perm)
+    assert Hb.num_levels == Hp.num_levels
+    # p-levels are the same operators up to relabelling (compare spectra of level 1)
+    for l in range(2):
+        ib, ip = Hb.level_info(l), Hp.level_info(l)
+        assert (ib["n"], ib["nnz"]) == (ip["n"], ip["nnz"])
+    eb = np.linalg.eigvalsh(_dense_level(Hb, 1))
+    ep = np.linalg.eigvalsh(_dense_level(Hp, 1))
+    assert np.allclose(eb, ep, atol=1e-12 * eb.max())
+    # the solutions agree through the relabelling
+    xb = Hb.solve(base.b, rtol=1e-11)[0]
+    xp = Hp.solve(perm.b, rtol=1e-11)[0]
+    key = lambda c: np.lexsort(np.round(c, 12).T[::-1])
+    pmap = np.empty(base.n, np.int64)
+    pmap[key(base.coords)] = key(perm.coords)
+    assert np.allclose(xp[pmap], xb, atol=1e-9 * np.abs(xb).max())
+
+
+def test_results_do_not_depend_on_thread_count():
+    import os
+    import subprocess
+    import sys
+    code = ("import fegen, oracle, numpy as np;"
+            "P = fegen.make(6, 2, mesh='jitter', lam=1.0);"
+            "H = oracle.Hierarchy.from_problem(P);"
+            "x = H.solve(P.b, rtol=1e-10)[0];"
+            "print(np.frombuffer(x.tobytes(), np.uint64).sum() % 1000003)")
+    outs = []
+    for t in ["1", "3"]:
+        env = dict(os.environ, OMP_NUM_THREADS=t)
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        outs.append(r.stdout.strip())
+    assert outs[0] == outs[1]
