@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark: GIAMG-PCG time to a 1e-8 relative residual on one GB300.
+
+Workload (default): Helmholtz -lap u + 10 u = f on the unit cube, 16^3 hexahedra with interior
+vertices jittered by +-0.2 h (seed 1), nodal GLL order 6: 912,673 dofs, 410,227,705 nonzeros
+(FP64 CSR, 4.9 GB), manufactured right-hand side, Chebyshev degree 3, rtol 1e-8.  One step is one
+full solve (all V-cycle levels, the outer CG) with inputs resident in HBM.  The headline is the
+FP32 V-cycle inside FP64 flexible CG; the FP64 V-cycle in PCG is timed the same way beside it.
+
+  python bench.py [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (plain FP64 C, OpenMP row loops) on the host cores with
+the same metric: each step is one oracle CG iteration (one V-cycle and one product) scaled to the
+oracle's iteration count.  Under torchrun every rank solves its own copy (replicas; no
+collective on the data path) and rank 0 prints the line with the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-1e-8 relres & V-cycle HBM GB/s, FP32-in-FP64 vs FP64; p50/p99 ms"
+WORKLOAD_TEXT = {
+    "helmholtz_16cube_jitter_p6": "Helmholtz lambda=10, unit cube, 16^3 hex jittered +-0.2h (seed 1), GLL p=6",
+    "helmholtz_4cube_p4": "Helmholtz lambda=1, unit cube, 4^3 hex, GLL p=4",
+    "poisson_24cube_jitter_p4": "Poisson lambda=0, unit cube, 24^3 hex jittered (seed 2), GLL p=4",
+    "helmholtz_12cube_graded_p8": "Helmholtz lambda=1000, kappa=1+0.5sin(2pi x), 12^3 hex graded to z=0, GLL p=8",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="helmholtz_16cube_jitter_p6")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = (len(v) - 1) * q
+    lo = int(k)
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 8:
+                    continue
+                try:
+                    sm.append(float(p[0]))
+                    mx.append(float(p[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2512_15121_gb300", "csrc", "solve_kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, mode):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if it was taken
+    on the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload][mode]
+        if e.get("solve_kernels_sha") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as td
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    td.init_process_group(backend)
+    return rank, ws, local, td
+
+
+def max_over_ranks(td, v):
+    if td is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], device="cuda" if torch.cuda.is_available() else "cpu")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, ws, local, td = dist()
+    if rank != 0:
+        return
+    import fegen
+    import oracle
+    k = fegen.WORKLOADS[args.workload]["k"]
+    prob = fegen.workload(args.workload)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+    # iterations to the tolerance (untimed), then bounded steps of one iteration each
+    _, iters, _, _, st = H.solve(prob.b, rtol=args.rtol, precision=1)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        H.solve(prob.b, force_iters=1, precision=1)
+        dt = (time.perf_counter() - t0) * 1e3
+        if s >= args.warmup:
+            times.append(dt * iters)
+    cores = oracle.num_threads()
+    p50 = pct(times, 0.5)
+    line = {"metric": METRIC, "value": p50, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(times) / len(times), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle in f64 FCG (CPU oracle)",
+            "data": "synthetic", "impl": "reference", "p99_ms": pct(times, 0.99), "iters": iters,
+            "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
+                       "dofs": prob.n, "nnz": prob.nnz, "rtol": args.rtol, "cheb_degree": k},
+            "cpu_baseline": {"value": p50, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: one oracle CG iteration (1 V-cycle + 1 SpMV) on the full "
+                                       f"workload, scaled by the oracle's {iters} iterations to rtol"},
+            "e2e": {"value": p50, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import fegen
+    import paper_2512_15121_gb300 as g
+
+    rank, ws, local, td = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    k = fegen.WORKLOADS[args.workload]["k"]
+    prob = fegen.workload(args.workload)
+    stream = torch.cuda.current_stream(dev)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    levels = [S.level_info(l) for l in range(S.num_levels)]
+    b = torch.from_numpy(prob.b).to(dev)
+    x = torch.empty_like(b)
+
+    def timed(precision):
+        for _ in range(args.warmup):
+            S.solve(b, rtol=args.rtol, precision=precision, x=x)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if td:
+            td.barrier()
+        torch.cuda.synchronize()
+        S.profile(True)
+        c0 = g.launch_count()
+        t_start = time.perf_counter()
+        its = []
+        for e0, e1 in ev:
+            e0.record(stream)
+            _, it, rr = S.solve(b, rtol=args.rtol, precision=precision, x=x)
+            e1.record(stream)
+            its.append(it)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t_start) * 1e3
+        if td:
+            td.barrier()
+        launches = g.launch_count() - c0
+        ms = [a.elapsed_time(b_) for a, b_ in ev]
+        prof = [S.profile_read(c) for c in range(6)]
+        S.profile(False)
+        _, true_rr = S.stats(0)
+        return dict(p50=pct(ms, 0.5), p99=pct(ms, 0.99), total=sum(ms), wall=wall, iters=its[-1],
+                    iters_all=sorted(set(its)), launches=launches, prof=prof, true_relres=true_rr)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    mixed = timed(1)
+    fp64 = timed(0)
+    clk = clocks.stop()
+
+    # end to end through the C ABI with host buffers (pinned): H2D of b and D2H of x inside
+    S.set_device_ptrs(False)
+    bh = torch.from_numpy(prob.b).pin_memory()
+    xh = torch.empty(prob.n, dtype=torch.float64).pin_memory()
+    bh_np, xh_np = bh.numpy(), xh.numpy()
+    e2e = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        S.solve(bh_np, rtol=args.rtol, precision=1, x=xh_np)
+        dt = (time.perf_counter() - t0) * 1e3
+        if s >= args.warmup:
+            e2e.append(dt)
+    S.set_device_ptrs(True)
+
+    peak, peak_kind = measured_peaks()
+
+    def roof(res, mode):
+        ms, cnt, by = res["prof"][0]
+        if cnt == 0 or ms <= 0:
+            return None
+        achieved = by / cnt / (ms / cnt * 1e-3) / 1e9
+        tr = ncu_traffic(args.workload, mode)
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": tr,
+                "kernel": f"csr_rows ({'FP32' if mode == 'mixed' else 'FP64'} Chebyshev step / residual, finest level)",
+                "launches": cnt, "avg_launch_ms": round(ms / cnt, 4),
+                "algorithmic_bytes_per_launch": round(by / cnt), "peak_kind": peak_kind}
+
+    def vcycle_gbs(res):
+        # V-cycle bytes and time: every category except the outer CG product (5)
+        ms = sum(res["prof"][c][0] for c in range(5))
+        by = sum(res["prof"][c][2] for c in range(5))
+        return round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None
+
+    value = max_over_ranks(td, mixed["p50"])
+    ms_per_step = max_over_ranks(td, mixed["wall"] / args.steps)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, k, args.rtol, mixed["iters"])
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle in f64 FCG",
+        "data": "synthetic (seeded jittered-hex GLL assembly; stands in for the paper's Nektar++ matrices)",
+        "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
+                   "dofs": prob.n, "nnz": prob.nnz, "rtol": args.rtol, "cheb_degree": k,
+                   "levels": [(L["n"], L["nnz"], L["order"]) for L in levels],
+                   "l2": "inputs larger than L2 (finest matrix 4.9 GB), no flush", "parallelism": "replicas"},
+        "p50_ms": round(mixed["p50"], 3), "p99_ms": round(mixed["p99"], 3), "iters": mixed["iters"],
+        "true_relres": mixed["true_relres"],
+        "fp64": {"p50_ms": round(fp64["p50"], 3), "p99_ms": round(fp64["p99"], 3), "iters": fp64["iters"],
+                 "true_relres": fp64["true_relres"], "roofline": roof(fp64, "fp64"), "vcycle_gbs": vcycle_gbs(fp64)},
+        "speedup_mixed_vs_fp64": round(fp64["p50"] / mixed["p50"], 3),
+        "vcycle_gbs": vcycle_gbs(mixed),
+        "setup_ms": round(setup_ms, 1),
+        "roofline": roof(mixed, "mixed"),
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(pct(e2e, 0.5), 3), "unit": "ms", "h2d_bytes_per_step": 8 * prob.n,
+                "d2h_bytes_per_step": 8 * prob.n},
+        "gpu_launches": mixed["launches"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    S.close()
+
+
+def cpu_baseline(prob, k, rtol, iters):
+    """The oracle as it stands, on the host cores: two CG iterations (FP32 V-cycle, flexible CG)
+    on the full workload, scaled to the GPU's iteration count."""
+    import oracle
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+    t0 = time.perf_counter()
+    H.solve(prob.b, force_iters=2, precision=1)
+    per_iter = (time.perf_counter() - t0) * 1e3 / 2
+    H.close()
+    return {"value": round(per_iter * iters, 1), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"2 oracle CG iterations (FP32 V-cycle in FP64 flexible CG) on the full workload, "
+                      f"scaled to {iters} iterations"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

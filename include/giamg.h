@@ -1,0 +1,175 @@
+/*
+ * giamg.h -- C ABI of the GB300 GIAMG solver: geometrically informed algebraic multigrid
+ * preconditioned conjugate gradients for assembled high-order (nodal GLL, hexahedral) finite
+ * element systems, after arXiv 2512.15121.
+ *
+ * The problem statement follows the paper: the caller hands over an assembled symmetric
+ * positive definite matrix A (Eq. 1, Ax = b) and the element-to-dof map ("l2g") whose column
+ * order implies the basis order inside each element (Sec. 2.1 and the appendix, Eq. 8:
+ * local index (p+1)^2 i + (p+1) j + k, i along x).  Nothing else about the geometry is needed;
+ * nodal coordinates may be passed for validation only.
+ *
+ * Setup builds the hierarchy on the GPU: p-coarsening p -> p/2 -> ... -> 1 by element-local
+ * interpolation (Algorithms 2-4 and 7), then h-coarsening by smoothed aggregation (Sec. 2.5)
+ * while a level has more than coarse_max rows, Galerkin coarse operators R A P with R = P^T
+ * (Sec. 2), Jacobi-Chebyshev smoother bounds, and a dense Cholesky factor of the coarsest
+ * level.  A solve runs preconditioned CG with one V-cycle (Algorithm 1) per iteration.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GIAMG_OK (0) or a negative GIAMG_ERR_* code; giamg_last_error() then holds
+ *     a one-line description (per calling thread).  Nothing is thrown; no call aborts.
+ *   - Ownership: the caller owns every array it passes.  The library copies what it keeps
+ *     (host mode) or reads device arrays without retaining them (device mode); the handle owns
+ *     all device memory it allocates until giamg_free.
+ *   - Pointers: with options.device_ptrs == 0 all vector/matrix arguments are host pointers;
+ *     with device_ptrs == 1 they are device pointers on the handle's device.  Scalar outputs
+ *     (iters, relres, sizes) are always host pointers.
+ *   - Streams: all work is ordered on the stream given to giamg_setup (NULL = legacy default
+ *     stream).  Calls that return host scalars synchronise that stream before returning.
+ *   - Threads: a handle is not thread-safe; distinct handles are independent.
+ *   - Layouts: CSR with int64 row pointers, int32 column indices ascending within each row,
+ *     float64 values.  Vectors are contiguous float64.  Multi-RHS blocks are row-major n x m.
+ */
+#ifndef GIAMG_H
+#define GIAMG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GIAMG_API __attribute__((visibility("default")))
+#else
+#define GIAMG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GIAMG_OK = 0,
+  GIAMG_ERR_ARG = -1,        /* invalid argument (NULL pointer, size, option, level index) */
+  GIAMG_ERR_ORDER = -2,      /* element orders not uniform, or outside 1..GIAMG_MAX_ORDER */
+  GIAMG_ERR_MAP = -3,        /* element map out of range or inconsistent with A's pattern / coords */
+  GIAMG_ERR_OOM = -4,        /* device or host allocation failed */
+  GIAMG_ERR_CUDA = -5,       /* a CUDA runtime call failed (message carries the CUDA error) */
+  GIAMG_ERR_NOT_SPD = -6,    /* non-positive diagonal or Cholesky pivot */
+  GIAMG_ERR_BREAKDOWN = -7,  /* CG breakdown: p^T A p <= 0, r^T z <= 0 or a NaN */
+  GIAMG_ERR_MAXITER = -8,    /* max_iter reached above rtol; the outputs are still valid */
+  GIAMG_ERR_TIMEOUT = -9     /* a bounded device-side wait expired */
+};
+
+enum { GIAMG_LEVEL_P = 0, GIAMG_LEVEL_H = 1, GIAMG_LEVEL_COARSEST = 2 };
+#define GIAMG_MAX_ORDER 12
+
+typedef struct giamg_hierarchy* giamg_handle;
+
+typedef struct {
+  int cheb_degree;        /* Chebyshev degree k for pre- and post-smoothing (Sec. 2).  Default 3
+                             (Table 1 uses 3 for the Helmholtz operator; Sec. 3.2 uses 2). */
+  double cheb_lo;         /* smoothing interval [cheb_lo, cheb_hi] * rho_hat of D^-1 A; 0.1 */
+  double cheb_hi;         /* 1.1 */
+  int lanczos_steps;      /* Lanczos steps for rho_hat; 20 */
+  int coarse_max;         /* h-coarsen while a level has more rows than this; 500 */
+  int max_levels;         /* 16 */
+  double strength_theta;  /* 0: structural strength graph (bit-exact hierarchy); > 0 keeps
+                             |a_ij| >= theta sqrt(a_ii a_jj) */
+  int precision;          /* 0: FP64 V-cycle in PCG; 1: FP32 V-cycle in FP64 flexible CG */
+  int max_iter;           /* 1000 */
+  int force_iters;        /* 0, or run exactly this many iterations (parity tests) */
+  int device_ptrs;        /* 0: host arrays; 1: device arrays (e.g. torch tensors) */
+  int hash_kind;          /* node hash of MIS-2 / Lanczos start: 0 SplitMix64-based, 1 identity */
+} giamg_options;
+
+/* Fill *opt with the defaults listed above. */
+GIAMG_API void giamg_default_options(giamg_options* opt);
+
+/* Build the hierarchy (Sec. 2; Algorithms 2-4, 7; Sec. 2.5).
+ *   n, row_ptr[n+1], col_idx[nnz], val[nnz]: A, symmetric positive definite, columns ascending.
+ *     Dirichlet rows, if any, are identity rows whose columns have been removed elsewhere.
+ *   n_elem, elem_dof[n_elem][(p+1)^3]: element-to-dof map, entries in [0, n).
+ *   elem_order[n_elem]: polynomial order of each element; all equal (GIAMG_ERR_ORDER if not).
+ *     With p = 1 there is no p-level and elem_dof may be NULL.
+ *   coords[n][3]: nodal coordinates or NULL; when given, every element's nodes must be the
+ *     trilinear image of the GLL tensor points (1e-8 of the element size), else GIAMG_ERR_MAP.
+ *   opt: options (NULL = defaults).  cuda_stream: a cudaStream_t or NULL.
+ *   *out: the new handle.  Every element pair (a, b) must be present in A's pattern unless
+ *   one of the two rows is a Dirichlet identity row (GIAMG_ERR_MAP otherwise). */
+GIAMG_API int giamg_setup(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                int32_t n_elem, const int32_t* elem_dof, const int32_t* elem_order,
+                const double* coords, const giamg_options* opt, void* cuda_stream,
+                giamg_handle* out);
+
+/* Solve A x = b by PCG with one V-cycle per iteration (Sec. 2), x0 = 0 (Sec. 3.1), stopping
+ * when ||r||_2 / ||b||_2 <= rtol on the recursive residual, or after force_iters iterations
+ * when that option is set.  x: output (n).  *iters: iterations done; *relres: final relative
+ * residual.  GIAMG_ERR_MAXITER leaves a valid x. */
+GIAMG_API int giamg_solve(giamg_handle h, const double* b, double* x, double rtol, int* iters, double* relres);
+
+/* giamg_solve with the precision (0 FP64, 1 FP32 V-cycle + flexible CG) and force_iters chosen
+ * per call instead of from the handle's options. */
+GIAMG_API int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double* b, double* x,
+                   double rtol, int* iters, double* relres);
+
+/* After a solve: relative residual history hist[0..min(len, iters+1)) of the recursive
+ * residual, and the true relative residual ||b - A x|| / ||b|| recomputed in FP64. */
+GIAMG_API int giamg_solve_stats(giamg_handle h, double* hist, int len, double* true_relres);
+
+/* Hierarchy inspection (used by the bit-exact structure tests). */
+GIAMG_API int giamg_num_levels(giamg_handle h, int* n_levels);
+/* kind: GIAMG_LEVEL_*; n, nnz of A_l; order: p of a p-level (0 for aggregated levels);
+ * p_nnz / n_next: size of the prolongation to level l+1 (0 on the coarsest level). */
+GIAMG_API int giamg_level_info(giamg_handle h, int level, int* kind, int64_t* n, int64_t* nnz, int* order,
+                     int64_t* p_nnz, int64_t* n_next);
+/* Copy A_l to caller arrays sized from giamg_level_info (row_ptr n+1, col_idx/val nnz; any may
+ * be NULL), and the aggregate id of every row of an h-level (NULL to skip).  Host pointers
+ * unless device_ptrs is set. */
+GIAMG_API int giamg_export_level(giamg_handle h, int level, int64_t* row_ptr, int32_t* col_idx, double* val,
+                       int32_t* aggregates);
+/* Copy the assembled prolongation P_l (n x n_next, p_nnz entries) built during setup. */
+GIAMG_API int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_ptr, int32_t* col_idx,
+                              double* val);
+/* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */
+GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
+
+/* Single steps of the solve, on the handle's stream (parity tests call these):
+ *   giamg_apply_vcycle: z = V(r), Algorithm 1 from the finest level (precision 0 / 1).
+ *   giamg_level_spmv:   y = A_l x.
+ *   giamg_level_smooth: Chebyshev smoothing of A_l x = b in place (x_is_zero: x enters as 0).
+ *   giamg_level_restrict: r_c = R_l r_f (R = P^T; element form on p-levels).
+ *   giamg_level_prolong:  x_f += P_l e_c (element form on p-levels).
+ *   giamg_coarse_solve:  x = A_L^-1 r on the coarsest level (Cholesky triangular solves). */
+GIAMG_API int giamg_apply_vcycle(giamg_handle h, int precision, const double* r, double* z);
+GIAMG_API int giamg_level_spmv(giamg_handle h, int level, const double* x, double* y);
+GIAMG_API int giamg_level_smooth(giamg_handle h, int level, const double* b, double* x, int x_is_zero);
+GIAMG_API int giamg_level_restrict(giamg_handle h, int level, const double* r_f, double* r_c);
+GIAMG_API int giamg_level_prolong(giamg_handle h, int level, const double* e_c, double* x_f);
+GIAMG_API int giamg_coarse_solve(giamg_handle h, const double* r, double* x);
+
+/* Switch the pointer mode of later calls on this handle (0 host arrays, 1 device arrays). */
+GIAMG_API int giamg_set_device_ptrs(giamg_handle h, int device_ptrs);
+
+/* Opt-in timers (CUDA events around the launches of each category, on the handle's stream):
+ *   0 CSR row kernels of the finest level inside the V-cycle (smoother steps, residual)
+ *   1 CSR row kernels of the coarser levels   2 transfers   3 coarsest solve   4 vectors
+ *   5 the outer CG product q = A p
+ * giamg_profile_enable resets the records; giamg_profile_read synchronises the stream and
+ * returns, for one category, the summed kernel time (ms), the number of timed launches and the
+ * algorithmic bytes those launches must move (matrix values, indices and row pointers once,
+ * each vector once). */
+GIAMG_API int giamg_profile_enable(giamg_handle h, int enable);
+GIAMG_API int giamg_profile_read(giamg_handle h, int category, double* total_ms, int64_t* launches,
+                                 double* bytes);
+
+/* Number of kernels this library has launched in the process so far (all handles). */
+GIAMG_API int giamg_launch_count(int64_t* count);
+
+/* Release the handle and all of its device memory.  NULL is accepted. */
+GIAMG_API int giamg_free(giamg_handle h);
+
+/* Last error message of the calling thread ("" if none). */
+GIAMG_API const char* giamg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

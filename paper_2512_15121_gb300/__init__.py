@@ -1,0 +1,324 @@
+"""Python binding of the GB300 GIAMG solver (C ABI in include/giamg.h, libgiamg.so).
+
+Argument marshalling only: every step of setup and solve runs in the library's CUDA kernels.
+The functions keep the C names (giamg_setup, giamg_solve, ...); `Solver` wraps a handle.
+Vectors are numpy arrays (host mode, device_ptrs = 0) or CUDA torch tensors (device mode,
+device_ptrs = 1); PyTorch only supplies device memory and the stream.
+
+Importing succeeds without the shared library (so the CPU test suite can inspect the
+package); every call raises RuntimeError until `build()` has produced libgiamg.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgiamg.so")
+
+GIAMG_OK, GIAMG_ERR_ARG, GIAMG_ERR_ORDER, GIAMG_ERR_MAP, GIAMG_ERR_OOM = 0, -1, -2, -3, -4
+GIAMG_ERR_CUDA, GIAMG_ERR_NOT_SPD, GIAMG_ERR_BREAKDOWN, GIAMG_ERR_MAXITER, GIAMG_ERR_TIMEOUT = -5, -6, -7, -8, -9
+GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
+
+# every entry point the header declares (checked by the CPU tests against the .so)
+EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
+           "giamg_num_levels", "giamg_level_info", "giamg_export_level", "giamg_export_prolongation",
+           "giamg_level_rho", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_smooth",
+           "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
+           "giamg_last_error", "giamg_set_device_ptrs", "giamg_profile_enable", "giamg_profile_read",
+           "giamg_launch_count"]
+
+
+class GiamgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double),
+                ("lanczos_steps", ctypes.c_int), ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("strength_theta", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("force_iters", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("hash_kind", ctypes.c_int)]
+
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from . import nvcc_build
+    return nvcc_build.build(force=force, verbose=verbose)
+
+
+def lib():
+    """Load libgiamg.so; raise if it is missing (there is no fallback implementation)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgiamg.so not built ({LIB_PATH}); run paper_2512_15121_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        L.giamg_default_options.argtypes = [P(Options)]
+        L.giamg_default_options.restype = None
+        L.giamg_setup.argtypes = [i64, vp, vp, vp, ctypes.c_int32, vp, vp, vp, P(Options), vp, P(vp)]
+        L.giamg_solve.argtypes = [vp, vp, vp, dbl, P(i32), P(dbl)]
+        L.giamg_solve_ex.argtypes = [vp, i32, i32, vp, vp, dbl, P(i32), P(dbl)]
+        L.giamg_solve_stats.argtypes = [vp, vp, i32, P(dbl)]
+        L.giamg_num_levels.argtypes = [vp, P(i32)]
+        L.giamg_level_info.argtypes = [vp, i32, P(i32), P(i64), P(i64), P(i32), P(i64), P(i64)]
+        L.giamg_export_level.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.giamg_export_prolongation.argtypes = [vp, i32, vp, vp, vp]
+        L.giamg_level_rho.argtypes = [vp, i32, P(dbl)]
+        L.giamg_apply_vcycle.argtypes = [vp, i32, vp, vp]
+        L.giamg_level_spmv.argtypes = [vp, i32, vp, vp]
+        L.giamg_level_smooth.argtypes = [vp, i32, vp, vp, i32]
+        L.giamg_level_restrict.argtypes = [vp, i32, vp, vp]
+        L.giamg_level_prolong.argtypes = [vp, i32, vp, vp]
+        L.giamg_coarse_solve.argtypes = [vp, vp, vp]
+        L.giamg_free.argtypes = [vp]
+        L.giamg_set_device_ptrs.argtypes = [vp, i32]
+        L.giamg_profile_enable.argtypes = [vp, i32]
+        L.giamg_profile_read.argtypes = [vp, i32, P(dbl), P(i64), P(dbl)]
+        L.giamg_launch_count.argtypes = [P(i64)]
+        L.giamg_last_error.argtypes = []
+        L.giamg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != GIAMG_OK:
+        raise GiamgError(rc, lib().giamg_last_error().decode())
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def default_options(**over) -> Options:
+    o = Options()
+    lib().giamg_default_options(ctypes.byref(o))
+    for k, v in over.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------- C-named functions
+def giamg_setup(n, row_ptr, col_idx, val, n_elem, elem_dof, elem_order, coords=None, options=None, stream=None):
+    h = ctypes.c_void_p()
+    opt = options if options is not None else default_options()
+    _check(lib().giamg_setup(n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), n_elem, _ptr(elem_dof), _ptr(elem_order),
+                             _ptr(coords), ctypes.byref(opt), ctypes.c_void_p(stream) if stream else None,
+                             ctypes.byref(h)))
+    return h
+
+
+def giamg_solve(h, b, x, rtol):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    rc = lib().giamg_solve(h, _ptr(b), _ptr(x), rtol, ctypes.byref(it), ctypes.byref(rr))
+    return rc, it.value, rr.value
+
+
+def giamg_solve_ex(h, precision, force_iters, b, x, rtol):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    rc = lib().giamg_solve_ex(h, precision, force_iters, _ptr(b), _ptr(x), rtol, ctypes.byref(it), ctypes.byref(rr))
+    return rc, it.value, rr.value
+
+
+def launch_count() -> int:
+    c = ctypes.c_int64()
+    _check(lib().giamg_launch_count(ctypes.byref(c)))
+    return c.value
+
+
+def giamg_free(h):
+    _check(lib().giamg_free(h))
+
+
+class Solver:
+    """A GIAMG hierarchy on the GPU (one handle)."""
+
+    def __init__(self, n, row_ptr, col, val, elem_dof=None, p=1, coords=None, stream=None, **opts):
+        self.opts = default_options(**opts)
+        self.device = bool(self.opts.device_ptrs)
+        self.n = int(n)
+        if self.device:
+            import torch
+            ed = elem_dof
+            n_elem = int(ed.shape[0]) if ed is not None else 0
+            order = torch.full((max(n_elem, 1),), p, dtype=torch.int32, device=row_ptr.device)
+            if stream is None:
+                stream = torch.cuda.current_stream(row_ptr.device).cuda_stream
+        else:
+            row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+            col = np.ascontiguousarray(col, np.int32)
+            val = np.ascontiguousarray(val, np.float64)
+            ed = None if elem_dof is None else np.ascontiguousarray(elem_dof, np.int32)
+            n_elem = int(ed.shape[0]) if ed is not None else 0
+            order = np.full(max(n_elem, 1), p, np.int32)
+            coords = None if coords is None else np.ascontiguousarray(coords, np.float64)
+        self._h = giamg_setup(self.n, row_ptr, col, val, n_elem, ed, order if n_elem else None, coords,
+                              self.opts, stream)
+
+    @classmethod
+    def from_problem(cls, prob, device=False, coords=False, **opts):
+        if device:
+            import torch
+            dev = torch.device("cuda", torch.cuda.current_device())
+            t = lambda a: torch.from_numpy(a).to(dev)
+            return cls(prob.n, t(prob.row_ptr), t(prob.col), t(prob.val), t(prob.elem_dof), prob.p,
+                       t(prob.coords) if coords else None, device_ptrs=1, **opts)
+        return cls(prob.n, prob.row_ptr, prob.col, prob.val, prob.elem_dof, prob.p,
+                   prob.coords if coords else None, **opts)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            giamg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- allocation helpers
+    def _vec(self, n):
+        if self.device:
+            import torch
+            return torch.empty(n, dtype=torch.float64, device="cuda")
+        return np.empty(n, np.float64)
+
+    def _in(self, v):
+        if self.device:
+            import torch
+            if not isinstance(v, torch.Tensor):
+                v = torch.from_numpy(np.ascontiguousarray(v, np.float64))
+            return v.to("cuda", torch.float64).contiguous()
+        return np.ascontiguousarray(v, np.float64)
+
+    # -------------------------------------------------------------- solve
+    def solve(self, b, rtol=1e-8, precision=None, force_iters=None, x=None):
+        """Returns (x, iters, relres); raises GiamgError on failure other than max_iter."""
+        b = self._in(b)
+        x = self._vec(self.n) if x is None else x
+        prec = self.opts.precision if precision is None else precision
+        force = self.opts.force_iters if force_iters is None else force_iters
+        rc, it, rr = giamg_solve_ex(self._h, prec, force, b, x, rtol)
+        if rc not in (GIAMG_OK, GIAMG_ERR_MAXITER):
+            _check(rc)
+        self.last_status = rc
+        return x, it, rr
+
+    def stats(self, hist_len=0):
+        hist = np.zeros(max(hist_len, 1))
+        tr = ctypes.c_double()
+        _check(lib().giamg_solve_stats(self._h, _ptr(hist), hist_len, ctypes.byref(tr)))
+        return hist[:hist_len], tr.value
+
+    # -------------------------------------------------------------- profiling
+    def set_device_ptrs(self, on: bool):
+        _check(lib().giamg_set_device_ptrs(self._h, 1 if on else 0))
+        self.device = bool(on)
+
+    def profile(self, enable: bool):
+        _check(lib().giamg_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self, category: int):
+        ms, cnt, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().giamg_profile_read(self._h, category, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by)))
+        return ms.value, cnt.value, by.value
+
+    # -------------------------------------------------------------- hierarchy
+    @property
+    def num_levels(self):
+        k = ctypes.c_int()
+        _check(lib().giamg_num_levels(self._h, ctypes.byref(k)))
+        return k.value
+
+    def level_info(self, l):
+        k, o = ctypes.c_int(), ctypes.c_int()
+        n, nnz, pn, nn = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().giamg_level_info(self._h, l, ctypes.byref(k), ctypes.byref(n), ctypes.byref(nnz),
+                                      ctypes.byref(o), ctypes.byref(pn), ctypes.byref(nn)))
+        return dict(kind=k.value, n=n.value, nnz=nnz.value, order=o.value, p_nnz=pn.value, n_next=nn.value)
+
+    def _arrays(self, shapes):
+        if self.device:
+            import torch
+            td = {np.int64: torch.int64, np.int32: torch.int32, np.float64: torch.float64}
+            return [torch.empty(max(s, 1), dtype=td[d], device="cuda") for s, d in shapes]
+        return [np.empty(max(s, 1), d) for s, d in shapes]
+
+    def _host(self, a, n):
+        if self.device:
+            return a[:n].cpu().numpy()
+        return a[:n]
+
+    def level(self, l):
+        info = self.level_info(l)
+        rp, ci, v, agg = self._arrays([(info["n"] + 1, np.int64), (info["nnz"], np.int32), (info["nnz"], np.float64),
+                                       (info["n"], np.int32)])
+        want_agg = info["kind"] == GIAMG_LEVEL_H
+        _check(lib().giamg_export_level(self._h, l, _ptr(rp), _ptr(ci), _ptr(v), _ptr(agg) if want_agg else None))
+        return (self._host(rp, info["n"] + 1), self._host(ci, info["nnz"]), self._host(v, info["nnz"]),
+                self._host(agg, info["n"]) if want_agg else None)
+
+    def prolongation(self, l):
+        info = self.level_info(l)
+        rp, ci, v = self._arrays([(info["n"] + 1, np.int64), (info["p_nnz"], np.int32), (info["p_nnz"], np.float64)])
+        _check(lib().giamg_export_prolongation(self._h, l, _ptr(rp), _ptr(ci), _ptr(v)))
+        return (self._host(rp, info["n"] + 1), self._host(ci, info["p_nnz"]), self._host(v, info["p_nnz"]),
+                info["n_next"])
+
+    def rho_hat(self, l):
+        r = ctypes.c_double()
+        _check(lib().giamg_level_rho(self._h, l, ctypes.byref(r)))
+        return r.value
+
+    # -------------------------------------------------------------- single steps
+    def vcycle(self, r, precision=0):
+        r = self._in(r)
+        z = self._vec(self.n)
+        _check(lib().giamg_apply_vcycle(self._h, precision, _ptr(r), _ptr(z)))
+        return z
+
+    def spmv(self, l, x):
+        x = self._in(x)
+        y = self._vec(self.level_info(l)["n"])
+        _check(lib().giamg_level_spmv(self._h, l, _ptr(x), _ptr(y)))
+        return y
+
+    def smooth(self, l, b, x=None):
+        b = self._in(b)
+        xo = self._vec(self.level_info(l)["n"]) if x is None else self._in(x).clone() if self.device else self._in(x).copy()
+        _check(lib().giamg_level_smooth(self._h, l, _ptr(b), _ptr(xo), 1 if x is None else 0))
+        return xo
+
+    def restrict(self, l, rf):
+        rf = self._in(rf)
+        rc = self._vec(self.level_info(l)["n_next"])
+        _check(lib().giamg_level_restrict(self._h, l, _ptr(rf), _ptr(rc)))
+        return rc
+
+    def prolong(self, l, ec, xf):
+        ec = self._in(ec)
+        xo = self._in(xf).clone() if self.device else self._in(xf).copy()
+        _check(lib().giamg_level_prolong(self._h, l, _ptr(ec), _ptr(xo)))
+        return xo
+
+    def coarse_solve(self, r):
+        r = self._in(r)
+        x = self._vec(self.level_info(self.num_levels - 1)["n"])
+        _check(lib().giamg_coarse_solve(self._h, _ptr(r), _ptr(x)))
+        return x

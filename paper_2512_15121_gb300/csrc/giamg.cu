@@ -1,0 +1,902 @@
+// giamg.cu -- the C ABI (include/giamg.h): hierarchy setup, the V-cycle of Algorithm 1 and
+// the PCG / flexible CG loop of Sec. 2, orchestrated on the host with every step running in
+// the library's own kernels on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace giamg {
+
+static thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
+
+void set_error(int code, const std::string& msg) {
+  (void)code;
+  g_last_error = msg;
+}
+
+Hierarchy::~Hierarchy() {
+  for (Level* L : lev) delete L;
+  lev.clear();
+  if (h_sc) cudaFreeHost(h_sc);
+  for (cudaEvent_t e : prof.ev) cudaEventDestroy(e);
+}
+
+namespace {
+
+int next_order(int p) {
+  if (p <= 1) return 1;
+  if (p % 2 == 0) return p / 2;
+  for (int d = p / 2; d >= 1; --d)
+    if (p % d == 0) return d;
+  return 1;
+}
+
+// ------------------------------------------------------------------ profiling
+int prof_begin(Hierarchy& H, int cat) {
+  if (!H.prof.on) return -1;
+  Prof& P = H.prof;
+  if (P.used + 2 > P.ev.size()) {
+    for (int k = 0; k < 256; ++k) {
+      cudaEvent_t e;
+      GIAMG_CUDA(cudaEventCreate(&e));
+      P.ev.push_back(e);
+    }
+  }
+  const int e0 = (int)P.used++;
+  const int e1 = (int)P.used++;
+  GIAMG_CUDA(cudaEventRecord(P.ev[e0], H.stream));
+  P.recs.push_back({cat, e0, e1, 0.0});
+  return (int)P.recs.size() - 1;
+}
+void prof_end(Hierarchy& H, int rec, double bytes) {
+  if (rec < 0) return;
+  Prof::Rec& R = H.prof.recs[rec];
+  R.bytes = bytes;
+  GIAMG_CUDA(cudaEventRecord(H.prof.ev[R.e1], H.stream));
+}
+// algorithmic bytes of one CSR row-kernel launch: matrix (values, columns, row pointers), the
+// gathered vector counted once, the output, and `vecs` further streamed vectors
+double row_bytes(const DCSR& A, int vsize, int vecs) {
+  return (double)A.nnz * (vsize + 4) + 8.0 * (A.n + 1) + (double)vsize * A.n * (2 + vecs);
+}
+
+// copy count elements of a caller array (host or device) into a new device buffer
+template <typename T>
+void upload(DBuf<T>& dst, const T* src, size_t count, bool dev, cudaStream_t s) {
+  dst.alloc(std::max<size_t>(count, 1), s);
+  if (count)
+    GIAMG_CUDA(cudaMemcpyAsync(dst.get(), src, count * sizeof(T), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+// Chebyshev coefficients of Saad's Algorithm 12.1 with the Jacobi preconditioner:
+// step 0 uses c2 = 1/theta (and no previous direction), step s >= 1 uses
+// c1 = rho_s rho_{s-1}, c2 = 2 rho_s / delta with rho_s = 1 / (2 sigma - rho_{s-1}).
+struct Cheb {
+  std::vector<double> c1, c2;
+};
+Cheb cheb_coeffs(double rho_hat, double lo, double hi, int k) {
+  Cheb c;
+  const double a = lo * rho_hat, b = hi * rho_hat;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  c.c1.push_back(0.0);
+  c.c2.push_back(1.0 / theta);
+  for (int s = 1; s < k; ++s) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c.c1.push_back(rn * rho);
+    c.c2.push_back(2.0 * rn / delta);
+    rho = rn;
+  }
+  return c;
+}
+
+struct LevelExtra {
+  Cheb cheb;
+};
+
+struct Ctx {
+  Hierarchy* H;
+  std::vector<LevelExtra> ex;
+};
+
+// ------------------------------------------------------------------ V-cycle (Algorithm 1)
+const double* vcycle64(Hierarchy& H, const std::vector<LevelExtra>& ex, int l, const double* b) {
+  Level& L = *H.lev[l];
+  cudaStream_t s = H.stream;
+  if (L.kind == GIAMG_LEVEL_COARSEST) {  // direct solve of the coarsest matrix
+    const int pr = prof_begin(H, kProfCoarsest);
+    chol_solve(L.L.get(), L.nc, b, L.x.get(), s);
+    prof_end(H, pr, 8.0 * L.nc * L.nc + 16.0 * L.nc);
+    return L.x.get();
+  }
+  const Cheb& c = ex[l].cheb;
+  const int k = (int)c.c1.size();
+  double* x = L.x.get();
+  double* x2 = L.x2.get();
+  const int64_t n = L.A.n;
+  const int rc = l == 0 ? kProfL0Rows : kProfCoarseRows;
+  // presmooth (x enters as zero: the first step needs no product)
+  cheb_first(n, b, L.dinv.get(), c.c2[0], x, L.d.get(), s);
+  for (int j = 1; j < k; ++j) {
+    const int pr = prof_begin(H, rc);
+    cheb_step(L.A, b, x, x2, L.d.get(), L.dinv.get(), c.c1[j], c.c2[j], s, L.avg_row);
+    prof_end(H, pr, row_bytes(L.A, 8, 4));
+    std::swap(x, x2);
+  }
+  // residual, restriction (p- or h-), recursion, interpolation and correction
+  int pr = prof_begin(H, rc);
+  residual(L.A, b, x, L.r.get(), s, L.avg_row);
+  prof_end(H, pr, row_bytes(L.A, 8, 1));
+  Level& C = *H.lev[l + 1];
+  pr = prof_begin(H, kProfTransfer);
+  if (L.kind == GIAMG_LEVEL_P) p_restrict(L, L.r.get(), C.b.get(), s);
+  else h_restrict(L, L.r.get(), C.b.get(), s);
+  prof_end(H, pr, 8.0 * (L.A.n + L.n_next));
+  const double* xc = vcycle64(H, ex, l + 1, C.b.get());
+  pr = prof_begin(H, kProfTransfer);
+  if (L.kind == GIAMG_LEVEL_P) p_prolong(L, xc, x, s);
+  else h_prolong(L, xc, x, s);
+  prof_end(H, pr, 8.0 * (2 * L.A.n + L.n_next));
+  // postsmooth with the same polynomial
+  for (int j = 0; j < k; ++j) {
+    const int pq = prof_begin(H, rc);
+    cheb_step(L.A, b, x, x2, L.d.get(), L.dinv.get(), c.c1[j], c.c2[j], s, L.avg_row);
+    prof_end(H, pq, row_bytes(L.A, 8, j == 0 ? 3 : 4));
+    std::swap(x, x2);
+  }
+  return x;
+}
+
+const float* vcycle32(Hierarchy& H, const std::vector<LevelExtra>& ex, int l, const float* b) {
+  Level& L = *H.lev[l];
+  cudaStream_t s = H.stream;
+  if (L.kind == GIAMG_LEVEL_COARSEST) {
+    const int pr = prof_begin(H, kProfCoarsest);
+    chol_solve32(L.L.get(), L.nc, b, L.x32.get(), s);
+    prof_end(H, pr, 8.0 * L.nc * L.nc + 8.0 * L.nc);
+    return L.x32.get();
+  }
+  const Cheb& c = ex[l].cheb;
+  const int k = (int)c.c1.size();
+  float* x = L.x32.get();
+  float* x2 = L.x232.get();
+  const int64_t n = L.A.n;
+  const int rc = l == 0 ? kProfL0Rows : kProfCoarseRows;
+  cheb_first32(n, b, L.dinv32.get(), (float)c.c2[0], x, L.d32.get(), s);
+  for (int j = 1; j < k; ++j) {
+    const int pr = prof_begin(H, rc);
+    cheb_step32(L.A, b, x, x2, L.d32.get(), L.dinv32.get(), (float)c.c1[j], (float)c.c2[j], s, L.avg_row);
+    prof_end(H, pr, row_bytes(L.A, 4, 4));
+    std::swap(x, x2);
+  }
+  int pr = prof_begin(H, rc);
+  residual32(L.A, b, x, L.r32.get(), s, L.avg_row);
+  prof_end(H, pr, row_bytes(L.A, 4, 1));
+  Level& C = *H.lev[l + 1];
+  pr = prof_begin(H, kProfTransfer);
+  if (L.kind == GIAMG_LEVEL_P) p_restrict32(L, L.r32.get(), C.b32.get(), s);
+  else h_restrict32(L, L.r32.get(), C.b32.get(), s);
+  prof_end(H, pr, 4.0 * (L.A.n + L.n_next));
+  const float* xc = vcycle32(H, ex, l + 1, C.b32.get());
+  pr = prof_begin(H, kProfTransfer);
+  if (L.kind == GIAMG_LEVEL_P) p_prolong32(L, xc, x, s);
+  else h_prolong32(L, xc, x, s);
+  prof_end(H, pr, 4.0 * (2 * L.A.n + L.n_next));
+  for (int j = 0; j < k; ++j) {
+    const int pq = prof_begin(H, rc);
+    cheb_step32(L.A, b, x, x2, L.d32.get(), L.dinv32.get(), (float)c.c1[j], (float)c.c2[j], s, L.avg_row);
+    prof_end(H, pq, row_bytes(L.A, 4, j == 0 ? 3 : 4));
+    std::swap(x, x2);
+  }
+  return x;
+}
+
+// z = V(r) from the finest level; returns the device buffer holding z
+const double* apply_vcycle(Ctx& C, int precision, const double* r) {
+  Hierarchy& H = *C.H;
+  Level& L0 = *H.lev[0];
+  if (precision == 0) return vcycle64(H, C.ex, 0, r);
+  vec_to32(L0.A.n, r, L0.b32.get(), H.stream);
+  const float* z32 = vcycle32(H, C.ex, 0, L0.b32.get());
+  vec_to64(L0.A.n, z32, H.z.get(), H.stream);
+  return H.z.get();
+}
+
+void alloc_work(Level& L, cudaStream_t s) {
+  const int64_t n = std::max<int64_t>(L.A.n, 1);
+  L.x.alloc(n, s); L.x2.alloc(n, s); L.b.alloc(n, s); L.r.alloc(n, s); L.d.alloc(n, s);
+  L.x32.alloc(n, s); L.x232.alloc(n, s); L.b32.alloc(n, s); L.r32.alloc(n, s); L.d32.alloc(n, s);
+  L.x.zero(s); L.x2.zero(s); L.b.zero(s); L.r.zero(s); L.d.zero(s);
+  L.x32.zero(s); L.x232.zero(s); L.b32.zero(s); L.r32.zero(s); L.d32.zero(s);
+}
+
+// Galerkin coarse operator A_c = R (A P), R = P^T (Sec. 2)
+void galerkin(Level& F, DCSR& Ac, bool keep_R, cudaStream_t s) {
+  DCSR R, AP;
+  csr_transpose(F.P, R, s);
+  spgemm(F.A, F.P, AP, s);
+  spgemm(R, AP, Ac, s);
+  if (keep_R) {
+    F.R = std::move(R);
+    csr_to32(F.R, s);
+  }
+}
+
+void check_coords(const double* coords_h, const std::vector<int32_t>& l2g, int32_t n_elem, int p, int64_t n) {
+  // nodes must be the trilinear image of the GLL tensor points of each element
+  const int n1 = p + 1, nl = n1 * n1 * n1;
+  std::vector<double> xi(n1);
+  xi[0] = -1.0;
+  xi[p] = 1.0;
+  for (int j = 1; j <= p / 2; ++j) {  // Newton on P_{p-1} - x P_p (the GLL interior nodes)
+    double t = -std::cos(M_PI * j / p);
+    for (int it = 0; it < 100; ++it) {
+      double pm = 1.0, pc = t;
+      for (int k = 1; k < p; ++k) {
+        const double pn = ((2.0 * k + 1.0) * t * pc - k * pm) / (k + 1.0);
+        pm = pc;
+        pc = pn;
+      }
+      const double dt = (pm - t * pc) / (-(p + 1.0) * pc);
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    xi[j] = t;
+    xi[p - j] = -t;
+  }
+  if (p % 2 == 0) xi[p / 2] = 0.0;
+  for (int32_t e = 0; e < n_elem; ++e) {
+    const int32_t* m = &l2g[(size_t)e * nl];
+    double v[8][3];
+    double h = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      const int i = (c >> 2) & 1, j = (c >> 1) & 1, k = c & 1;
+      const int32_t g = m[(i * p) * n1 * n1 + (j * p) * n1 + k * p];
+      GIAMG_CHECK(g >= 0 && g < n, GIAMG_ERR_MAP, "element map entry out of range");
+      for (int d = 0; d < 3; ++d) v[c][d] = coords_h[3 * (int64_t)g + d];
+    }
+    for (int d = 0; d < 3; ++d) h = std::max(h, std::fabs(v[7][d] - v[0][d]));
+    for (int a = 0; a < nl; ++a) {
+      const int i = a / (n1 * n1), j = (a / n1) % n1, k = a % n1;
+      const double s = xi[i], t = xi[j], u = xi[k];
+      for (int d = 0; d < 3; ++d) {
+        double x = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          const int ci = (c >> 2) & 1, cj = (c >> 1) & 1, ck = c & 1;
+          const double w = (ci ? 1 + s : 1 - s) * (cj ? 1 + t : 1 - t) * (ck ? 1 + u : 1 - u) / 8.0;
+          x += w * v[c][d];
+        }
+        GIAMG_CHECK(std::fabs(x - coords_h[3 * (int64_t)m[a] + d]) <= 1e-8 * std::max(h, 1e-300), GIAMG_ERR_MAP,
+                    "coordinates are not the trilinear image of the GLL points of element " + std::to_string(e));
+      }
+    }
+  }
+}
+
+__global__ void csr_check_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 unsigned long long* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = rp[i], e = rp[i + 1];
+    if (e < s) {
+      atomicAdd(bad, 1ull);
+      continue;
+    }
+    for (int64_t t = s; t < e; ++t) {
+      const int32_t c = ci[t];
+      if (c < 0 || c >= n || (t > s && ci[t - 1] >= c)) atomicAdd(bad, 1ull);
+    }
+  }
+}
+
+Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int32_t n_elem,
+                const int32_t* elem_dof, const int32_t* elem_order, const double* coords, const giamg_options* optp,
+                void* stream) {
+  giamg_options opt;
+  if (optp) opt = *optp;
+  else giamg_default_options(&opt);
+  GIAMG_CHECK(n > 0 && n < ((int64_t)1 << 31), GIAMG_ERR_ARG, "n must be in [1, 2^31)");
+  GIAMG_CHECK(row_ptr && col_idx && val, GIAMG_ERR_ARG, "row_ptr, col_idx and val are required");
+  GIAMG_CHECK(opt.cheb_degree >= 1 && opt.cheb_degree <= 64, GIAMG_ERR_ARG, "cheb_degree must be in [1, 64]");
+  GIAMG_CHECK(opt.cheb_lo > 0 && opt.cheb_hi > opt.cheb_lo, GIAMG_ERR_ARG, "need 0 < cheb_lo < cheb_hi");
+  GIAMG_CHECK(opt.max_levels >= 1 && opt.max_levels <= 64, GIAMG_ERR_ARG, "max_levels must be in [1, 64]");
+  GIAMG_CHECK(opt.lanczos_steps >= 1, GIAMG_ERR_ARG, "lanczos_steps must be >= 1");
+  GIAMG_CHECK(opt.precision == 0 || opt.precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+  const bool dev = opt.device_ptrs != 0;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // element orders: uniform p
+  int p = 1;
+  if (n_elem > 0) {
+    GIAMG_CHECK(elem_order != nullptr, GIAMG_ERR_ARG, "elem_order is required when n_elem > 0");
+    std::vector<int32_t> ord(n_elem);
+    if (dev) GIAMG_CUDA(cudaMemcpy(ord.data(), elem_order, sizeof(int32_t) * n_elem, cudaMemcpyDeviceToHost));
+    else std::memcpy(ord.data(), elem_order, sizeof(int32_t) * n_elem);
+    p = ord[0];
+    for (int32_t e = 0; e < n_elem; ++e)
+      GIAMG_CHECK(ord[e] == p, GIAMG_ERR_ORDER, "element orders are not uniform");
+    GIAMG_CHECK(p >= 1 && p <= GIAMG_MAX_ORDER, GIAMG_ERR_ORDER, "element order outside 1..12");
+    GIAMG_CHECK(p == 1 || elem_dof != nullptr, GIAMG_ERR_MAP, "elem_dof is required for p > 1");
+  } else {
+    GIAMG_CHECK(elem_dof == nullptr || n_elem == 0, GIAMG_ERR_ARG, "n_elem must be positive with elem_dof");
+  }
+  int64_t nnz = 0;
+  if (dev) GIAMG_CUDA(cudaMemcpy(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  else nnz = row_ptr[n];
+  GIAMG_CHECK(nnz >= n, GIAMG_ERR_ARG, "row_ptr[n] smaller than n (a diagonal is needed in every row)");
+
+  Ctx* C = new Ctx();
+  C->H = new Hierarchy();
+  Hierarchy& H = *C->H;
+  try {
+    H.opt = opt;
+    H.stream = s;
+    GIAMG_CUDA(cudaGetDevice(&H.device));
+    H.n = n;
+    Level* L0 = new Level();
+    H.lev.push_back(L0);
+    L0->order = p;
+    L0->A.n = n;
+    L0->A.m = n;
+    L0->A.nnz = nnz;
+    upload(L0->A.rp, row_ptr, (size_t)n + 1, dev, s);
+    upload(L0->A.ci, col_idx, (size_t)nnz, dev, s);
+    upload(L0->A.v, val, (size_t)nnz, dev, s);
+    {
+      DBuf<unsigned long long> bad;
+      bad.alloc(1, s);
+      bad.zero(s);
+      { csr_check_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(n, L0->A.rp.get(),
+                                                                                            L0->A.ci.get(), bad.get()); note_launch(); }
+      GIAMG_CUDA(cudaGetLastError());
+      unsigned long long hb = 0;
+      GIAMG_CUDA(cudaMemcpyAsync(&hb, bad.get(), sizeof(hb), cudaMemcpyDeviceToHost, s));
+      GIAMG_CUDA(cudaStreamSynchronize(s));
+      GIAMG_CHECK(hb == 0, GIAMG_ERR_ARG, "CSR invalid: row pointers decrease, or columns out of range / not ascending");
+    }
+    L0->avg_row = (double)nnz / n;
+    const int nl0 = (p + 1) * (p + 1) * (p + 1);
+    if (p > 1) {
+      upload(L0->l2g, elem_dof, (size_t)n_elem * nl0, dev, s);
+      const int64_t bad = validate_map(L0->A, L0->l2g.get(), n_elem, nl0, s);
+      GIAMG_CHECK(bad == 0, GIAMG_ERR_MAP,
+                  "element map inconsistent with A: " + std::to_string(bad) + " entries out of range or missing from the pattern");
+      L0->n_elem = n_elem;
+    }
+    if (coords && p >= 1 && n_elem > 0 && elem_dof) {
+      std::vector<double> ch((size_t)n * 3);
+      std::vector<int32_t> mh((size_t)n_elem * nl0);
+      GIAMG_CUDA(cudaMemcpy(ch.data(), coords, sizeof(double) * 3 * n, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      GIAMG_CUDA(cudaMemcpy(mh.data(), elem_dof, sizeof(int32_t) * mh.size(), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      check_coords(ch.data(), mh, n_elem, p, n);
+    }
+    L0->dinv.alloc(n, s);
+    L0->dinv32.alloc(n, s);
+    GIAMG_CHECK(diag_inverse(L0->A, L0->dinv.get(), L0->dinv32.get(), s), GIAMG_ERR_NOT_SPD,
+                "A has a non-positive or missing diagonal entry");
+
+    // p-coarsening (Algorithms 2-4, 7) down to order 1
+    while (H.lev.back()->order > 1 && (int)H.lev.size() < opt.max_levels) {
+      Level& F = *H.lev.back();
+      Level* Cl = new Level();
+      F.p = F.order;
+      F.q = next_order(F.order);
+      F.n_elem = n_elem;
+      p_level_build(F, *Cl, s);
+      Cl->order = F.q;
+      galerkin(F, Cl->A, false, s);
+      F.kind = GIAMG_LEVEL_P;
+      Cl->avg_row = Cl->A.n ? (double)Cl->A.nnz / Cl->A.n : 0.0;
+      Cl->dinv.alloc(std::max<int64_t>(Cl->A.n, 1), s);
+      Cl->dinv32.alloc(std::max<int64_t>(Cl->A.n, 1), s);
+      GIAMG_CHECK(diag_inverse(Cl->A, Cl->dinv.get(), Cl->dinv32.get(), s), GIAMG_ERR_NOT_SPD,
+                  "coarse operator has a non-positive diagonal entry");
+      H.lev.push_back(Cl);
+    }
+    // h-coarsening by smoothed aggregation (Sec. 2.5)
+    while (H.lev.back()->A.n > opt.coarse_max && (int)H.lev.size() < opt.max_levels) {
+      Level& F = *H.lev.back();
+      const int64_t n_agg = h_level_aggregate(F, opt.strength_theta, opt.hash_kind, s);
+      if ((double)n_agg > 0.9 * (double)F.A.n) {
+        F.agg.release();
+        F.n_next = 0;
+        break;
+      }
+      h_level_prolongation(F, s);
+      Level* Cl = new Level();
+      galerkin(F, Cl->A, true, s);
+      F.kind = GIAMG_LEVEL_H;
+      Cl->order = 0;
+      Cl->avg_row = Cl->A.n ? (double)Cl->A.nnz / Cl->A.n : 0.0;
+      Cl->dinv.alloc(std::max<int64_t>(Cl->A.n, 1), s);
+      Cl->dinv32.alloc(std::max<int64_t>(Cl->A.n, 1), s);
+      GIAMG_CHECK(diag_inverse(Cl->A, Cl->dinv.get(), Cl->dinv32.get(), s), GIAMG_ERR_NOT_SPD,
+                  "coarse operator has a non-positive diagonal entry");
+      H.lev.push_back(Cl);
+    }
+    // coarsest level: dense Cholesky
+    Level& Lc = *H.lev.back();
+    Lc.kind = GIAMG_LEVEL_COARSEST;
+    Lc.nc = Lc.A.n;
+    GIAMG_CHECK(Lc.nc <= 8192, GIAMG_ERR_ARG,
+                "coarsest level has " + std::to_string(Lc.nc) + " rows (> 8192); aggregation stalled");
+    Lc.L.alloc((size_t)Lc.nc * Lc.nc, s);
+    csr_to_dense_cm(Lc.A, Lc.L.get(), s);
+    GIAMG_CHECK(cholesky_factor(Lc.L.get(), Lc.nc, s) == GIAMG_OK, GIAMG_ERR_NOT_SPD,
+                "coarsest matrix is not positive definite");
+    // smoother bounds, FP32 copies, work vectors
+    C->ex.resize(H.lev.size());
+    for (size_t l = 0; l < H.lev.size(); ++l) {
+      Level& L = *H.lev[l];
+      csr_to32(L.A, s);
+      alloc_work(L, s);
+      if (L.kind != GIAMG_LEVEL_COARSEST) {
+        L.rho = lanczos_rho(L.A, opt.lanczos_steps, opt.hash_kind, H);
+        GIAMG_CHECK(L.rho > 0.0 && std::isfinite(L.rho), GIAMG_ERR_NOT_SPD, "Lanczos bound is not positive");
+        C->ex[l].cheb = cheb_coeffs(L.rho, opt.cheb_lo, opt.cheb_hi, opt.cheb_degree);
+      }
+    }
+    // PCG work
+    H.r.alloc(n, s); H.z.alloc(n, s); H.p.alloc(n, s); H.q.alloc(n, s);
+    H.xw.alloc(n, s); H.rold.alloc(n, s); H.tmp.alloc(n, s);
+    H.partial.alloc(2 * kRedBlocks, s);
+    H.sc.alloc(1, s);
+    H.sc.zero(s);
+    GIAMG_CUDA(cudaMallocHost((void**)&H.h_sc, sizeof(Scalars)));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete C->H;
+    delete C;
+    throw;
+  }
+  return C;
+}
+
+// staging of caller vectors in host mode
+struct InVec {
+  const double* d = nullptr;
+  DBuf<double> buf;
+  InVec(const double* p, int64_t n, bool dev, cudaStream_t s) {
+    if (dev) d = p;
+    else {
+      buf.alloc(std::max<int64_t>(n, 1), s);
+      GIAMG_CUDA(cudaMemcpyAsync(buf.get(), p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      d = buf.get();
+    }
+  }
+};
+struct OutVec {
+  double* d = nullptr;
+  double* host = nullptr;
+  int64_t n;
+  cudaStream_t s;
+  DBuf<double> buf;
+  OutVec(double* p, int64_t n_, bool dev, cudaStream_t s_, bool load) : n(n_), s(s_) {
+    if (dev) d = p;
+    else {
+      host = p;
+      buf.alloc(std::max<int64_t>(n, 1), s);
+      d = buf.get();
+      if (load) GIAMG_CUDA(cudaMemcpyAsync(d, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    }
+  }
+  void finish() {
+    if (host) GIAMG_CUDA(cudaMemcpyAsync(host, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+  }
+};
+
+int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, double* x_out, double rtol, int* iters,
+               double* relres) {
+  Hierarchy& H = *C.H;
+  cudaStream_t s = H.stream;
+  const int64_t n = H.n;
+  const bool dev = H.opt.device_ptrs != 0;
+  GIAMG_CHECK(b_in && x_out, GIAMG_ERR_ARG, "b and x are required");
+  GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+  GIAMG_CHECK(rtol >= 0.0, GIAMG_ERR_ARG, "rtol must be non-negative");
+  InVec b(b_in, n, dev, s);
+  OutVec x(x_out, n, dev, s, false);
+  Level& L0 = *H.lev[0];
+  const int flexible = precision ? 1 : 0;
+  double* partial = H.partial.get();
+  Scalars* sc = H.sc.get();
+  H.hist.clear();
+  pcg_init(n, b.d, x.d, H.r.get(), partial, s);
+  pcg_finish_bb(sc, partial, s);
+  GIAMG_CUDA(cudaMemcpyAsync(H.h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  const double bb = H.h_sc->bb;
+  int it = 0;
+  double rr = 1.0;
+  int status = GIAMG_OK;
+  if (bb == 0.0) {
+    H.hist.push_back(0.0);
+    rr = 0.0;
+  } else {
+    H.hist.push_back(1.0);
+    const double* z = apply_vcycle(C, precision, H.r.get());
+    pcg_dot_rz(n, H.r.get(), z, H.rold.get(), flexible, partial, s);
+    pcg_finish_rz(sc, partial, 1, flexible, s);
+    pcg_update_p(n, z, H.p.get(), sc, 1, s);
+    const int limit = force_iters > 0 ? force_iters : H.opt.max_iter;
+    while (it < limit) {
+      const int pr = prof_begin(H, kProfOuterSpmv);
+      spmv(L0.A, H.p.get(), H.q.get(), s, L0.avg_row);
+      prof_end(H, pr, row_bytes(L0.A, 8, 0));
+      dot_partial(n, H.p.get(), H.q.get(), partial, s);
+      pcg_finish_pq(sc, partial, s);
+      pcg_update_xr(n, H.p.get(), H.q.get(), x.d, H.r.get(), H.rold.get(), flexible, sc, partial, s);
+      pcg_finish_rr(sc, partial, s);
+      GIAMG_CUDA(cudaMemcpyAsync(H.h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+      GIAMG_CUDA(cudaStreamSynchronize(s));
+      ++it;
+      if (H.h_sc->status != 0) {
+        status = GIAMG_ERR_BREAKDOWN;
+        break;
+      }
+      rr = std::sqrt(H.h_sc->rr / bb);
+      H.hist.push_back(rr);
+      if (force_iters <= 0 && rr <= rtol) break;
+      if (it == limit) break;
+      z = apply_vcycle(C, precision, H.r.get());
+      pcg_dot_rz(n, H.r.get(), z, H.rold.get(), flexible, partial, s);
+      pcg_finish_rz(sc, partial, 0, flexible, s);
+      pcg_update_p(n, z, H.p.get(), sc, 0, s);
+    }
+    if (status == GIAMG_OK && force_iters <= 0 && !(rr <= rtol)) status = GIAMG_ERR_MAXITER;
+  }
+  // keep b and x for the true residual of giamg_solve_stats
+  vec_copy(n, b.d, H.tmp.get(), s);
+  vec_copy(n, x.d, H.xw.get(), s);
+  x.finish();
+  H.last_iters = it;
+  H.last_true_relres = -1.0;
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  if (status == GIAMG_ERR_BREAKDOWN) throw Error{status, "CG breakdown (p^T A p <= 0, r^T z <= 0 or NaN)"};
+  if (status == GIAMG_ERR_MAXITER) throw Error{status, "max_iter reached before rtol"};
+  return GIAMG_OK;
+}
+
+Ctx* ctx_of(giamg_handle h) {
+  GIAMG_CHECK(h != nullptr, GIAMG_ERR_ARG, "NULL handle");
+  return reinterpret_cast<Ctx*>(h);
+}
+Level& level_of(Ctx& C, int l) {
+  GIAMG_CHECK(l >= 0 && l < (int)C.H->lev.size(), GIAMG_ERR_ARG, "level index out of range");
+  return *C.H->lev[l];
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const Error& e) {
+    set_error(e.code, e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error(GIAMG_ERR_OOM, "host allocation failed");
+    return GIAMG_ERR_OOM;
+  } catch (...) {
+    set_error(GIAMG_ERR_ARG, "unexpected error");
+    return GIAMG_ERR_ARG;
+  }
+}
+
+template <typename T>
+void copy_out(T* dst, const T* src, size_t count, bool dev, cudaStream_t s) {
+  if (!dst || count == 0) return;
+  GIAMG_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+}  // namespace
+}  // namespace giamg
+
+using namespace giamg;
+
+extern "C" {
+
+void giamg_default_options(giamg_options* o) {
+  if (!o) return;
+  o->cheb_degree = 3;
+  o->cheb_lo = 0.1;
+  o->cheb_hi = 1.1;
+  o->lanczos_steps = 20;
+  o->coarse_max = 500;
+  o->max_levels = 16;
+  o->strength_theta = 0.0;
+  o->precision = 0;
+  o->max_iter = 1000;
+  o->force_iters = 0;
+  o->device_ptrs = 0;
+  o->hash_kind = 0;
+}
+
+int giamg_setup(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int32_t n_elem,
+                const int32_t* elem_dof, const int32_t* elem_order, const double* coords, const giamg_options* opt,
+                void* cuda_stream, giamg_handle* out) {
+  return guarded([&] {
+    GIAMG_CHECK(out != nullptr, GIAMG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    Ctx* C = setup_impl(n, row_ptr, col_idx, val, n_elem, elem_dof, elem_order, coords, opt, cuda_stream);
+    *out = reinterpret_cast<giamg_handle>(C);
+    return GIAMG_OK;
+  });
+}
+
+int giamg_solve(giamg_handle h, const double* b, double* x, double rtol, int* iters, double* relres) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    return solve_impl(C, C.H->opt.precision, C.H->opt.force_iters, b, x, rtol, iters, relres);
+  });
+}
+
+int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double* b, double* x, double rtol, int* iters,
+                   double* relres) {
+  return guarded([&] { return solve_impl(*ctx_of(h), precision, force_iters, b, x, rtol, iters, relres); });
+}
+
+int giamg_solve_stats(giamg_handle h, double* hist, int len, double* true_relres) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Hierarchy& H = *C.H;
+    if (hist)
+      for (int i = 0; i < len && i < (int)H.hist.size(); ++i) hist[i] = H.hist[i];
+    if (true_relres) {
+      cudaStream_t s = H.stream;
+      Level& L0 = *H.lev[0];
+      residual(L0.A, H.tmp.get(), H.xw.get(), H.q.get(), s, L0.avg_row);
+      DBuf<double> out;
+      out.alloc(2, s);
+      dot_partial(H.n, H.q.get(), H.q.get(), H.partial.get(), s);
+      reduce_to(H.partial.get(), out.get(), s);
+      dot_partial(H.n, H.tmp.get(), H.tmp.get(), H.partial.get(), s);
+      reduce_to(H.partial.get(), out.get() + 1, s);
+      double hv[2];
+      GIAMG_CUDA(cudaMemcpyAsync(hv, out.get(), sizeof(hv), cudaMemcpyDeviceToHost, s));
+      GIAMG_CUDA(cudaStreamSynchronize(s));
+      *true_relres = hv[1] > 0 ? std::sqrt(hv[0] / hv[1]) : 0.0;
+    }
+    return GIAMG_OK;
+  });
+}
+
+int giamg_num_levels(giamg_handle h, int* n_levels) {
+  return guarded([&] {
+    GIAMG_CHECK(n_levels, GIAMG_ERR_ARG, "n_levels is NULL");
+    *n_levels = (int)ctx_of(h)->H->lev.size();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_info(giamg_handle h, int level, int* kind, int64_t* n, int64_t* nnz, int* order, int64_t* p_nnz,
+                     int64_t* n_next) {
+  return guarded([&] {
+    Level& L = level_of(*ctx_of(h), level);
+    if (kind) *kind = L.kind;
+    if (n) *n = L.A.n;
+    if (nnz) *nnz = L.A.nnz;
+    if (order) *order = L.order;
+    if (p_nnz) *p_nnz = L.kind == GIAMG_LEVEL_COARSEST ? 0 : L.P.nnz;
+    if (n_next) *n_next = L.kind == GIAMG_LEVEL_COARSEST ? 0 : L.n_next;
+    return GIAMG_OK;
+  });
+}
+
+int giamg_export_level(giamg_handle h, int level, int64_t* row_ptr, int32_t* col_idx, double* val, int32_t* aggregates) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    const bool dev = C.H->opt.device_ptrs != 0;
+    cudaStream_t s = C.H->stream;
+    copy_out(row_ptr, L.A.rp.get(), (size_t)L.A.n + 1, dev, s);
+    copy_out(col_idx, L.A.ci.get(), (size_t)L.A.nnz, dev, s);
+    copy_out(val, L.A.v.get(), (size_t)L.A.nnz, dev, s);
+    if (aggregates && L.kind == GIAMG_LEVEL_H) copy_out(aggregates, L.agg.get(), (size_t)L.A.n, dev, s);
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    return GIAMG_OK;
+  });
+}
+
+int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_ptr, int32_t* col_idx, double* val) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level has no prolongation");
+    const bool dev = C.H->opt.device_ptrs != 0;
+    cudaStream_t s = C.H->stream;
+    copy_out(row_ptr, L.P.rp.get(), (size_t)L.P.n + 1, dev, s);
+    copy_out(col_idx, L.P.ci.get(), (size_t)L.P.nnz, dev, s);
+    copy_out(val, L.P.v.get(), (size_t)L.P.nnz, dev, s);
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_rho(giamg_handle h, int level, double* rho_hat) {
+  return guarded([&] {
+    GIAMG_CHECK(rho_hat, GIAMG_ERR_ARG, "rho_hat is NULL");
+    *rho_hat = level_of(*ctx_of(h), level).rho;
+    return GIAMG_OK;
+  });
+}
+
+int giamg_apply_vcycle(giamg_handle h, int precision, const double* r, double* z) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Hierarchy& H = *C.H;
+    GIAMG_CHECK(r && z, GIAMG_ERR_ARG, "r and z are required");
+    GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+    const bool dev = H.opt.device_ptrs != 0;
+    InVec ri(r, H.n, dev, H.stream);
+    OutVec zo(z, H.n, dev, H.stream, false);
+    const double* zz = apply_vcycle(C, precision, ri.d);
+    vec_copy(H.n, zz, zo.d, H.stream);
+    zo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_spmv(giamg_handle h, int level, const double* x, double* y) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(x && y, GIAMG_ERR_ARG, "x and y are required");
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVec xi(x, L.A.n, dev, C.H->stream);
+    OutVec yo(y, L.A.n, dev, C.H->stream, false);
+    spmv(L.A, xi.d, yo.d, C.H->stream, L.avg_row);
+    yo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_smooth(giamg_handle h, int level, const double* b, double* x, int x_is_zero) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level is solved, not smoothed");
+    GIAMG_CHECK(b && x, GIAMG_ERR_ARG, "b and x are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVec bi(b, L.A.n, dev, s);
+    OutVec xo(x, L.A.n, dev, s, !x_is_zero);
+    const Cheb& c = C.ex[level].cheb;
+    double* xa = L.x.get();
+    double* xb = L.x2.get();
+    int j0 = 0;
+    if (x_is_zero) {
+      cheb_first(L.A.n, bi.d, L.dinv.get(), c.c2[0], xa, L.d.get(), s);
+      j0 = 1;
+    } else {
+      vec_copy(L.A.n, xo.d, xa, s);
+    }
+    for (int j = j0; j < (int)c.c1.size(); ++j) {
+      cheb_step(L.A, bi.d, xa, xb, L.d.get(), L.dinv.get(), c.c1[j], c.c2[j], s, L.avg_row);
+      std::swap(xa, xb);
+    }
+    vec_copy(L.A.n, xa, xo.d, s);
+    xo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_restrict(giamg_handle h, int level, const double* r_f, double* r_c) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level has no restriction");
+    GIAMG_CHECK(r_f && r_c, GIAMG_ERR_ARG, "r_f and r_c are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVec ri(r_f, L.A.n, dev, s);
+    OutVec ro(r_c, L.n_next, dev, s, false);
+    if (L.kind == GIAMG_LEVEL_P) p_restrict(L, ri.d, ro.d, s);
+    else h_restrict(L, ri.d, ro.d, s);
+    ro.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_prolong(giamg_handle h, int level, const double* e_c, double* x_f) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level has no prolongation");
+    GIAMG_CHECK(e_c && x_f, GIAMG_ERR_ARG, "e_c and x_f are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVec ei(e_c, L.n_next, dev, s);
+    OutVec xo(x_f, L.A.n, dev, s, true);
+    if (L.kind == GIAMG_LEVEL_P) p_prolong(L, ei.d, xo.d, s);
+    else h_prolong(L, ei.d, xo.d, s);
+    xo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_coarse_solve(giamg_handle h, const double* r, double* x) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = *C.H->lev.back();
+    GIAMG_CHECK(r && x, GIAMG_ERR_ARG, "r and x are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVec ri(r, L.nc, dev, s);
+    OutVec xo(x, L.nc, dev, s, false);
+    chol_solve(L.L.get(), L.nc, ri.d, xo.d, s);
+    xo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_free(giamg_handle h) {
+  if (!h) return GIAMG_OK;
+  return guarded([&] {
+    Ctx* C = reinterpret_cast<Ctx*>(h);
+    cudaStream_t s = C->H->stream;
+    delete C->H;
+    delete C;
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    return GIAMG_OK;
+  });
+}
+
+const char* giamg_last_error(void) { return g_last_error.c_str(); }
+
+int giamg_set_device_ptrs(giamg_handle h, int device_ptrs) {
+  return guarded([&] {
+    GIAMG_CHECK(device_ptrs == 0 || device_ptrs == 1, GIAMG_ERR_ARG, "device_ptrs must be 0 or 1");
+    ctx_of(h)->H->opt.device_ptrs = device_ptrs;
+    return GIAMG_OK;
+  });
+}
+
+int giamg_profile_enable(giamg_handle h, int enable) {
+  return guarded([&] {
+    Hierarchy& H = *ctx_of(h)->H;
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));
+    H.prof.on = enable != 0;
+    H.prof.recs.clear();
+    H.prof.used = 0;
+    return GIAMG_OK;
+  });
+}
+
+int giamg_profile_read(giamg_handle h, int category, double* total_ms, int64_t* launches, double* bytes) {
+  return guarded([&] {
+    Hierarchy& H = *ctx_of(h)->H;
+    GIAMG_CHECK(category >= 0 && category < kProfCats, GIAMG_ERR_ARG, "profile category out of range");
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));
+    double ms = 0.0, by = 0.0;
+    int64_t cnt = 0;
+    for (const Prof::Rec& R : H.prof.recs) {
+      if (R.cat != category) continue;
+      float t = 0.f;
+      GIAMG_CUDA(cudaEventElapsedTime(&t, H.prof.ev[R.e0], H.prof.ev[R.e1]));
+      ms += t;
+      by += R.bytes;
+      ++cnt;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = cnt;
+    if (bytes) *bytes = by;
+    return GIAMG_OK;
+  });
+}
+
+int giamg_launch_count(int64_t* count) {
+  if (!count) return GIAMG_ERR_ARG;
+  *count = (int64_t)g_launches.load();
+  return GIAMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// internal.cuh -- data structures and kernel launchers shared by the library's translation
+// units.  Nothing here is part of the C ABI (see include/giamg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "giamg.h"
+
+namespace giamg {
+
+// ------------------------------------------------------------------ launch counter
+extern std::atomic<long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int code;
+  std::string msg;
+};
+void set_error(int code, const std::string& msg);
+
+#define GIAMG_CUDA(call)                                                                      \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      throw ::giamg::Error{GIAMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define GIAMG_CHECK(cond, code, msg) \
+  do {                               \
+    if (!(cond)) throw ::giamg::Error{(code), (msg)}; \
+  } while (0)
+
+// ------------------------------------------------------------------ device memory
+// Owning device buffer (stream-ordered allocation on the handle's stream).
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { swap(o); }
+  DBuf& operator=(DBuf&& o) noexcept { release(); swap(o); return *this; }
+  ~DBuf() { release(); }
+  void swap(DBuf& o) { std::swap(p, o.p); std::swap(n, o.n); std::swap(s, o.s); }
+  void alloc(size_t count, cudaStream_t stream) {
+    release();
+    s = stream;
+    n = count;
+    if (count == 0) return;
+    cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      (void)cudaGetLastError();
+      throw Error{GIAMG_ERR_OOM, std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
+                                     " bytes failed: " + cudaGetErrorString(e)};
+    }
+  }
+  void zero(cudaStream_t stream) {
+    if (n) GIAMG_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  T* get() const { return p; }
+};
+
+struct DCSR {
+  int64_t n = 0, m = 0, nnz = 0;
+  DBuf<int64_t> rp;
+  DBuf<int32_t> ci;
+  DBuf<double> v;
+  DBuf<float> v32;
+};
+
+// ------------------------------------------------------------------ hierarchy
+struct Level {
+  int kind = GIAMG_LEVEL_COARSEST;
+  int order = 0;  // p of a p-level, 0 for aggregated levels
+  DCSR A;
+  double avg_row = 0.0;
+  DBuf<double> dinv;
+  DBuf<float> dinv32;
+  double rho = 0.0;  // Lanczos estimate of lambda_max(D^-1 A)
+
+  // transfer to the next level
+  DCSR P;  // assembled prolongation n x n_next (built in setup; used by h-levels and export)
+  DCSR R;  // R = P^T (h-levels)
+  int64_t n_next = 0;
+  // p-level element form
+  int p = 0, q = 0;
+  int32_t n_elem = 0;
+  DBuf<int32_t> l2g;      // [n_elem][(p+1)^3] this level's element map
+  DBuf<uint8_t> own;      // [n_elem][(p+1)^3] 1 if the element is the fine dof's first element
+  DBuf<int32_t> l2g_c;    // [n_elem][(q+1)^3] next level's element map
+  DBuf<double> p1d;       // [(p+1)][(q+1)]
+  DBuf<float> p1d32;
+  DBuf<int64_t> cinc_ptr; // coarse dof -> element slots e*(q+1)^3+b, ascending
+  DBuf<int32_t> cinc;
+  DBuf<double> part;      // [n_elem][(q+1)^3] restriction partial sums
+  DBuf<float> part32;
+  // h-level
+  DBuf<int32_t> agg;
+
+  // coarsest level
+  int64_t nc = 0;
+  DBuf<double> L;  // dense Cholesky factor, column-major lower triangle, nc x nc
+
+  // work vectors (FP64 and FP32 copies)
+  DBuf<double> x, x2, b, r, d;
+  DBuf<float> x32, x232, b32, r32, d32;
+};
+
+struct Scalars {  // PCG scalars kept on the device
+  double rho, rho_old, pq, alpha, beta, rr, bb, zr_old;
+  int status;
+  int pad;
+};
+
+// Opt-in CUDA-event timers by category (they add event records to the stream)
+enum ProfCat {
+  kProfL0Rows = 0,
+  kProfCoarseRows = 1,
+  kProfTransfer = 2,
+  kProfCoarsest = 3,
+  kProfVector = 4,
+  kProfOuterSpmv = 5,
+  kProfCats = 6
+};
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  struct Rec {
+    int cat;
+    int e0, e1;
+    double bytes;
+  };
+  std::vector<Rec> recs;
+  size_t used = 0;
+};
+
+struct Hierarchy {
+  giamg_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<Level*> lev;
+  int64_t n = 0;
+  // PCG work
+  DBuf<double> r, z, p, q, xw, rold, tmp;
+  DBuf<double> partial;  // reduction partial sums
+  DBuf<Scalars> sc;
+  Scalars* h_sc = nullptr;  // pinned host copy
+  std::vector<double> hist;
+  int last_iters = 0;
+  double last_true_relres = -1.0;
+  Prof prof;
+  ~Hierarchy();
+};
+
+// ------------------------------------------------------------------ kernels (launchers)
+// reductions: fixed-size grid, partial sums reduced in a fixed order (bitwise reproducible)
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+// SpMV family on a CSR level (FP64 and FP32 values)
+void spmv(const DCSR& A, const double* x, double* y, cudaStream_t s, double avg_row);
+void spmv32(const DCSR& A, const float* x, float* y, cudaStream_t s, double avg_row);
+// y = b - A x
+void residual(const DCSR& A, const double* b, const double* x, double* r, cudaStream_t s, double avg_row);
+void residual32(const DCSR& A, const float* b, const float* x, float* r, cudaStream_t s, double avg_row);
+// Chebyshev step: r = b - A x; d = c1 d + c2 dinv r (c1 == 0: d is not read); xo = x + d
+void cheb_step(const DCSR& A, const double* b, const double* x, double* xo, double* d, const double* dinv,
+               double c1, double c2, cudaStream_t s, double avg_row);
+void cheb_step32(const DCSR& A, const float* b, const float* x, float* xo, float* d, const float* dinv,
+                 float c1, float c2, cudaStream_t s, double avg_row);
+// first step from x = 0: d = dinv b * c2; x = d
+void cheb_first(int64_t n, const double* b, const double* dinv, double c2, double* x, double* d, cudaStream_t s);
+void cheb_first32(int64_t n, const float* b, const float* dinv, float c2, float* x, float* d, cudaStream_t s);
+
+// p-level transfers in element form
+void p_restrict(const Level& L, const double* rf, double* rc, cudaStream_t s);
+void p_prolong(const Level& L, const double* ec, double* xf, cudaStream_t s);
+void p_restrict32(const Level& L, const float* rf, float* rc, cudaStream_t s);
+void p_prolong32(const Level& L, const float* ec, float* xf, cudaStream_t s);
+// h-level transfers: rc = R rf ; xf += P ec
+void h_restrict(const Level& L, const double* rf, double* rc, cudaStream_t s);
+void h_prolong(const Level& L, const double* ec, double* xf, cudaStream_t s);
+void h_restrict32(const Level& L, const float* rf, float* rc, cudaStream_t s);
+void h_prolong32(const Level& L, const float* ec, float* xf, cudaStream_t s);
+
+// coarsest level
+int cholesky_factor(double* Lcm, int64_t nc, cudaStream_t s);  // returns GIAMG_OK or NOT_SPD
+void chol_solve(const double* Lcm, int64_t nc, const double* b, double* x, cudaStream_t s);
+void chol_solve32(const double* Lcm, int64_t nc, const float* b, float* x, cudaStream_t s);
+
+// vectors
+void dot_partial(int64_t n, const double* x, const double* y, double* partial, cudaStream_t s);
+void vec_copy(int64_t n, const double* x, double* y, cudaStream_t s);
+void vec_fill(int64_t n, double v, double* y, cudaStream_t s);
+void vec_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+void vec_to32(int64_t n, const double* x, float* y, cudaStream_t s);
+void vec_to64(int64_t n, const float* x, double* y, cudaStream_t s);
+void vec_add32(int64_t n, const float* x, float* y, cudaStream_t s);
+
+// PCG kernels working on device scalars
+void pcg_init(int64_t n, const double* b, double* x, double* r, double* partial, cudaStream_t s);
+void pcg_finish_bb(Scalars* sc, const double* partial, cudaStream_t s);
+void pcg_dot_rz(int64_t n, const double* r, const double* z, const double* rold, int flexible, double* partial,
+                cudaStream_t s);
+void pcg_finish_rz(Scalars* sc, const double* partial, int first, int flexible, cudaStream_t s);
+void pcg_update_p(int64_t n, const double* z, double* p, const Scalars* sc, int first, cudaStream_t s);
+void pcg_spmv_pq(const DCSR& A, const double* p, double* q, double* partial, cudaStream_t s, double avg_row);
+void pcg_finish_pq(Scalars* sc, const double* partial, cudaStream_t s);
+void pcg_update_xr(int64_t n, const double* p, const double* q, double* x, double* r, double* rold, int flexible,
+                   const Scalars* sc, double* partial, cudaStream_t s);
+void pcg_finish_rr(Scalars* sc, const double* partial, cudaStream_t s);
+void reduce_to(const double* partial, double* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ setup kernels
+uint32_t host_hash(int kind, int64_t i);
+// exclusive scan of int32 flags/counts into int64 offsets (out has n+1 entries)
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// stable LSD radix sort of (key, idx) pairs by key (keys < 2^key_bits)
+void radix_sort_pairs(uint32_t* keys, int64_t* idx, int64_t n, int key_bits, cudaStream_t s);
+// transpose of a CSR matrix, rows of the result in ascending order
+void csr_transpose(const DCSR& A, DCSR& T, cudaStream_t s);
+// C = A B: symbolic union, no dropping, columns ascending, entries summed in ascending inner
+// index with separately rounded products (matches a sequential Gustavson product bit for bit)
+void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
+void csr_to32(DCSR& A, cudaStream_t s);
+// diagonal inverse (checks positivity; returns false if a diagonal entry is <= 0 or missing)
+bool diag_inverse(const DCSR& A, double* dinv, float* dinv32, cudaStream_t s);
+// Lanczos estimate of lambda_max(D^-1/2 A D^-1/2)
+double lanczos_rho(const DCSR& A, int steps, int hash_kind, Hierarchy& H);
+// p-level construction: next map, owners, assembled P
+void p_level_build(Level& F, Level& C, cudaStream_t s);
+// h-level construction: MIS-2, aggregates, smoothed prolongation
+int64_t h_level_aggregate(Level& F, double theta, int hash_kind, cudaStream_t s);
+void h_level_prolongation(Level& F, cudaStream_t s);
+// validation of the element map against A's pattern; returns number of violations
+int64_t validate_map(const DCSR& A, const int32_t* l2g, int32_t n_elem, int nloc, cudaStream_t s);
+// dense copy of a small CSR into column-major storage
+void csr_to_dense_cm(const DCSR& A, double* D, cudaStream_t s);
+
+}  // namespace giamg

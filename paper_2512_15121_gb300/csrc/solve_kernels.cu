@@ -1,0 +1,621 @@
+// solve_kernels.cu -- kernels of one GIAMG-PCG iteration (Sec. 2, Algorithm 1):
+//   CSR SpMV / residual / fused Jacobi-Chebyshev step on every level,
+//   p-level restriction and prolongation as element contractions (Algorithms 2-4, 7 in
+//   element form: one 1D interpolation table applied along the three directions),
+//   h-level transfers as CSR products, the coarsest-level Cholesky solves, and the
+//   deterministic reductions and vector updates of the outer conjugate gradients.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace giamg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t work, int per_block) {
+  int64_t g = (work + per_block - 1) / per_block;
+  return (unsigned)std::max<int64_t>(g, 1);
+}
+
+// ------------------------------------------------------------------ CSR row kernels
+// TPR threads cooperate on one row; the group's partial sums are combined with shuffles.
+enum RowMode { kSpmv = 0, kResidual = 1, kCheb = 2, kAddSpmv = 3 };
+
+template <int TPR, typename V, int MODE>
+__global__ void __launch_bounds__(kThreads) csr_rows(int64_t n, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                                     const V* __restrict__ x, const V* __restrict__ b,
+                                                     V* __restrict__ y, V* __restrict__ d,
+                                                     const V* __restrict__ dinv, V c1, V c2) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = gt / TPR;
+  const int lane = threadIdx.x % TPR;
+  const bool valid = row < n;
+  V acc0 = 0, acc1 = 0;
+  if (valid) {
+    const int64_t s = rp[row], e = rp[row + 1];
+    int64_t t = s + lane;
+    for (; t + TPR < e; t += 2 * TPR) {
+      acc0 += val[t] * x[ci[t]];
+      acc1 += val[t + TPR] * x[ci[t + TPR]];
+    }
+    if (t < e) acc0 += val[t] * x[ci[t]];
+  }
+  V acc = acc0 + acc1;
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+  if (!valid || lane != 0) return;
+  if (MODE == kSpmv) {
+    y[row] = acc;
+  } else if (MODE == kAddSpmv) {
+    y[row] += acc;
+  } else if (MODE == kResidual) {
+    y[row] = b[row] - acc;
+  } else {  // Chebyshev step
+    const V r = b[row] - acc;
+    const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * r;
+    d[row] = dn;
+    y[row] = x[row] + dn;
+  }
+}
+
+template <typename V, int MODE>
+void launch_rows(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                 cudaStream_t s, double avg) {
+  const int64_t n = A.n;
+  if (n == 0) return;
+  const int64_t* rp = A.rp.get();
+  const int32_t* ci = A.ci.get();
+  if (avg >= 48) {
+    { csr_rows<32, V, MODE><<<grid_for(n * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
+  } else if (avg >= 20) {
+    { csr_rows<16, V, MODE><<<grid_for(n * 16, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
+  } else if (avg >= 8) {
+    { csr_rows<8, V, MODE><<<grid_for(n * 8, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
+  } else {
+    { csr_rows<4, V, MODE><<<grid_for(n * 4, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
+  }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ element transfers
+// Prolongation x_f += P e_c on a p-level: per element, gather the (q+1)^3 coarse values,
+// interpolate to the (p+1)^3 fine nodes by three 1D passes with the table P1D[a][b]
+// (Algorithm 7's nodal interpolation, sum-factorised), and write the fine dofs this element
+// owns (the first element containing a dof owns it, as in the assembled P).
+template <typename V>
+__global__ void p_prolong_kernel(int32_t n_elem, int p, int q, const int32_t* __restrict__ l2g,
+                                 const uint8_t* __restrict__ own, const int32_t* __restrict__ l2g_c,
+                                 const V* __restrict__ p1d, const V* __restrict__ ec, V* __restrict__ xf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int n1 = p + 1, m1 = q + 1;
+  const int nlf = n1 * n1 * n1, nlc = m1 * m1 * m1;
+  V* T = sm;                  // n1 * m1
+  V* u = T + n1 * m1;         // nlc
+  V* t1 = u + nlc;            // m1 * m1 * n1
+  V* t2 = t1 + m1 * m1 * n1;  // m1 * n1 * n1
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n1 * m1; i += nt) T[i] = p1d[i];
+  for (int b = tid; b < nlc; b += nt) u[b] = ec[l2g_c[(int64_t)e * nlc + b]];
+  __syncthreads();
+  for (int i = tid; i < m1 * m1 * n1; i += nt) {  // t1[b1][b2][a3]
+    const int a3 = i % n1, b12 = i / n1;
+    V s = 0;
+    for (int b3 = 0; b3 < m1; ++b3) s += T[a3 * m1 + b3] * u[b12 * m1 + b3];
+    t1[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < m1 * n1 * n1; i += nt) {  // t2[b1][a2][a3]
+    const int a3 = i % n1, a2 = (i / n1) % n1, b1 = i / (n1 * n1);
+    V s = 0;
+    for (int b2 = 0; b2 < m1; ++b2) s += T[a2 * m1 + b2] * t1[(b1 * m1 + b2) * n1 + a3];
+    t2[i] = s;
+  }
+  __syncthreads();
+  for (int a = tid; a < nlf; a += nt) {
+    const int64_t slot = (int64_t)e * nlf + a;
+    if (!own[slot]) continue;
+    const int a23 = a % (n1 * n1), a1 = a / (n1 * n1);
+    V s = 0;
+    for (int b1 = 0; b1 < m1; ++b1) s += T[a1 * m1 + b1] * t2[b1 * n1 * n1 + a23];
+    xf[l2g[slot]] += s;
+  }
+}
+
+// Restriction r_c = P^T r_f on a p-level, step 1: per element, the partial sums
+// part[e][b] = sum over the fine dofs a the element owns of P_e[a][b] r_f[a].
+template <typename V>
+__global__ void p_restrict_kernel(int32_t n_elem, int p, int q, const int32_t* __restrict__ l2g,
+                                  const uint8_t* __restrict__ own, const V* __restrict__ p1d,
+                                  const V* __restrict__ rf, V* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int n1 = p + 1, m1 = q + 1;
+  const int nlf = n1 * n1 * n1, nlc = m1 * m1 * m1;
+  V* T = sm;                  // n1 * m1
+  V* v = T + n1 * m1;         // nlf
+  V* t1 = v + nlf;            // n1 * n1 * m1
+  V* t2 = t1 + n1 * n1 * m1;  // n1 * m1 * m1
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n1 * m1; i += nt) T[i] = p1d[i];
+  for (int a = tid; a < nlf; a += nt) {
+    const int64_t slot = (int64_t)e * nlf + a;
+    v[a] = own[slot] ? rf[l2g[slot]] : V(0);
+  }
+  __syncthreads();
+  for (int i = tid; i < n1 * n1 * m1; i += nt) {  // t1[a1][a2][b3]
+    const int b3 = i % m1, a12 = i / m1;
+    V s = 0;
+    for (int a3 = 0; a3 < n1; ++a3) s += T[a3 * m1 + b3] * v[a12 * n1 + a3];
+    t1[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < n1 * m1 * m1; i += nt) {  // t2[a1][b2][b3]
+    const int b3 = i % m1, b2 = (i / m1) % m1, a1 = i / (m1 * m1);
+    V s = 0;
+    for (int a2 = 0; a2 < n1; ++a2) s += T[a2 * m1 + b2] * t1[(a1 * n1 + a2) * m1 + b3];
+    t2[i] = s;
+  }
+  __syncthreads();
+  for (int b = tid; b < nlc; b += nt) {
+    const int b23 = b % (m1 * m1), b1 = b / (m1 * m1);
+    V s = 0;
+    for (int a1 = 0; a1 < n1; ++a1) s += T[a1 * m1 + b1] * t2[a1 * m1 * m1 + b23];
+    part[(int64_t)e * nlc + b] = s;
+  }
+}
+
+// step 2: every coarse dof sums its element partials in ascending element order
+template <typename V>
+__global__ void p_gather_kernel(int64_t nc, const int64_t* __restrict__ ptr, const int32_t* __restrict__ slot,
+                                const V* __restrict__ part, V* __restrict__ rc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  V s = 0;
+  for (int64_t t = ptr[c]; t < ptr[c + 1]; ++t) s += part[slot[t]];
+  rc[c] = s;
+}
+
+template <typename V>
+size_t prolong_smem(int p, int q) {
+  const int n1 = p + 1, m1 = q + 1;
+  return sizeof(V) * (size_t)(n1 * m1 + m1 * m1 * m1 + m1 * m1 * n1 + m1 * n1 * n1);
+}
+template <typename V>
+size_t restrict_smem(int p, int q) {
+  const int n1 = p + 1, m1 = q + 1;
+  return sizeof(V) * (size_t)(n1 * m1 + n1 * n1 * n1 + n1 * n1 * m1 + n1 * m1 * m1);
+}
+
+// ------------------------------------------------------------------ coarsest level
+// Right-looking Cholesky, column-major: step k scales column k, then updates the trailing
+// lower triangle.  One launch pair per column; the pivot test writes a status word.
+__global__ void chol_scale_col(double* L, int64_t nc, int64_t k, int* status) {
+  __shared__ double piv;
+  if (threadIdx.x == 0) {
+    double d = L[k * nc + k];
+    if (!(d > 0.0)) {
+      *status = 1;
+      d = 1.0;
+    }
+    piv = sqrt(d);
+    L[k * nc + k] = piv;
+  }
+  __syncthreads();
+  for (int64_t i = k + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x)
+    L[k * nc + i] /= piv;
+}
+__global__ void chol_update(double* L, int64_t nc, int64_t k) {
+  // columns j > k, rows i >= j: L[i][j] -= L[i][k] L[j][k]
+  const int64_t m = nc - k - 1;
+  const int64_t total = m * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t jj = t / m, ii = t % m;
+    if (ii < jj) continue;
+    const int64_t j = k + 1 + jj, i = k + 1 + ii;
+    L[j * nc + i] -= L[k * nc + i] * L[k * nc + j];
+  }
+}
+__global__ void zero_upper(double* L, int64_t nc) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc * nc; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / nc, i = t % nc;
+    if (i < j) L[t] = 0.0;
+  }
+}
+
+// L L^T x = b by forward substitution on the columns of L and backward substitution on the
+// rows of L (one CTA; every step updates the remaining entries in parallel).
+template <typename V>
+__global__ void chol_solve_kernel(const double* __restrict__ L, int64_t nc, const V* __restrict__ b, V* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* y = reinterpret_cast<double*>(smem_raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t i = tid; i < nc; i += nt) y[i] = (double)b[i];
+  __syncthreads();
+  for (int64_t k = 0; k < nc; ++k) {
+    const double yk = y[k] / L[k * nc + k];
+    for (int64_t i = k + 1 + tid; i < nc; i += nt) y[i] -= L[k * nc + i] * yk;
+    __syncthreads();
+    if (tid == 0) y[k] = yk;
+    __syncthreads();
+  }
+  for (int64_t k = nc - 1; k >= 0; --k) {
+    const double xk = y[k] / L[k * nc + k];
+    for (int64_t i = tid; i < k; i += nt) y[i] -= L[i * nc + k] * xk;
+    __syncthreads();
+    if (tid == 0) y[k] = xk;
+    __syncthreads();
+  }
+  for (int64_t i = tid; i < nc; i += nt) x[i] = (V)y[i];
+}
+
+// ------------------------------------------------------------------ reductions and vectors
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  // fixed-shape tree: warp shuffles, then warp leaders through shared memory
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;
+}
+
+__global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const double* __restrict__ x,
+                                                          const double* __restrict__ y, double* partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// two dots in one pass: <r, z> and, for flexible CG, <z, r - rold>
+__global__ void __launch_bounds__(kRedThreads) dot_rz_kernel(int64_t n, const double* __restrict__ r,
+                                                             const double* __restrict__ z,
+                                                             const double* __restrict__ rold, int flexible,
+                                                             double* partial) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[i], ri = r[i];
+    s0 += ri * zi;
+    if (flexible) s1 += zi * (ri - rold[i]);
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    partial[kRedBlocks + blockIdx.x] = s1;
+  }
+}
+
+// sum of kRedBlocks partials by one block in a fixed order
+__device__ double sum_partials(const double* partial, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += partial[i];
+  return block_sum(v, sh);
+}
+
+__global__ void reduce_kernel(const double* partial, double* out) {
+  __shared__ double sh[32];
+  const double v = sum_partials(partial, sh);
+  if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void finish_bb_kernel(Scalars* sc, const double* partial) {
+  __shared__ double sh[32];
+  const double v = sum_partials(partial, sh);
+  if (threadIdx.x == 0) {
+    sc->bb = v;
+    sc->rr = v;
+    sc->status = 0;
+  }
+}
+
+__global__ void finish_rz_kernel(Scalars* sc, const double* partial, int first, int flexible) {
+  __shared__ double sh[32];
+  const double rz = sum_partials(partial, sh);
+  const double zd = sum_partials(partial + kRedBlocks, sh);
+  if (threadIdx.x == 0) {
+    if (!(rz > 0.0) && sc->status == 0) sc->status = GIAMG_ERR_BREAKDOWN;
+    if (first) {
+      sc->beta = 0.0;
+    } else {
+      sc->beta = (flexible ? zd : rz) / sc->rho;
+    }
+    sc->rho_old = sc->rho;
+    sc->rho = rz;
+  }
+}
+
+__global__ void finish_pq_kernel(Scalars* sc, const double* partial) {
+  __shared__ double sh[32];
+  const double pq = sum_partials(partial, sh);
+  if (threadIdx.x == 0) {
+    sc->pq = pq;
+    if (!(pq > 0.0) && sc->status == 0) sc->status = GIAMG_ERR_BREAKDOWN;
+    sc->alpha = sc->rho / pq;
+  }
+}
+
+__global__ void finish_rr_kernel(Scalars* sc, const double* partial) {
+  __shared__ double sh[32];
+  const double rr = sum_partials(partial, sh);
+  if (threadIdx.x == 0) {
+    sc->rr = rr;
+    if (!(rr == rr) && sc->status == 0) sc->status = GIAMG_ERR_BREAKDOWN;
+  }
+}
+
+__global__ void update_p_kernel(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+                                const Scalars* __restrict__ sc, int first) {
+  const double beta = first ? 0.0 : sc->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+__global__ void __launch_bounds__(kRedThreads) update_xr_kernel(int64_t n, const double* __restrict__ p,
+                                                                const double* __restrict__ q, double* __restrict__ x,
+                                                                double* __restrict__ r, double* __restrict__ rold,
+                                                                int flexible, const Scalars* __restrict__ sc,
+                                                                double* partial) {
+  __shared__ double sh[32];
+  const double alpha = sc->alpha;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    if (flexible) rold[i] = ri;
+    x[i] = x[i] + alpha * p[i];
+    const double rn = ri - alpha * q[i];
+    r[i] = rn;
+    s += rn * rn;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void pcg_init_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ x,
+                                double* __restrict__ r, double* partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    x[i] = 0.0;
+    r[i] = bi;
+    s += bi * bi;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename V>
+__global__ void cheb_first_kernel(int64_t n, const V* __restrict__ b, const V* __restrict__ dinv, V c2, V* __restrict__ x,
+                                  V* __restrict__ d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const V v = c2 * dinv[i] * b[i];
+    d[i] = v;
+    x[i] = v;
+  }
+}
+
+__global__ void copy_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) y[i] = x[i];
+}
+__global__ void fill_kernel(int64_t n, double v, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) y[i] = v;
+}
+__global__ void axpy_kernel(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = y[i] + a * x[i];
+}
+__global__ void to32_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void to64_kernel(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+__global__ void add32_kernel(int64_t n, const float* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = y[i] + x[i];
+}
+
+inline unsigned vec_grid(int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 16); }
+
+}  // namespace
+
+// ================================================================== launchers
+void spmv(const DCSR& A, const double* x, double* y, cudaStream_t s, double avg) {
+  launch_rows<double, kSpmv>(A, A.v.get(), x, nullptr, y, nullptr, nullptr, 0.0, 0.0, s, avg);
+}
+void spmv32(const DCSR& A, const float* x, float* y, cudaStream_t s, double avg) {
+  launch_rows<float, kSpmv>(A, A.v32.get(), x, nullptr, y, nullptr, nullptr, 0.f, 0.f, s, avg);
+}
+void residual(const DCSR& A, const double* b, const double* x, double* r, cudaStream_t s, double avg) {
+  launch_rows<double, kResidual>(A, A.v.get(), x, b, r, nullptr, nullptr, 0.0, 0.0, s, avg);
+}
+void residual32(const DCSR& A, const float* b, const float* x, float* r, cudaStream_t s, double avg) {
+  launch_rows<float, kResidual>(A, A.v32.get(), x, b, r, nullptr, nullptr, 0.f, 0.f, s, avg);
+}
+void cheb_step(const DCSR& A, const double* b, const double* x, double* xo, double* d, const double* dinv, double c1,
+               double c2, cudaStream_t s, double avg) {
+  launch_rows<double, kCheb>(A, A.v.get(), x, b, xo, d, dinv, c1, c2, s, avg);
+}
+void cheb_step32(const DCSR& A, const float* b, const float* x, float* xo, float* d, const float* dinv, float c1,
+                 float c2, cudaStream_t s, double avg) {
+  launch_rows<float, kCheb>(A, A.v32.get(), x, b, xo, d, dinv, c1, c2, s, avg);
+}
+void cheb_first(int64_t n, const double* b, const double* dinv, double c2, double* x, double* d, cudaStream_t s) {
+  { cheb_first_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, b, dinv, c2, x, d); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void cheb_first32(int64_t n, const float* b, const float* dinv, float c2, float* x, float* d, cudaStream_t s) {
+  { cheb_first_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, b, dinv, c2, x, d); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+template <typename V>
+static void p_restrict_t(const Level& L, const V* rf, V* rc, const V* p1d, V* part, cudaStream_t s) {
+  const size_t sm = restrict_smem<V>(L.p, L.q);
+  { p_restrict_kernel<V><<<(unsigned)L.n_elem, 128, sm, s>>>(L.n_elem, L.p, L.q, L.l2g.get(), L.own.get(), p1d, rf, part); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  { p_gather_kernel<V><<<grid_for(L.n_next, 256), 256, 0, s>>>(L.n_next, L.cinc_ptr.get(), L.cinc.get(), part, rc); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+template <typename V>
+static void p_prolong_t(const Level& L, const V* ec, V* xf, const V* p1d, cudaStream_t s) {
+  const size_t sm = prolong_smem<V>(L.p, L.q);
+  { p_prolong_kernel<V><<<(unsigned)L.n_elem, 128, sm, s>>>(L.n_elem, L.p, L.q, L.l2g.get(), L.own.get(), L.l2g_c.get(),
+                                                           p1d, ec, xf); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void p_restrict(const Level& L, const double* rf, double* rc, cudaStream_t s) {
+  p_restrict_t<double>(L, rf, rc, L.p1d.get(), L.part.get(), s);
+}
+void p_prolong(const Level& L, const double* ec, double* xf, cudaStream_t s) { p_prolong_t<double>(L, ec, xf, L.p1d.get(), s); }
+void p_restrict32(const Level& L, const float* rf, float* rc, cudaStream_t s) {
+  p_restrict_t<float>(L, rf, rc, L.p1d32.get(), L.part32.get(), s);
+}
+void p_prolong32(const Level& L, const float* ec, float* xf, cudaStream_t s) { p_prolong_t<float>(L, ec, xf, L.p1d32.get(), s); }
+
+void h_restrict(const Level& L, const double* rf, double* rc, cudaStream_t s) {
+  launch_rows<double, kSpmv>(L.R, L.R.v.get(), rf, nullptr, rc, nullptr, nullptr, 0.0, 0.0, s,
+                             L.R.n ? (double)L.R.nnz / L.R.n : 0.0);
+}
+void h_prolong(const Level& L, const double* ec, double* xf, cudaStream_t s) {
+  launch_rows<double, kAddSpmv>(L.P, L.P.v.get(), ec, nullptr, xf, nullptr, nullptr, 0.0, 0.0, s,
+                                L.P.n ? (double)L.P.nnz / L.P.n : 0.0);
+}
+void h_restrict32(const Level& L, const float* rf, float* rc, cudaStream_t s) {
+  launch_rows<float, kSpmv>(L.R, L.R.v32.get(), rf, nullptr, rc, nullptr, nullptr, 0.f, 0.f, s,
+                            L.R.n ? (double)L.R.nnz / L.R.n : 0.0);
+}
+void h_prolong32(const Level& L, const float* ec, float* xf, cudaStream_t s) {
+  launch_rows<float, kAddSpmv>(L.P, L.P.v32.get(), ec, nullptr, xf, nullptr, nullptr, 0.f, 0.f, s,
+                               L.P.n ? (double)L.P.nnz / L.P.n : 0.0);
+}
+
+int cholesky_factor(double* L, int64_t nc, cudaStream_t s) {
+  int* st = nullptr;
+  GIAMG_CUDA(cudaMallocAsync((void**)&st, sizeof(int), s));
+  GIAMG_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
+  for (int64_t k = 0; k < nc; ++k) {
+    { chol_scale_col<<<1, 256, 0, s>>>(L, nc, k, st); note_launch(); }
+    const int64_t m = nc - k - 1;
+    if (m > 0) { chol_update<<<grid_for(m * m, 256), 256, 0, s>>>(L, nc, k); note_launch(); }
+  }
+  { zero_upper<<<grid_for(nc * nc, 256), 256, 0, s>>>(L, nc); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  int h = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  cudaFreeAsync(st, s);
+  return h ? GIAMG_ERR_NOT_SPD : GIAMG_OK;
+}
+static void chol_smem_attr() {
+  static bool done = false;
+  if (done) return;
+  GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
+  GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
+  done = true;
+}
+void chol_solve(const double* L, int64_t nc, const double* b, double* x, cudaStream_t s) {
+  chol_smem_attr();
+  { chol_solve_kernel<double><<<1, 512, sizeof(double) * nc, s>>>(L, nc, b, x); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void chol_solve32(const double* L, int64_t nc, const float* b, float* x, cudaStream_t s) {
+  chol_smem_attr();
+  { chol_solve_kernel<float><<<1, 512, sizeof(double) * nc, s>>>(L, nc, b, x); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+void dot_partial(int64_t n, const double* x, const double* y, double* partial, cudaStream_t s) {
+  { dot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void reduce_to(const double* partial, double* out, cudaStream_t s) {
+  { reduce_kernel<<<1, 1024, 0, s>>>(partial, out); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void vec_copy(int64_t n, const double* x, double* y, cudaStream_t s) {
+  { copy_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void vec_fill(int64_t n, double v, double* y, cudaStream_t s) {
+  { fill_kernel<<<vec_grid(n), 256, 0, s>>>(n, v, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void vec_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
+  { axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void vec_to32(int64_t n, const double* x, float* y, cudaStream_t s) {
+  { to32_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void vec_to64(int64_t n, const float* x, double* y, cudaStream_t s) {
+  { to64_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void vec_add32(int64_t n, const float* x, float* y, cudaStream_t s) {
+  { add32_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+void pcg_init(int64_t n, const double* b, double* x, double* r, double* partial, cudaStream_t s) {
+  { pcg_init_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, x, r, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_finish_bb(Scalars* sc, const double* partial, cudaStream_t s) {
+  { finish_bb_kernel<<<1, 1024, 0, s>>>(sc, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_dot_rz(int64_t n, const double* r, const double* z, const double* rold, int flexible, double* partial,
+                cudaStream_t s) {
+  { dot_rz_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, z, rold, flexible, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_finish_rz(Scalars* sc, const double* partial, int first, int flexible, cudaStream_t s) {
+  { finish_rz_kernel<<<1, 1024, 0, s>>>(sc, partial, first, flexible); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_update_p(int64_t n, const double* z, double* p, const Scalars* sc, int first, cudaStream_t s) {
+  { update_p_kernel<<<vec_grid(n), 256, 0, s>>>(n, z, p, sc, first); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_spmv_pq(const DCSR& A, const double* p, double* q, double* partial, cudaStream_t s, double avg) {
+  spmv(A, p, q, s, avg);
+  dot_partial(A.n, p, q, partial, s);
+}
+void pcg_finish_pq(Scalars* sc, const double* partial, cudaStream_t s) {
+  { finish_pq_kernel<<<1, 1024, 0, s>>>(sc, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_update_xr(int64_t n, const double* p, const double* q, double* x, double* r, double* rold, int flexible,
+                   const Scalars* sc, double* partial, cudaStream_t s) {
+  { update_xr_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, p, q, x, r, rold, flexible, sc, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void pcg_finish_rr(Scalars* sc, const double* partial, cudaStream_t s) {
+  { finish_rr_kernel<<<1, 1024, 0, s>>>(sc, partial); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+}  // namespace giamg

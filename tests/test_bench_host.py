@@ -1,0 +1,51 @@
+"""Host logic of bench.py: percentiles, and the multi-process path (replicas with a barrier and a
+max over ranks) on two gloo processes."""
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_percentiles():
+    v = [5.0, 1.0, 3.0, 2.0, 4.0]
+    assert bench.pct(v, 0.5) == 3.0
+    assert bench.pct(v, 0.0) == 1.0 and bench.pct(v, 1.0) == 5.0
+    assert abs(bench.pct(v, 0.99) - 4.96) < 1e-12
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+WORKER = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import bench
+rank, ws, local, td = bench.dist()
+v = bench.max_over_ranks(td, 10.0 + rank)
+td.barrier()
+print(f"rank {{rank}} of {{ws}} max {{v}}")
+td.destroy_process_group()
+"""
+
+
+def test_two_rank_max_over_ranks_with_gloo():
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, WORLD_SIZE="2", RANK=str(r), LOCAL_RANK=str(r), MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, "-c", WORKER.format(root=ROOT)], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=120) for p in procs]
+    for p, (o, e) in zip(procs, outs):
+        assert p.returncode == 0, e
+    assert all("max 11.0" in o for o, _ in outs)

@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same inputs.
+
+Bars (written where they are used):
+  hierarchy structure (sizes, row pointers, columns, aggregates, P patterns)   bit-exact
+  hierarchy values (A_l, P_l)                                                   1e-12 relative
+  level SpMV                                                                    1e-13 of |A||x|
+  transfers, smoother, coarse solve, V-cycle (FP64)                             1e-10 relative
+  V-cycle with FP32 levels vs the oracle's FP32 V-cycle                         1e-4 relative
+  PCG with the oracle's iteration count forced                                  x within 1e-10
+  PCG stopping freely                                                           iterations +-1
+The cases span several tiles and ragged sizes: uniform, jittered and graded meshes, p = 2..8,
+a relabelled numbering with per-element index symmetries, and levels with aggregation.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import fegen  # noqa: E402
+import oracle  # noqa: E402
+import paper_2512_15121_gb300 as g  # noqa: E402
+
+CASES = {
+    "cube4_p4": dict(n=4, p=4, mesh="uniform", lam=1.0, k=3),
+    "jitter8_p2_poisson": dict(n=8, p=2, mesh="jitter", lam=0.0, rhs="fourier", k=2),
+    "jitter6_p6": dict(n=6, p=6, mesh="jitter", lam=10.0, k=3),
+    "graded345_p8_kappa": dict(n=(3, 4, 5), p=8, mesh="graded", lam=1000.0, kappa=1, k=2),
+    "jitter6_p4_relabelled": dict(n=6, p=4, mesh="jitter", lam=1.0, perm_seed=5, sym_seed=6, k=3),
+    "jitter12_p2_ragged": dict(n=(12, 11, 13), p=2, mesh="jitter", lam=1.0, k=2),
+    "cube2_p3_odd": dict(n=2, p=3, mesh="uniform", lam=1.0, k=3),
+}
+
+_cache = {}
+
+
+def setup_case(name):
+    if name not in _cache:
+        cfg = dict(CASES[name])
+        k = cfg.pop("k")
+        prob = fegen.make(**cfg)
+        orc = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+        gpu = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+        _cache[name] = (prob, orc, gpu, k)
+    return _cache[name]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _release():
+    yield
+    for prob, orc, gpu, k in _cache.values():
+        gpu.close()
+    _cache.clear()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hierarchy_structure_bit_exact(name):
+    prob, orc, gpu, _ = setup_case(name)
+    assert gpu.num_levels == orc.num_levels
+    for l in range(orc.num_levels):
+        a, b = gpu.level_info(l), orc.level_info(l)
+        assert a == b, (l, a, b)
+        grp, gci, gv, gagg = gpu.level(l)
+        orp, oci, ov, oagg = orc.level(l)
+        assert np.array_equal(grp, orp) and np.array_equal(gci, oci), l
+        assert np.max(np.abs(gv - ov)) <= 1e-12 * np.max(np.abs(ov)), l
+        if oagg is not None:
+            assert np.array_equal(gagg, oagg), l
+        if b["kind"] != oracle.KIND_COARSEST:
+            prp, pci, pv, _ = gpu.prolongation(l)
+            qrp, qci, qv, _ = orc.prolongation(l)
+            assert np.array_equal(prp, qrp) and np.array_equal(pci, qci), l
+            assert np.max(np.abs(pv - qv)) <= 1e-12 * np.max(np.abs(qv)), l
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_chebyshev_bounds(name):
+    prob, orc, gpu, _ = setup_case(name)
+    for l in range(orc.num_levels - 1):
+        assert abs(gpu.rho_hat(l) - orc.rho_hat(l)) <= 1e-10 * orc.rho_hat(l)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_level_spmv(name):
+    prob, orc, gpu, _ = setup_case(name)
+    rng = np.random.default_rng(1)
+    for l in range(orc.num_levels):
+        n = orc.level_info(l)["n"]
+        x = rng.normal(size=n)
+        y = host(gpu.spmv(l, dev(x)))
+        yo = orc.spmv(l, x)
+        rp, ci, v, _ = orc.level(l)
+        import scipy.sparse as sp
+        absA = sp.csr_matrix((np.abs(v), ci, rp), shape=(n, n))
+        scale = absA @ np.abs(x)
+        assert np.all(np.abs(y - yo) <= 1e-13 * scale + 1e-300), l
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_transfers(name):
+    prob, orc, gpu, _ = setup_case(name)
+    rng = np.random.default_rng(2)
+    for l in range(orc.num_levels - 1):
+        info = orc.level_info(l)
+        rf = rng.normal(size=info["n"])
+        rc = host(gpu.restrict(l, dev(rf)))
+        rco = orc.restrict(l, rf)
+        assert np.max(np.abs(rc - rco)) <= 1e-12 * np.max(np.abs(rco)), l
+        ec = rng.normal(size=info["n_next"])
+        xf = rng.normal(size=info["n"])
+        xo = host(gpu.prolong(l, dev(ec), dev(xf)))
+        xoo = orc.prolong(l, ec, xf)
+        assert np.max(np.abs(xo - xoo)) <= 1e-12 * np.max(np.abs(xoo)), l
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_smoother_and_coarse_solve(name):
+    prob, orc, gpu, _ = setup_case(name)
+    rng = np.random.default_rng(3)
+    for l in range(orc.num_levels - 1):
+        n = orc.level_info(l)["n"]
+        b = rng.normal(size=n)
+        x0 = rng.normal(size=n)
+        for start in (None, x0):
+            xg = host(gpu.smooth(l, dev(b), None if start is None else dev(start)))
+            xo = orc.cheb(l, b, start)
+            assert np.max(np.abs(xg - xo)) <= 1e-10 * np.max(np.abs(xo)), l
+    nc = orc.level_info(orc.num_levels - 1)["n"]
+    r = rng.normal(size=nc)
+    assert np.allclose(host(gpu.coarse_solve(dev(r))), orc.coarse_solve(r), rtol=0, atol=1e-10 * np.abs(orc.coarse_solve(r)).max())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle(name):
+    prob, orc, gpu, _ = setup_case(name)
+    rng = np.random.default_rng(4)
+    r = rng.normal(size=prob.n)
+    z = host(gpu.vcycle(dev(r), 0))
+    zo = orc.vcycle(r, 0)
+    assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo)
+    z32 = host(gpu.vcycle(dev(r), 1))
+    zo32 = orc.vcycle(r, 1)
+    assert np.linalg.norm(z32 - zo32) <= 1e-4 * np.linalg.norm(zo32)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pcg_parity(name):
+    prob, orc, gpu, _ = setup_case(name)
+    b = prob.b
+    xo, ito, rro, hist, st = orc.solve(b, rtol=1e-8)
+    assert st == "ok"
+    x, it, rr = gpu.solve(dev(b), rtol=1e-8, force_iters=ito)
+    assert it == ito
+    assert np.linalg.norm(host(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+    x2, it2, rr2 = gpu.solve(dev(b), rtol=1e-8)
+    assert abs(it2 - ito) <= 1 and rr2 <= 1e-8
+    ghist, true_rr = gpu.stats(it2 + 1)
+    assert np.allclose(ghist[: min(len(hist), it2 + 1)], hist[: min(len(hist), it2 + 1)], rtol=1e-6, atol=1e-14)
+    r_true = b - orc.spmv(0, host(x2))
+    assert abs(true_rr - np.linalg.norm(r_true) / np.linalg.norm(b)) <= 1e-6 * true_rr + 1e-15
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_precision_solve(name):
+    prob, orc, gpu, _ = setup_case(name)
+    b = prob.b
+    x, it, rr = gpu.solve(dev(b), rtol=1e-8, precision=1)
+    assert rr <= 1e-8
+    r_true = b - orc.spmv(0, host(x))
+    assert np.linalg.norm(r_true) <= 1.5e-8 * np.linalg.norm(b)
+    xo, ito, _, _, _ = orc.solve(b, rtol=1e-8, precision=1)
+    assert abs(it - ito) <= 2
+
+
+def test_solve_is_bitwise_reproducible():
+    prob, orc, gpu, _ = setup_case("jitter6_p6")
+    b = dev(prob.b)
+    x1, i1, _ = gpu.solve(b, rtol=1e-9)
+    x2, i2, _ = gpu.solve(b, rtol=1e-9)
+    assert i1 == i2 and torch.equal(x1, x2)
+
+
+def test_host_mode_matches_device_mode():
+    prob = fegen.make(3, 4, mesh="jitter", lam=1.0)
+    a = g.Solver.from_problem(prob, device=False, coords=True)
+    d = g.Solver.from_problem(prob, device=True, coords=True)
+    xa, ia, ra = a.solve(prob.b, rtol=1e-9)
+    xd, idd, rd = d.solve(dev(prob.b), rtol=1e-9)
+    assert ia == idd and np.array_equal(xa, host(xd))
+    a.close()
+    d.close()
+
+
+def test_zero_rhs_and_exact_iteration_limit():
+    prob, orc, gpu, _ = setup_case("cube2_p3_odd")
+    x, it, rr = gpu.solve(dev(np.zeros(prob.n)), rtol=1e-8)
+    assert it == 0 and rr == 0.0 and torch.count_nonzero(x) == 0
+    capped = g.Solver.from_problem(prob, device=True, max_iter=2)
+    x, it, rr = capped.solve(dev(prob.b), rtol=1e-30)
+    assert capped.last_status == g.GIAMG_ERR_MAXITER and it == 2 and rr > 0
+    capped.close()
+
+
+def test_errors_are_reported_not_raised_in_c():
+    prob = fegen.make(2, 2, lam=1.0)
+    # non-uniform orders
+    order = np.full(prob.n_elem, 2, np.int32)
+    order[1] = 3
+    h = __import__("ctypes").c_void_p()
+    L = g.lib()
+    opt = g.default_options()
+    rc = L.giamg_setup(prob.n, g._ptr(prob.row_ptr), g._ptr(prob.col), g._ptr(prob.val), prob.n_elem,
+                       g._ptr(prob.elem_dof), g._ptr(order), None, __import__("ctypes").byref(opt), None,
+                       __import__("ctypes").byref(h))
+    assert rc == g.GIAMG_ERR_ORDER and b"uniform" in L.giamg_last_error()
+    # element map pairing dofs of far-apart elements (no Dirichlet rows to excuse the pairs)
+    free = fegen.make(2, 2, lam=1.0, dirichlet=False)
+    bad = free.elem_dof.copy()
+    bad[0, 0], bad[-1, -1] = bad[-1, -1], bad[0, 0]
+    with pytest.raises(g.GiamgError) as e:
+        g.Solver(free.n, free.row_ptr, free.col, free.val, bad, 2)
+    assert e.value.code == g.GIAMG_ERR_MAP
+    # out-of-range map entry
+    bad = prob.elem_dof.copy()
+    bad[0, 0] = prob.n + 7
+    with pytest.raises(g.GiamgError) as e:
+        g.Solver(prob.n, prob.row_ptr, prob.col, prob.val, bad, 2)
+    assert e.value.code == g.GIAMG_ERR_MAP
+    # not positive definite: flip the sign of the matrix
+    with pytest.raises(g.GiamgError) as e:
+        g.Solver(prob.n, prob.row_ptr, prob.col, -prob.val, prob.elem_dof, 2)
+    assert e.value.code == g.GIAMG_ERR_NOT_SPD
+    # coordinates that are not the element's GLL image
+    c = prob.coords.copy()
+    c[prob.elem_dof[0, 13]] += 0.01
+    with pytest.raises(g.GiamgError) as e:
+        g.Solver(prob.n, prob.row_ptr, prob.col, prob.val, prob.elem_dof, 2, coords=c)
+    assert e.value.code == g.GIAMG_ERR_MAP
+    # unsorted columns
+    col = prob.col.copy()
+    i = np.flatnonzero(np.diff(prob.row_ptr) > 2)[0]
+    s = prob.row_ptr[i]
+    col[s], col[s + 1] = col[s + 1], col[s]
+    with pytest.raises(g.GiamgError) as e:
+        g.Solver(prob.n, prob.row_ptr, col, prob.val, prob.elem_dof, 2)
+    assert e.value.code == g.GIAMG_ERR_ARG
+
+
+def test_strength_threshold_option_runs_and_matches_oracle():
+    prob = fegen.make(8, 2, mesh="jitter", lam=0.0, rhs="fourier")
+    orc = oracle.Hierarchy.from_problem(prob, cheb_degree=2, strength_theta=0.05)
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=2, strength_theta=0.05)
+    assert gpu.num_levels == orc.num_levels
+    for l in range(orc.num_levels):
+        grp, gci, gv, gagg = gpu.level(l)
+        orp, oci, ov, oagg = orc.level(l)
+        assert np.array_equal(grp, orp) and np.array_equal(gci, oci)
+        if oagg is not None:
+            assert np.array_equal(gagg, oagg)
+    gpu.close()
