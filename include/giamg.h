@@ -163,6 +163,20 @@ GIAMG_API int giamg_profile_read(giamg_handle h, int category, double* total_ms,
 /* Number of kernels this library has launched in the process so far (all handles). */
 GIAMG_API int giamg_launch_count(int64_t* count);
 
+/* The true relative residual ||b - A x||_2 / ||b||_2 on the finest level, computed without
+ * allocating any memory (the paper has no counterpart; this is a service for callers).
+ * Callers that cannot call cudaMalloc -- code whose device memory is owned by another allocator
+ * that has reserved the GPU, or a loop that must keep a fixed memory footprint -- get the same
+ * number as giamg_solve_stats, which allocates a small buffer on every call.
+ *   b, x: device arrays of the handle's n (always device pointers, whatever device_ptrs says);
+ *   *true_relres: host output.  Work runs on the handle's stream, which is synchronised.
+ * The partial sums live in a static 1 MiB device array that every GPU loading the library holds
+ * until the process exits; matrices with more than 16,777,216 rows are rejected with
+ * GIAMG_ERR_ARG.  The first call on a device looks up that array's device address (make it
+ * before any stream capture).  All calls on one device share the array, so calls that overlap
+ * on the same GPU race; each call writes every entry it reads, so nothing needs clearing. */
+GIAMG_API int giamg_true_relres_noalloc(giamg_handle h, const double* b, const double* x, double* true_relres);
+
 /* Release the handle and all of its device memory.  NULL is accepted. */
 GIAMG_API int giamg_free(giamg_handle h);
 

@@ -28,7 +28,7 @@ EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_e
            "giamg_level_rho", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
            "giamg_last_error", "giamg_set_device_ptrs", "giamg_profile_enable", "giamg_profile_read",
-           "giamg_launch_count"]
+           "giamg_launch_count", "giamg_true_relres_noalloc"]
 
 
 class GiamgError(RuntimeError):
@@ -83,6 +83,7 @@ def lib():
         L.giamg_profile_enable.argtypes = [vp, i32]
         L.giamg_profile_read.argtypes = [vp, i32, P(dbl), P(i64), P(dbl)]
         L.giamg_launch_count.argtypes = [P(i64)]
+        L.giamg_true_relres_noalloc.argtypes = [vp, vp, vp, P(dbl)]
         L.giamg_last_error.argtypes = []
         L.giamg_last_error.restype = ctypes.c_char_p
         _lib = L

@@ -598,6 +598,9 @@ void copy_out(T* dst, const T* src, size_t count, bool dev, cudaStream_t s) {
 }
 
 }  // namespace
+
+Hierarchy* hierarchy_of(giamg_handle h) { return ctx_of(h)->H; }
+
 }  // namespace giamg
 
 using namespace giamg;

@@ -167,6 +167,9 @@ struct Hierarchy {
   ~Hierarchy();
 };
 
+// the hierarchy behind a C handle (throws GIAMG_ERR_ARG for NULL)
+Hierarchy* hierarchy_of(giamg_handle h);
+
 // ------------------------------------------------------------------ kernels (launchers)
 // reductions: fixed-size grid, partial sums reduced in a fixed order (bitwise reproducible)
 constexpr int kRedBlocks = 1024;
