@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--workload", default="helmholtz_16cube_jitter_p6")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the multi-RHS and serving measurements")
     return ap.parse_args()
 
 
@@ -277,6 +278,10 @@ def run_ours(args):
     S.set_device_ptrs(True)
 
     peak, peak_kind = measured_peaks()
+    variant = {}
+    for mode, prec in (("fp64", 0), ("mixed", 1)):
+        tpr, form = S.kernel(0, prec)
+        variant[mode] = f"{form} form, {tpr} threads per row"
 
     def roof(res, mode):
         ms, cnt, by = res["prof"][0]
@@ -286,7 +291,8 @@ def run_ours(args):
         tr = ncu_traffic(args.workload, mode)
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr,
-                "kernel": f"csr_rows ({'FP32' if mode == 'mixed' else 'FP64'} Chebyshev step / residual, finest level)",
+                "kernel": f"finest-level row kernels ({'FP32' if mode == 'mixed' else 'FP64'} Chebyshev step and "
+                          f"residual): {variant[mode]}",
                 "launches": cnt, "avg_launch_ms": round(ms / cnt, 4),
                 "algorithmic_bytes_per_launch": round(by / cnt), "peak_kind": peak_kind}
 
@@ -295,6 +301,8 @@ def run_ours(args):
         ms = sum(res["prof"][c][0] for c in range(5))
         by = sum(res["prof"][c][2] for c in range(5))
         return round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None
+
+    extras = {} if args.no_extras else {"batch": measure_batch(g, torch), "serving": measure_serving()}
 
     value = max_over_ranks(td, mixed["p50"])
     ms_per_step = max_over_ranks(td, mixed["wall"] / args.steps)
@@ -327,8 +335,59 @@ def run_ours(args):
         "gpu_launches": mixed["launches"],
         "clocks": clk,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     S.close()
+
+
+def measure_batch(g, torch, m=32, reps=5):
+    """32 right-hand sides of the 24^3 Poisson workload as one multi-RHS solve (FP32 V-cycle in
+    flexible CG), against one single-RHS solve of the first column."""
+    import numpy as np
+    import fegen
+    name = "poisson_24cube_jitter_p4"
+    prob = fegen.workload(name, rhs="none")
+    B = np.stack([prob.rhs("fourier", 1000 + j) for j in range(m)], axis=1)
+    S = g.Solver.from_problem(prob, device=True, cheb_degree=fegen.WORKLOADS[name]["k"])
+    Bd = torch.from_numpy(B).cuda()
+    b0 = Bd[:, 0].contiguous()
+    for _ in range(2):
+        S.solve_batch(Bd, rtol=1e-8, precision=1)
+        S.solve(b0, rtol=1e-8, precision=1)
+    st = torch.cuda.current_stream()
+    tb, ts = [], []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        X, it, rr = S.solve_batch(Bd, rtol=1e-8, precision=1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+        e0.record(st)
+        S.solve(b0, rtol=1e-8, precision=1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    S.close()
+    pb, ps = pct(tb, 0.5), pct(ts, 0.5)
+    return {"workload": name, "dofs": prob.n, "nnz": prob.nnz, "m": m, "p50_ms": round(pb, 3),
+            "per_solve_ms": round(pb / m, 3), "single_rhs_p50_ms": round(ps, 3),
+            "throughput_vs_single": round(ps * m / pb, 2), "iters": [int(it.min()), int(it.max())],
+            "max_relres": float(rr.max()), "dtype": "f32 V-cycle in f64 FCG"}
+
+
+def measure_serving(n_requests=128, rate=150.0):
+    """A stream of solve requests (jittered 4^3..8^3 meshes, p in {2,4,6}, lambda in {0,1,1000},
+    1..8 right-hand sides, Poisson arrivals) through the continuous-batching server."""
+    from paper_2512_15121_gb300 import serve
+    reqs, ops = serve.synthetic_stream(n_requests, seed=7, rate_per_s=rate)
+    srv = serve.Server(slots=4)
+    stats = serve.run_stream(srv, reqs)
+    srv.close()
+    stats.update({k: int(v) for k, v in srv.stats.items()})
+    stats.update({"rate_per_s": rate, "operators": len(ops), "errors": sum(r.error is not None for r in reqs),
+                  "mix": "jittered 4^3/6^3/8^3, p in {2,4,6}, lambda in {0,1,1000}, 1-8 RHS, FP32 V-cycle"})
+    return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()}
 
 
 def cpu_baseline(prob, k, rtol, iters):

@@ -78,6 +78,16 @@ typedef struct {
   int force_iters;        /* 0, or run exactly this many iterations (parity tests) */
   int device_ptrs;        /* 0: host arrays; 1: device arrays (e.g. torch tensors) */
   int hash_kind;          /* node hash of MIS-2 / Lanczos start: 0 SplitMix64-based, 1 identity */
+  int compress_patterns;  /* 1 (default): detect rows that repeat one of a few offset patterns
+                             (stored as a template id instead of column indices) and groups of rows
+                             with identical column sets (x gathered once per group); detection is
+                             exact, plain CSR otherwise; 0: plain CSR everywhere */
+  int autotune;           /* 1: time the row-kernel variants on every large level at setup and keep
+                             the fastest; 0 (default): the variants measured best inside the solve
+                             (FP32 rows: pattern form; FP64 rows: CSR with 16 threads per row) */
+  int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
+                             groups (falls back to CSR where the form is not available) */
+  int row_threads;        /* force threads per row (4, 8, 16, 32); 0 automatic */
 } giamg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -91,7 +101,8 @@ GIAMG_API void giamg_default_options(giamg_options* opt);
  *     With p = 1 there is no p-level and elem_dof may be NULL.
  *   coords[n][3]: nodal coordinates or NULL; when given, every element's nodes must be the
  *     trilinear image of the GLL tensor points (1e-8 of the element size), else GIAMG_ERR_MAP.
- *   opt: options (NULL = defaults).  cuda_stream: a cudaStream_t or NULL.
+ *   opt: options (NULL = defaults).  cuda_stream: a cudaStream_t or NULL; with device_ptrs
+ *     the inputs are read on this stream, so they may still be in flight on it at the call.
  *   *out: the new handle.  Every element pair (a, b) must be present in A's pattern unless
  *   one of the two rows is a Dirichlet identity row (GIAMG_ERR_MAP otherwise). */
 GIAMG_API int giamg_setup(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
@@ -109,6 +120,17 @@ GIAMG_API int giamg_solve(giamg_handle h, const double* b, double* x, double rto
  * per call instead of from the handle's options. */
 GIAMG_API int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double* b, double* x,
                    double rtol, int* iters, double* relres);
+
+/* m independent solves A X_j = B_j sharing every matrix pass (multi-right-hand-side PCG: one
+ * CG recurrence per column, each with its own alpha, beta and stopping test; the products and
+ * the V-cycle work on all columns at once, so the matrix is read once per m solves).
+ *   B, X: row-major n x m (the m values of a row are contiguous), 1 <= m <= 32.
+ *   iters[m], relres[m]: per-column iterations and final relative residuals (host arrays).
+ * Columns stop independently; GIAMG_ERR_MAXITER if any column misses rtol. */
+GIAMG_API int giamg_solve_batch(giamg_handle h, int m, const double* B, double* X, double rtol, int* iters,
+                                double* relres);
+GIAMG_API int giamg_solve_batch_ex(giamg_handle h, int precision, int force_iters, int m, const double* B, double* X,
+                                   double rtol, int* iters, double* relres);
 
 /* After a solve: relative residual history hist[0..min(len, iters+1)) of the recursive
  * residual, and the true relative residual ||b - A x|| / ||b|| recomputed in FP64. */
@@ -128,6 +150,13 @@ GIAMG_API int giamg_export_level(giamg_handle h, int level, int64_t* row_ptr, in
 /* Copy the assembled prolongation P_l (n x n_next, p_nnz entries) built during setup. */
 GIAMG_API int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_ptr, int32_t* col_idx,
                               double* val);
+/* Row-pattern compression of A_l: number of templates and of stored offsets (0, 0 when the
+ * level uses plain CSR). */
+GIAMG_API int giamg_level_templates(giamg_handle h, int level, int64_t* n_templates, int64_t* n_offsets);
+/* Row-kernel variant used on A_l for precision 0 (FP64) or 1 (FP32): threads per row and the
+ * form (*pattern: 0 CSR, 1 row patterns, 2 row groups with identical column sets), chosen by the
+ * setup-time tuner when autotune is set. */
+GIAMG_API int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern);
 /* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */
 GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
 
@@ -137,7 +166,9 @@ GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
  *   giamg_level_smooth: Chebyshev smoothing of A_l x = b in place (x_is_zero: x enters as 0).
  *   giamg_level_restrict: r_c = R_l r_f (R = P^T; element form on p-levels).
  *   giamg_level_prolong:  x_f += P_l e_c (element form on p-levels).
- *   giamg_coarse_solve:  x = A_L^-1 r on the coarsest level (Cholesky triangular solves). */
+ *   giamg_coarse_solve:  x = A_L^-1 r on the coarsest level (Cholesky triangular solves).
+ * The V-cycle applies A_L^-1 as a dense matrix formed at setup from the Cholesky factor by the
+ * same triangular solves on the unit vectors. */
 GIAMG_API int giamg_apply_vcycle(giamg_handle h, int precision, const double* r, double* z);
 GIAMG_API int giamg_level_spmv(giamg_handle h, int level, const double* x, double* y);
 GIAMG_API int giamg_level_smooth(giamg_handle h, int level, const double* b, double* x, int x_is_zero);

@@ -24,7 +24,8 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 
 # every entry point the header declares (checked by the CPU tests against the .so)
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
-           "giamg_num_levels", "giamg_level_info", "giamg_export_level", "giamg_export_prolongation",
+           "giamg_solve_batch", "giamg_solve_batch_ex",
+           "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
            "giamg_level_rho", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
            "giamg_last_error", "giamg_set_device_ptrs", "giamg_profile_enable", "giamg_profile_read",
@@ -41,7 +42,9 @@ class Options(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double),
                 ("lanczos_steps", ctypes.c_int), ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("strength_theta", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("force_iters", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("hash_kind", ctypes.c_int)]
+                ("force_iters", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("hash_kind", ctypes.c_int),
+                ("compress_patterns", ctypes.c_int), ("autotune", ctypes.c_int), ("row_form", ctypes.c_int),
+                ("row_threads", ctypes.c_int)]
 
 
 _lib = None
@@ -67,11 +70,15 @@ def lib():
         L.giamg_solve.argtypes = [vp, vp, vp, dbl, P(i32), P(dbl)]
         L.giamg_solve_ex.argtypes = [vp, i32, i32, vp, vp, dbl, P(i32), P(dbl)]
         L.giamg_solve_stats.argtypes = [vp, vp, i32, P(dbl)]
+        L.giamg_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
+        L.giamg_solve_batch_ex.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
         L.giamg_num_levels.argtypes = [vp, P(i32)]
         L.giamg_level_info.argtypes = [vp, i32, P(i32), P(i64), P(i64), P(i32), P(i64), P(i64)]
         L.giamg_export_level.argtypes = [vp, i32, vp, vp, vp, vp]
         L.giamg_export_prolongation.argtypes = [vp, i32, vp, vp, vp]
         L.giamg_level_rho.argtypes = [vp, i32, P(dbl)]
+        L.giamg_level_templates.argtypes = [vp, i32, P(i64), P(i64)]
+        L.giamg_level_kernel.argtypes = [vp, i32, i32, P(i32), P(i32)]
         L.giamg_apply_vcycle.argtypes = [vp, i32, vp, vp]
         L.giamg_level_spmv.argtypes = [vp, i32, vp, vp]
         L.giamg_level_smooth.argtypes = [vp, i32, vp, vp, i32]
@@ -157,9 +164,12 @@ class Solver:
             import torch
             ed = elem_dof
             n_elem = int(ed.shape[0]) if ed is not None else 0
+            cur = torch.cuda.current_stream(row_ptr.device)
             order = torch.full((max(n_elem, 1),), p, dtype=torch.int32, device=row_ptr.device)
             if stream is None:
-                stream = torch.cuda.current_stream(row_ptr.device).cuda_stream
+                stream = cur.cuda_stream
+            elif int(stream) != int(cur.cuda_stream):
+                cur.synchronize()  # inputs written on torch's stream are read on `stream`
         else:
             row_ptr = np.ascontiguousarray(row_ptr, np.int64)
             col = np.ascontiguousarray(col, np.int32)
@@ -221,6 +231,26 @@ class Solver:
         self.last_status = rc
         return x, it, rr
 
+    def solve_batch(self, B, rtol=1e-8, precision=None, force_iters=None, X=None):
+        """B: n x m (row-major, m <= 32).  Returns (X, iters[m], relres[m])."""
+        m = int(B.shape[1])
+        if self.device:
+            import torch
+            B = B.to("cuda", torch.float64).contiguous()
+            X = torch.empty_like(B) if X is None else X
+        else:
+            B = np.ascontiguousarray(B, np.float64)
+            X = np.empty_like(B) if X is None else X
+        it = np.zeros(m, np.int32)
+        rr = np.zeros(m, np.float64)
+        prec = self.opts.precision if precision is None else precision
+        force = self.opts.force_iters if force_iters is None else force_iters
+        rc = lib().giamg_solve_batch_ex(self._h, prec, force, m, _ptr(B), _ptr(X), rtol, _ptr(it), _ptr(rr))
+        if rc not in (GIAMG_OK, GIAMG_ERR_MAXITER):
+            _check(rc)
+        self.last_status = rc
+        return X, it, rr
+
     def stats(self, hist_len=0):
         hist = np.zeros(max(hist_len, 1))
         tr = ctypes.c_double()
@@ -281,6 +311,16 @@ class Solver:
         _check(lib().giamg_export_prolongation(self._h, l, _ptr(rp), _ptr(ci), _ptr(v)))
         return (self._host(rp, info["n"] + 1), self._host(ci, info["p_nnz"]), self._host(v, info["p_nnz"]),
                 info["n_next"])
+
+    def templates(self, l):
+        t, o = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().giamg_level_templates(self._h, l, ctypes.byref(t), ctypes.byref(o)))
+        return t.value, o.value
+
+    def kernel(self, l, precision):
+        t, p = ctypes.c_int(), ctypes.c_int()
+        _check(lib().giamg_level_kernel(self._h, l, precision, ctypes.byref(t), ctypes.byref(p)))
+        return t.value, ["csr", "pattern", "groups"][p.value]
 
     def rho_hat(self, l):
         r = ctypes.c_double()

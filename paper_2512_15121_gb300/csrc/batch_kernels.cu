@@ -1,0 +1,534 @@
+// batch_kernels.cu -- kernels of the multi-right-hand-side solve: m independent CG recurrences
+// (m <= 32) that share every matrix pass.  Blocks of vectors are row-major n x m, so the m
+// values of one row are contiguous.
+//
+//   SpMM row kernels: G = next power of two >= m lanes per row, lane j holds column j; each
+//     nonzero (value, column) is loaded once per row and applied to the m gathered values
+//     X[col * m + j] (one coalesced segment), so the matrix is read once per m solves.
+//   p-transfers: the element contractions of the single-vector path with a column index.
+//   coarsest solve: X = A^-1 B with the dense inverse.
+//   CG updates and dot products per column, reduced in a fixed order (reproducible bits).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace giamg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t work, int per_block) {
+  return (unsigned)std::max<int64_t>((work + per_block - 1) / per_block, 1);
+}
+inline unsigned vec_grid(int64_t n) {
+  return (unsigned)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 16);
+}
+
+enum BatchMode { kSpmm = 0, kResid = 1, kCheb = 2, kAdd = 3 };
+
+// One row per group of G lanes; lane j < m owns column j.  PAT: columns from the row's template.
+template <int G, typename V, int MODE, bool PAT>
+__global__ void __launch_bounds__(kThreads)
+    bat_rows(int64_t n, int m, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+             const int32_t* __restrict__ tid, const int64_t* __restrict__ tptr, const int32_t* __restrict__ toff,
+             const V* __restrict__ val, const V* __restrict__ X, const V* __restrict__ B, V* __restrict__ Y,
+             V* __restrict__ D, const V* __restrict__ dinv, V c1, V c2) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = gt / G;
+  const int j = threadIdx.x % G;
+  if (row >= n || j >= m) return;
+  const int64_t s = rp[row], e = rp[row + 1];
+  V acc0 = 0, acc1 = 0;
+  if (PAT) {
+    const int32_t* __restrict__ off = toff + tptr[tid[row]];
+    const V* __restrict__ xr = X + row * m + j;
+    const int len = (int)(e - s);
+    int k = 0;
+    for (; k + 1 < len; k += 2) {
+      acc0 = fma(__ldg(val + s + k), xr[(int64_t)__ldg(off + k) * m], acc0);
+      acc1 = fma(__ldg(val + s + k + 1), xr[(int64_t)__ldg(off + k + 1) * m], acc1);
+    }
+    if (k < len) acc0 = fma(__ldg(val + s + k), xr[(int64_t)__ldg(off + k) * m], acc0);
+  } else {
+    const V* __restrict__ xc = X + j;
+    int64_t t = s;
+    for (; t + 1 < e; t += 2) {
+      acc0 = fma(__ldg(val + t), xc[(int64_t)__ldg(ci + t) * m], acc0);
+      acc1 = fma(__ldg(val + t + 1), xc[(int64_t)__ldg(ci + t + 1) * m], acc1);
+    }
+    if (t < e) acc0 = fma(__ldg(val + t), xc[(int64_t)__ldg(ci + t) * m], acc0);
+  }
+  const V acc = acc0 + acc1;
+  const int64_t o = row * m + j;
+  if (MODE == kSpmm) {
+    Y[o] = acc;
+  } else if (MODE == kAdd) {
+    Y[o] += acc;
+  } else if (MODE == kResid) {
+    Y[o] = B[o] - acc;
+  } else {
+    const V r = B[o] - acc;
+    const V dn = (c1 == V(0) ? V(0) : c1 * D[o]) + c2 * dinv[row] * r;
+    D[o] = dn;
+    Y[o] = X[o] + dn;
+  }
+}
+
+template <int G, typename V, int MODE, bool PAT>
+void launch_g(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y, V* D, const V* dinv, V c1, V c2,
+              cudaStream_t s) {
+  bat_rows<G, V, MODE, PAT><<<grid_for(A.n * G, kThreads), kThreads, 0, s>>>(
+      A.n, m, A.rp.get(), A.ci.get(), A.pat.tid.get(), A.pat.tptr.get(), A.pat.toff.get(), val, X, B, Y, D, dinv, c1, c2);
+  note_launch();
+}
+
+template <typename V, int MODE>
+void launch_bat(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y, V* D, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  if (A.n == 0) return;
+  const bool own = val == (sizeof(V) == 8 ? (const V*)A.v.get() : (const V*)A.v32.get());
+  const bool pat = own && A.pat.on;
+  const int G = m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
+#define BAT_CASE(GG)                                                              \
+  case GG:                                                                        \
+    if (pat) launch_g<GG, V, MODE, true>(A, m, val, X, B, Y, D, dinv, c1, c2, s); \
+    else launch_g<GG, V, MODE, false>(A, m, val, X, B, Y, D, dinv, c1, c2, s);    \
+    break;
+  switch (G) {
+    BAT_CASE(1)
+    BAT_CASE(2)
+    BAT_CASE(4)
+    BAT_CASE(8)
+    BAT_CASE(16)
+    BAT_CASE(32)
+  }
+#undef BAT_CASE
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ element transfers, m columns
+// The single-vector contractions with the column as the fastest index of every work array.
+template <typename V>
+__global__ void bp_prolong_kernel(int32_t n_elem, int p, int q, int m, const int32_t* __restrict__ l2g,
+                                  const uint8_t* __restrict__ own, const int32_t* __restrict__ l2g_c,
+                                  const V* __restrict__ p1d, const V* __restrict__ ec, V* __restrict__ xf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int n1 = p + 1, m1 = q + 1;
+  const int nlf = n1 * n1 * n1, nlc = m1 * m1 * m1;
+  V* T = sm;                      // n1 * m1
+  V* u = T + n1 * m1;             // nlc * m
+  V* t1 = u + nlc * m;            // m1 * m1 * n1 * m
+  V* t2 = t1 + m1 * m1 * n1 * m;  // m1 * n1 * n1 * m
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n1 * m1; i += nt) T[i] = p1d[i];
+  for (int i = tid; i < nlc * m; i += nt) {
+    const int b = i / m, j = i % m;
+    u[i] = ec[(int64_t)l2g_c[(int64_t)e * nlc + b] * m + j];
+  }
+  __syncthreads();
+  for (int i = tid; i < m1 * m1 * n1 * m; i += nt) {
+    const int j = i % m, w = i / m, a3 = w % n1, b12 = w / n1;
+    V s = 0;
+    for (int b3 = 0; b3 < m1; ++b3) s += T[a3 * m1 + b3] * u[(b12 * m1 + b3) * m + j];
+    t1[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < m1 * n1 * n1 * m; i += nt) {
+    const int j = i % m, w = i / m, a3 = w % n1, a2 = (w / n1) % n1, b1 = w / (n1 * n1);
+    V s = 0;
+    for (int b2 = 0; b2 < m1; ++b2) s += T[a2 * m1 + b2] * t1[((b1 * m1 + b2) * n1 + a3) * m + j];
+    t2[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < nlf * m; i += nt) {
+    const int j = i % m, a = i / m;
+    const int64_t slot = (int64_t)e * nlf + a;
+    if (!own[slot]) continue;
+    const int a23 = a % (n1 * n1), a1 = a / (n1 * n1);
+    V s = 0;
+    for (int b1 = 0; b1 < m1; ++b1) s += T[a1 * m1 + b1] * t2[(b1 * n1 * n1 + a23) * m + j];
+    xf[(int64_t)l2g[slot] * m + j] += s;
+  }
+}
+
+template <typename V>
+__global__ void bp_restrict_kernel(int32_t n_elem, int p, int q, int m, const int32_t* __restrict__ l2g,
+                                   const uint8_t* __restrict__ own, const V* __restrict__ p1d,
+                                   const V* __restrict__ rf, V* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int n1 = p + 1, m1 = q + 1;
+  const int nlf = n1 * n1 * n1, nlc = m1 * m1 * m1;
+  V* T = sm;                      // n1 * m1
+  V* v = T + n1 * m1;             // nlf * m
+  V* t1 = v + nlf * m;            // n1 * n1 * m1 * m
+  V* t2 = t1 + n1 * n1 * m1 * m;  // n1 * m1 * m1 * m
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n1 * m1; i += nt) T[i] = p1d[i];
+  for (int i = tid; i < nlf * m; i += nt) {
+    const int a = i / m, j = i % m;
+    const int64_t slot = (int64_t)e * nlf + a;
+    v[i] = own[slot] ? rf[(int64_t)l2g[slot] * m + j] : V(0);
+  }
+  __syncthreads();
+  for (int i = tid; i < n1 * n1 * m1 * m; i += nt) {
+    const int j = i % m, w = i / m, b3 = w % m1, a12 = w / m1;
+    V s = 0;
+    for (int a3 = 0; a3 < n1; ++a3) s += T[a3 * m1 + b3] * v[(a12 * n1 + a3) * m + j];
+    t1[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < n1 * m1 * m1 * m; i += nt) {
+    const int j = i % m, w = i / m, b3 = w % m1, b2 = (w / m1) % m1, a1 = w / (m1 * m1);
+    V s = 0;
+    for (int a2 = 0; a2 < n1; ++a2) s += T[a2 * m1 + b2] * t1[((a1 * n1 + a2) * m1 + b3) * m + j];
+    t2[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < nlc * m; i += nt) {
+    const int j = i % m, b = i / m;
+    const int b23 = b % (m1 * m1), b1 = b / (m1 * m1);
+    V s = 0;
+    for (int a1 = 0; a1 < n1; ++a1) s += T[a1 * m1 + b1] * t2[(a1 * m1 * m1 + b23) * m + j];
+    part[((int64_t)e * nlc + b) * m + j] = s;
+  }
+}
+
+template <typename V>
+__global__ void bp_gather_kernel(int64_t nc, int m, const int64_t* __restrict__ ptr, const int32_t* __restrict__ slot,
+                                 const V* __restrict__ part, V* __restrict__ rc) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nc * m) return;
+  const int64_t c = g / m;
+  const int j = (int)(g % m);
+  V s = 0;
+  for (int64_t t = ptr[c]; t < ptr[c + 1]; ++t) s += part[(int64_t)slot[t] * m + j];
+  rc[g] = s;
+}
+
+template <typename V>
+size_t bprolong_smem(int p, int q, int m) {
+  const int n1 = p + 1, m1 = q + 1;
+  return sizeof(V) * ((size_t)n1 * m1 + (size_t)m * (m1 * m1 * m1 + m1 * m1 * n1 + m1 * n1 * n1));
+}
+template <typename V>
+size_t brestrict_smem(int p, int q, int m) {
+  const int n1 = p + 1, m1 = q + 1;
+  return sizeof(V) * ((size_t)n1 * m1 + (size_t)m * (n1 * n1 * n1 + n1 * n1 * m1 + n1 * m1 * m1));
+}
+
+// ------------------------------------------------------------------ coarsest solve, vectors
+template <typename V>
+__global__ void bat_inverse_apply(const double* __restrict__ Ainv, int64_t nc, int m, const V* __restrict__ B,
+                                  V* __restrict__ X) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nc * m) return;
+  const int64_t row = g / m;
+  const int j = (int)(g % m);
+  double s = 0.0;
+  for (int64_t k = 0; k < nc; ++k) s += Ainv[row * nc + k] * (double)B[k * m + j];
+  X[g] = (V)s;
+}
+
+template <typename V>
+__global__ void bat_cheb_first(int64_t n, int m, const V* __restrict__ B, const V* __restrict__ dinv, V c2,
+                               V* __restrict__ X, V* __restrict__ D) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * m; i += (int64_t)gridDim.x * blockDim.x) {
+    const V v = c2 * dinv[i / m] * B[i];
+    D[i] = v;
+    X[i] = v;
+  }
+}
+
+// per-column partial sums over a fixed partition of the rows: block b handles rows
+// [b*chunk, (b+1)*chunk); lane j of each warp accumulates column j (m <= 32)
+__device__ __forceinline__ void column_block_sum(double v, int m, double* sh, double* out) {
+  // v: this thread's partial for column (threadIdx.x & 31); reduce over the block's warps
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  sh[w * 32 + l] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sh[k * 32 + threadIdx.x];
+    if (threadIdx.x < m) out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Batched CG scalars, one entry per column.
+struct BatchScalars {
+  double rho[32], pq[32], alpha[32], beta[32], rr[32], bb[32];
+  int status[32], active[32];
+};
+
+__global__ void __launch_bounds__(kRedThreads) bat_init(int64_t n, int m, const double* __restrict__ B,
+                                                        double* __restrict__ X, double* __restrict__ R,
+                                                        double* partial) {
+  __shared__ double sh[32 * 32];
+  const int l = threadIdx.x & 31;
+  double s = 0.0;
+  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
+    if (l < m) {
+      const double b = B[i * m + l];
+      X[i * m + l] = 0.0;
+      R[i * m + l] = b;
+      s += b * b;
+    }
+  }
+  column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
+}
+
+// <r_j, z_j> and, for flexible CG, <z_j, r_j - rold_j>
+__global__ void __launch_bounds__(kRedThreads) bat_dot_rz(int64_t n, int m, const double* __restrict__ R,
+                                                          const double* __restrict__ Z,
+                                                          const double* __restrict__ Rold, int flexible,
+                                                          double* partial) {
+  __shared__ double sh[32 * 32];
+  const int l = threadIdx.x & 31;
+  double s0 = 0.0, s1 = 0.0;
+  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
+    if (l < m) {
+      const double z = Z[i * m + l], r = R[i * m + l];
+      s0 += r * z;
+      if (flexible) s1 += z * (r - Rold[i * m + l]);
+    }
+  }
+  column_block_sum(s0, m, sh, partial + (int64_t)blockIdx.x * 32);
+  column_block_sum(s1, m, sh, partial + (int64_t)(gridDim.x + blockIdx.x) * 32);
+}
+
+__global__ void __launch_bounds__(kRedThreads) bat_dot(int64_t n, int m, const double* __restrict__ P,
+                                                       const double* __restrict__ Q, double* partial) {
+  __shared__ double sh[32 * 32];
+  const int l = threadIdx.x & 31;
+  double s = 0.0;
+  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5)
+    if (l < m) s += P[i * m + l] * Q[i * m + l];
+  column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
+}
+
+// column sums of the block partials in block order
+__device__ double column_total(const double* partial, int blocks, int j) {
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += partial[(int64_t)b * 32 + j];
+  return s;
+}
+
+__global__ void bat_finish_bb(BatchScalars* sc, const double* partial, int blocks, int m) {
+  const int j = threadIdx.x;
+  if (j >= m) return;
+  const double v = column_total(partial, blocks, j);
+  sc->bb[j] = v;
+  sc->rr[j] = v;
+  sc->status[j] = 0;
+  sc->active[j] = v > 0.0 ? 1 : 0;
+}
+
+__global__ void bat_finish_rz(BatchScalars* sc, const double* partial, int blocks, int m, int first, int flexible) {
+  const int j = threadIdx.x;
+  if (j >= m) return;
+  const double rz = column_total(partial, blocks, j);
+  const double zd = column_total(partial + (int64_t)blocks * 32, blocks, j);
+  if (!sc->active[j]) {
+    sc->beta[j] = 0.0;
+    return;
+  }
+  if (!(rz > 0.0) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
+  sc->beta[j] = first ? 0.0 : (flexible ? zd : rz) / sc->rho[j];
+  sc->rho[j] = rz;
+}
+
+__global__ void bat_finish_pq(BatchScalars* sc, const double* partial, int blocks, int m) {
+  const int j = threadIdx.x;
+  if (j >= m) return;
+  const double pq = column_total(partial, blocks, j);
+  sc->pq[j] = pq;
+  if (!sc->active[j]) {
+    sc->alpha[j] = 0.0;
+    return;
+  }
+  if (!(pq > 0.0) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
+  sc->alpha[j] = sc->rho[j] / pq;
+}
+
+// after the update: record ||r_j||^2 and retire columns that reached the tolerance
+__global__ void bat_finish_rr(BatchScalars* sc, const double* partial, int blocks, int m, double tol2, int force) {
+  const int j = threadIdx.x;
+  if (j >= m) return;
+  const double rr = column_total(partial, blocks, j);
+  if (!sc->active[j]) return;
+  sc->rr[j] = rr;
+  if (!(rr == rr) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
+  if (sc->status[j] != 0 || (!force && rr <= tol2 * sc->bb[j])) sc->active[j] = 0;
+}
+
+__global__ void bat_update_p(int64_t n, int m, const double* __restrict__ Z, double* __restrict__ P,
+                             const BatchScalars* __restrict__ sc, int first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % m);
+    if (!sc->active[j]) continue;
+    P[i] = first ? Z[i] : Z[i] + sc->beta[j] * P[i];
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) bat_update_xr(int64_t n, int m, const double* __restrict__ P,
+                                                             const double* __restrict__ Q, double* __restrict__ X,
+                                                             double* __restrict__ R, double* __restrict__ Rold,
+                                                             int flexible, const BatchScalars* __restrict__ sc,
+                                                             double* partial) {
+  __shared__ double sh[32 * 32];
+  const int l = threadIdx.x & 31;
+  const bool act = l < m && sc->active[l];
+  const double alpha = act ? sc->alpha[l] : 0.0;
+  double s = 0.0;
+  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
+    if (act) {
+      const int64_t o = i * m + l;
+      const double ri = R[o];
+      if (flexible) Rold[o] = ri;
+      X[o] = X[o] + alpha * P[o];
+      const double rn = ri - alpha * Q[o];
+      R[o] = rn;
+      s += rn * rn;
+    }
+  }
+  column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
+}
+
+template <typename T, typename U>
+__global__ void bat_convert(int64_t count, const T* __restrict__ x, U* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (U)x[i];
+}
+
+constexpr int kBatBlocks = 1024;
+
+}  // namespace
+
+// ================================================================== launchers
+void bat_rows_launch64(const DCSR& A, int m, int mode, const double* val, const double* X, const double* B, double* Y,
+                       double* D, const double* dinv, double c1, double c2, cudaStream_t s) {
+  switch (mode) {
+    case kSpmm: launch_bat<double, kSpmm>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    case kResid: launch_bat<double, kResid>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    case kCheb: launch_bat<double, kCheb>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    default: launch_bat<double, kAdd>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+  }
+}
+void bat_rows_launch32(const DCSR& A, int m, int mode, const float* val, const float* X, const float* B, float* Y,
+                       float* D, const float* dinv, float c1, float c2, cudaStream_t s) {
+  switch (mode) {
+    case kSpmm: launch_bat<float, kSpmm>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    case kResid: launch_bat<float, kResid>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    case kCheb: launch_bat<float, kCheb>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    default: launch_bat<float, kAdd>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+  }
+}
+
+template <typename V>
+static void bp_restrict_t(const Level& L, int m, const V* rf, V* rc, const V* p1d, V* part, cudaStream_t s) {
+  const size_t sm = brestrict_smem<V>(L.p, L.q, m);
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(bp_restrict_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  GIAMG_CHECK(sm <= 200 * 1024, GIAMG_ERR_ARG, "batched restriction: too many columns for the element order");
+  { bp_restrict_kernel<V><<<(unsigned)L.n_elem, 256, sm, s>>>(L.n_elem, L.p, L.q, m, L.l2g.get(), L.own.get(), p1d, rf, part); note_launch(); }
+  { bp_gather_kernel<V><<<grid_for(L.n_next * m, 256), 256, 0, s>>>(L.n_next, m, L.cinc_ptr.get(), L.cinc.get(), part, rc); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+template <typename V>
+static void bp_prolong_t(const Level& L, int m, const V* ec, V* xf, const V* p1d, cudaStream_t s) {
+  const size_t sm = bprolong_smem<V>(L.p, L.q, m);
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(bp_prolong_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  GIAMG_CHECK(sm <= 200 * 1024, GIAMG_ERR_ARG, "batched prolongation: too many columns for the element order");
+  { bp_prolong_kernel<V><<<(unsigned)L.n_elem, 256, sm, s>>>(L.n_elem, L.p, L.q, m, L.l2g.get(), L.own.get(), L.l2g_c.get(), p1d, ec, xf); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_p_restrict(const Level& L, int m, const double* rf, double* rc, double* part, cudaStream_t s) {
+  bp_restrict_t<double>(L, m, rf, rc, L.p1d.get(), part, s);
+}
+void bat_p_restrict32(const Level& L, int m, const float* rf, float* rc, float* part, cudaStream_t s) {
+  bp_restrict_t<float>(L, m, rf, rc, L.p1d32.get(), part, s);
+}
+void bat_p_prolong(const Level& L, int m, const double* ec, double* xf, cudaStream_t s) {
+  bp_prolong_t<double>(L, m, ec, xf, L.p1d.get(), s);
+}
+void bat_p_prolong32(const Level& L, int m, const float* ec, float* xf, cudaStream_t s) {
+  bp_prolong_t<float>(L, m, ec, xf, L.p1d32.get(), s);
+}
+void bat_inverse(const double* Ainv, int64_t nc, int m, const double* B, double* X, cudaStream_t s) {
+  { bat_inverse_apply<double><<<grid_for(nc * m, 256), 256, 0, s>>>(Ainv, nc, m, B, X); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_inverse32(const double* Ainv, int64_t nc, int m, const float* B, float* X, cudaStream_t s) {
+  { bat_inverse_apply<float><<<grid_for(nc * m, 256), 256, 0, s>>>(Ainv, nc, m, B, X); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_cheb_first64(int64_t n, int m, const double* B, const double* dinv, double c2, double* X, double* D, cudaStream_t s) {
+  { bat_cheb_first<double><<<vec_grid(n * m), 256, 0, s>>>(n, m, B, dinv, c2, X, D); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_cheb_first32(int64_t n, int m, const float* B, const float* dinv, float c2, float* X, float* D, cudaStream_t s) {
+  { bat_cheb_first<float><<<vec_grid(n * m), 256, 0, s>>>(n, m, B, dinv, c2, X, D); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_to32(int64_t count, const double* x, float* y, cudaStream_t s) {
+  { bat_convert<double, float><<<vec_grid(count), 256, 0, s>>>(count, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_to64(int64_t count, const float* x, double* y, cudaStream_t s) {
+  { bat_convert<float, double><<<vec_grid(count), 256, 0, s>>>(count, x, y); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+size_t batch_scalars_bytes() { return sizeof(BatchScalars); }
+int batch_reduction_blocks() { return kBatBlocks; }
+
+void bat_pcg_init(int64_t n, int m, const double* B, double* X, double* R, double* partial, void* sc, cudaStream_t s) {
+  { bat_init<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, B, X, R, partial); note_launch(); }
+  { bat_finish_bb<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_pcg_rz(int64_t n, int m, const double* R, const double* Z, const double* Rold, int flexible, int first,
+                double* partial, void* sc, cudaStream_t s) {
+  { bat_dot_rz<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, R, Z, Rold, flexible, partial); note_launch(); }
+  { bat_finish_rz<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m, first, flexible); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_pcg_update_p(int64_t n, int m, const double* Z, double* P, const void* sc, int first, cudaStream_t s) {
+  { bat_update_p<<<vec_grid(n * m), 256, 0, s>>>(n, m, Z, P, (const BatchScalars*)sc, first); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_pcg_pq(int64_t n, int m, const double* P, const double* Q, double* partial, void* sc, cudaStream_t s) {
+  { bat_dot<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, P, Q, partial); note_launch(); }
+  { bat_finish_pq<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_pcg_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, double* Rold,
+                       int flexible, double* partial, void* sc, double tol2, int force, cudaStream_t s) {
+  { bat_update_xr<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, P, Q, X, R, Rold, flexible, (const BatchScalars*)sc, partial); note_launch(); }
+  { bat_finish_rr<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m, tol2, force); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+}  // namespace giamg

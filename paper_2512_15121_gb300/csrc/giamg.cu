@@ -25,6 +25,7 @@ Hierarchy::~Hierarchy() {
   for (Level* L : lev) delete L;
   lev.clear();
   if (h_sc) cudaFreeHost(h_sc);
+  if (h_bsc) cudaFreeHost(h_bsc);
   for (cudaEvent_t e : prof.ev) cudaEventDestroy(e);
 }
 
@@ -61,10 +62,12 @@ void prof_end(Hierarchy& H, int rec, double bytes) {
   R.bytes = bytes;
   GIAMG_CUDA(cudaEventRecord(H.prof.ev[R.e1], H.stream));
 }
-// algorithmic bytes of one CSR row-kernel launch: matrix (values, columns, row pointers), the
-// gathered vector counted once, the output, and `vecs` further streamed vectors
+// algorithmic bytes of one CSR row-kernel launch: matrix (values, column indices or one template
+// id per row, row pointers), the gathered vector counted once, the output, and `vecs` further
+// streamed vectors
 double row_bytes(const DCSR& A, int vsize, int vecs) {
-  return (double)A.nnz * (vsize + 4) + 8.0 * (A.n + 1) + (double)vsize * A.n * (2 + vecs);
+  const double index = A.pat.on ? 4.0 * A.n : 4.0 * A.nnz;
+  return (double)A.nnz * vsize + index + 8.0 * (A.n + 1) + (double)vsize * A.n * (2 + vecs);
 }
 
 // copy count elements of a caller array (host or device) into a new device buffer
@@ -112,7 +115,7 @@ const double* vcycle64(Hierarchy& H, const std::vector<LevelExtra>& ex, int l, c
   cudaStream_t s = H.stream;
   if (L.kind == GIAMG_LEVEL_COARSEST) {  // direct solve of the coarsest matrix
     const int pr = prof_begin(H, kProfCoarsest);
-    chol_solve(L.L.get(), L.nc, b, L.x.get(), s);
+    inverse_apply(L.Ainv.get(), L.nc, b, L.x.get(), s);
     prof_end(H, pr, 8.0 * L.nc * L.nc + 16.0 * L.nc);
     return L.x.get();
   }
@@ -159,7 +162,7 @@ const float* vcycle32(Hierarchy& H, const std::vector<LevelExtra>& ex, int l, co
   cudaStream_t s = H.stream;
   if (L.kind == GIAMG_LEVEL_COARSEST) {
     const int pr = prof_begin(H, kProfCoarsest);
-    chol_solve32(L.L.get(), L.nc, b, L.x32.get(), s);
+    inverse_apply32(L.Ainv.get(), L.nc, b, L.x32.get(), s);
     prof_end(H, pr, 8.0 * L.nc * L.nc + 8.0 * L.nc);
     return L.x32.get();
   }
@@ -295,6 +298,18 @@ __global__ void csr_check_kernel(int64_t n, const int64_t* __restrict__ rp, cons
   }
 }
 
+// Host copy of a caller array.  Device arrays are read on the handle's stream, so an input the
+// caller produced on that stream (and not yet finished) is read after it is written.
+void read_host(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t s) {
+  if (!bytes) return;
+  if (!dev) {
+    std::memcpy(dst, src, bytes);
+    return;
+  }
+  GIAMG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+}
+
 Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int32_t n_elem,
                 const int32_t* elem_dof, const int32_t* elem_order, const double* coords, const giamg_options* optp,
                 void* stream) {
@@ -308,6 +323,10 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   GIAMG_CHECK(opt.max_levels >= 1 && opt.max_levels <= 64, GIAMG_ERR_ARG, "max_levels must be in [1, 64]");
   GIAMG_CHECK(opt.lanczos_steps >= 1, GIAMG_ERR_ARG, "lanczos_steps must be >= 1");
   GIAMG_CHECK(opt.precision == 0 || opt.precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 3, GIAMG_ERR_ARG, "row_form must be in 0..3");
+  GIAMG_CHECK(opt.row_threads == 0 || opt.row_threads == 4 || opt.row_threads == 8 || opt.row_threads == 16 ||
+                  opt.row_threads == 32,
+              GIAMG_ERR_ARG, "row_threads must be 0, 4, 8, 16 or 32");
   const bool dev = opt.device_ptrs != 0;
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -316,8 +335,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   if (n_elem > 0) {
     GIAMG_CHECK(elem_order != nullptr, GIAMG_ERR_ARG, "elem_order is required when n_elem > 0");
     std::vector<int32_t> ord(n_elem);
-    if (dev) GIAMG_CUDA(cudaMemcpy(ord.data(), elem_order, sizeof(int32_t) * n_elem, cudaMemcpyDeviceToHost));
-    else std::memcpy(ord.data(), elem_order, sizeof(int32_t) * n_elem);
+    read_host(ord.data(), elem_order, sizeof(int32_t) * n_elem, dev, s);
     p = ord[0];
     for (int32_t e = 0; e < n_elem; ++e)
       GIAMG_CHECK(ord[e] == p, GIAMG_ERR_ORDER, "element orders are not uniform");
@@ -327,8 +345,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     GIAMG_CHECK(elem_dof == nullptr || n_elem == 0, GIAMG_ERR_ARG, "n_elem must be positive with elem_dof");
   }
   int64_t nnz = 0;
-  if (dev) GIAMG_CUDA(cudaMemcpy(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
-  else nnz = row_ptr[n];
+  read_host(&nnz, row_ptr + n, sizeof(int64_t), dev, s);
   GIAMG_CHECK(nnz >= n, GIAMG_ERR_ARG, "row_ptr[n] smaller than n (a diagonal is needed in every row)");
 
   Ctx* C = new Ctx();
@@ -372,8 +389,8 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     if (coords && p >= 1 && n_elem > 0 && elem_dof) {
       std::vector<double> ch((size_t)n * 3);
       std::vector<int32_t> mh((size_t)n_elem * nl0);
-      GIAMG_CUDA(cudaMemcpy(ch.data(), coords, sizeof(double) * 3 * n, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-      GIAMG_CUDA(cudaMemcpy(mh.data(), elem_dof, sizeof(int32_t) * mh.size(), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      read_host(ch.data(), coords, sizeof(double) * 3 * n, dev, s);
+      read_host(mh.data(), elem_dof, sizeof(int32_t) * mh.size(), dev, s);
       check_coords(ch.data(), mh, n_elem, p, n);
     }
     L0->dinv.alloc(n, s);
@@ -430,11 +447,19 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     csr_to_dense_cm(Lc.A, Lc.L.get(), s);
     GIAMG_CHECK(cholesky_factor(Lc.L.get(), Lc.nc, s) == GIAMG_OK, GIAMG_ERR_NOT_SPD,
                 "coarsest matrix is not positive definite");
+    Lc.Ainv.alloc((size_t)Lc.nc * Lc.nc, s);
+    chol_inverse(Lc.L.get(), Lc.nc, Lc.Ainv.get(), s);
     // smoother bounds, FP32 copies, work vectors
     C->ex.resize(H.lev.size());
     for (size_t l = 0; l < H.lev.size(); ++l) {
       Level& L = *H.lev[l];
       csr_to32(L.A, s);
+      if (opt.compress_patterns) {
+        pattern_build(L.A, s, 1 << 16, 1 << 24);
+        groups_build(L.A, s, 1 << 22);
+      }
+      if (opt.autotune) tune_rows(L.A, s);
+      else choose_rows(L.A, opt.row_form, opt.row_threads);
       alloc_work(L, s);
       if (L.kind != GIAMG_LEVEL_COARSEST) {
         L.rho = lanczos_rho(L.A, opt.lanczos_steps, opt.hash_kind, H);
@@ -565,6 +590,173 @@ int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, doubl
   return GIAMG_OK;
 }
 
+// ------------------------------------------------------------------ multi-right-hand-side solve
+void alloc_batch(Hierarchy& H, int m) {
+  if (H.bm >= m) return;
+  cudaStream_t s = H.stream;
+  for (Level* Lp : H.lev) {
+    Level& L = *Lp;
+    const size_t nm = (size_t)std::max<int64_t>(L.A.n, 1) * m;
+    L.bx.alloc(nm, s); L.bx2.alloc(nm, s); L.bb.alloc(nm, s); L.br.alloc(nm, s); L.bd.alloc(nm, s);
+    L.bx32.alloc(nm, s); L.bx232.alloc(nm, s); L.bb32.alloc(nm, s); L.br32.alloc(nm, s); L.bd32.alloc(nm, s);
+    if (L.kind == GIAMG_LEVEL_P) {
+      const size_t pm = (size_t)L.n_elem * (L.q + 1) * (L.q + 1) * (L.q + 1) * m;
+      L.bpart.alloc(pm, s);
+      L.bpart32.alloc(pm, s);
+    }
+    L.bm = m;
+  }
+  const size_t nm = (size_t)H.n * m;
+  H.bR.alloc(nm, s); H.bZ.alloc(nm, s); H.bP.alloc(nm, s); H.bQ.alloc(nm, s); H.bRold.alloc(nm, s);
+  H.bX.alloc(nm, s); H.bB.alloc(nm, s);
+  H.bpartial.alloc((size_t)2 * batch_reduction_blocks() * 32, s);
+  H.bsc.alloc(batch_scalars_bytes(), s);
+  if (!H.h_bsc) GIAMG_CUDA(cudaMallocHost(&H.h_bsc, batch_scalars_bytes()));
+  H.bm = m;
+}
+
+// Algorithm 1 on m columns at once (same smoother polynomial and transfers as vcycle64)
+const double* bvcycle64(Hierarchy& H, const std::vector<LevelExtra>& ex, int l, int m, const double* b) {
+  Level& L = *H.lev[l];
+  cudaStream_t s = H.stream;
+  if (L.kind == GIAMG_LEVEL_COARSEST) {
+    bat_inverse(L.Ainv.get(), L.nc, m, b, L.bx.get(), s);
+    return L.bx.get();
+  }
+  const Cheb& c = ex[l].cheb;
+  const int k = (int)c.c1.size();
+  double* x = L.bx.get();
+  double* x2 = L.bx2.get();
+  const int64_t n = L.A.n;
+  bat_cheb_first64(n, m, b, L.dinv.get(), c.c2[0], x, L.bd.get(), s);
+  for (int j = 1; j < k; ++j) {
+    bat_rows_launch64(L.A, m, 2, L.A.v.get(), x, b, x2, L.bd.get(), L.dinv.get(), c.c1[j], c.c2[j], s);
+    std::swap(x, x2);
+  }
+  bat_rows_launch64(L.A, m, 1, L.A.v.get(), x, b, L.br.get(), nullptr, nullptr, 0.0, 0.0, s);
+  Level& C = *H.lev[l + 1];
+  if (L.kind == GIAMG_LEVEL_P) bat_p_restrict(L, m, L.br.get(), C.bb.get(), L.bpart.get(), s);
+  else bat_rows_launch64(L.R, m, 0, L.R.v.get(), L.br.get(), nullptr, C.bb.get(), nullptr, nullptr, 0.0, 0.0, s);
+  const double* xc = bvcycle64(H, ex, l + 1, m, C.bb.get());
+  if (L.kind == GIAMG_LEVEL_P) bat_p_prolong(L, m, xc, x, s);
+  else bat_rows_launch64(L.P, m, 3, L.P.v.get(), xc, nullptr, x, nullptr, nullptr, 0.0, 0.0, s);
+  for (int j = 0; j < k; ++j) {
+    bat_rows_launch64(L.A, m, 2, L.A.v.get(), x, b, x2, L.bd.get(), L.dinv.get(), c.c1[j], c.c2[j], s);
+    std::swap(x, x2);
+  }
+  return x;
+}
+
+const float* bvcycle32(Hierarchy& H, const std::vector<LevelExtra>& ex, int l, int m, const float* b) {
+  Level& L = *H.lev[l];
+  cudaStream_t s = H.stream;
+  if (L.kind == GIAMG_LEVEL_COARSEST) {
+    bat_inverse32(L.Ainv.get(), L.nc, m, b, L.bx32.get(), s);
+    return L.bx32.get();
+  }
+  const Cheb& c = ex[l].cheb;
+  const int k = (int)c.c1.size();
+  float* x = L.bx32.get();
+  float* x2 = L.bx232.get();
+  const int64_t n = L.A.n;
+  bat_cheb_first32(n, m, b, L.dinv32.get(), (float)c.c2[0], x, L.bd32.get(), s);
+  for (int j = 1; j < k; ++j) {
+    bat_rows_launch32(L.A, m, 2, L.A.v32.get(), x, b, x2, L.bd32.get(), L.dinv32.get(), (float)c.c1[j], (float)c.c2[j], s);
+    std::swap(x, x2);
+  }
+  bat_rows_launch32(L.A, m, 1, L.A.v32.get(), x, b, L.br32.get(), nullptr, nullptr, 0.f, 0.f, s);
+  Level& C = *H.lev[l + 1];
+  if (L.kind == GIAMG_LEVEL_P) bat_p_restrict32(L, m, L.br32.get(), C.bb32.get(), L.bpart32.get(), s);
+  else bat_rows_launch32(L.R, m, 0, L.R.v32.get(), L.br32.get(), nullptr, C.bb32.get(), nullptr, nullptr, 0.f, 0.f, s);
+  const float* xc = bvcycle32(H, ex, l + 1, m, C.bb32.get());
+  if (L.kind == GIAMG_LEVEL_P) bat_p_prolong32(L, m, xc, x, s);
+  else bat_rows_launch32(L.P, m, 3, L.P.v32.get(), xc, nullptr, x, nullptr, nullptr, 0.f, 0.f, s);
+  for (int j = 0; j < k; ++j) {
+    bat_rows_launch32(L.A, m, 2, L.A.v32.get(), x, b, x2, L.bd32.get(), L.dinv32.get(), (float)c.c1[j], (float)c.c2[j], s);
+    std::swap(x, x2);
+  }
+  return x;
+}
+
+const double* apply_bvcycle(Ctx& C, int precision, int m, const double* r) {
+  Hierarchy& H = *C.H;
+  Level& L0 = *H.lev[0];
+  if (precision == 0) return bvcycle64(H, C.ex, 0, m, r);
+  bat_to32(L0.A.n * m, r, L0.bb32.get(), H.stream);
+  const float* z32 = bvcycle32(H, C.ex, 0, m, L0.bb32.get());
+  bat_to64(L0.A.n * m, z32, H.bZ.get(), H.stream);
+  return H.bZ.get();
+}
+
+int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double* B_in, double* X_out, double rtol,
+                     int* iters, double* relres) {
+  Hierarchy& H = *C.H;
+  cudaStream_t s = H.stream;
+  const int64_t n = H.n;
+  GIAMG_CHECK(m >= 1 && m <= 32, GIAMG_ERR_ARG, "m must be in [1, 32]");
+  GIAMG_CHECK(B_in && X_out, GIAMG_ERR_ARG, "B and X are required");
+  GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+  GIAMG_CHECK(rtol >= 0.0, GIAMG_ERR_ARG, "rtol must be non-negative");
+  alloc_batch(H, m);
+  const bool dev = H.opt.device_ptrs != 0;
+  const double* Bd = B_in;
+  double* Xd = X_out;
+  if (!dev) {
+    GIAMG_CUDA(cudaMemcpyAsync(H.bB.get(), B_in, sizeof(double) * n * m, cudaMemcpyHostToDevice, s));
+    Bd = H.bB.get();
+    Xd = H.bX.get();
+  }
+  Level& L0 = *H.lev[0];
+  const int flexible = precision ? 1 : 0;
+  BatchScalarsHost* hs = (BatchScalarsHost*)H.h_bsc;
+  void* sc = H.bsc.get();
+  double* partial = H.bpartial.get();
+  const double tol2 = rtol * rtol;
+  const int force = force_iters > 0 ? 1 : 0;
+  bat_pcg_init(n, m, Bd, Xd, H.bR.get(), partial, sc, s);
+  GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> bb(m);
+  std::vector<int> its(m, 0);
+  for (int j = 0; j < m; ++j) bb[j] = hs->bb[j];
+  int active = 0;
+  for (int j = 0; j < m; ++j) active += hs->active[j];
+  const int limit = force ? force_iters : H.opt.max_iter;
+  int it = 0;
+  bool breakdown = false;
+  while (active > 0 && it < limit) {
+    const double* Z = apply_bvcycle(C, precision, m, H.bR.get());
+    bat_pcg_rz(n, m, H.bR.get(), Z, H.bRold.get(), flexible, it == 0 ? 1 : 0, partial, sc, s);
+    bat_pcg_update_p(n, m, Z, H.bP.get(), sc, it == 0 ? 1 : 0, s);
+    bat_rows_launch64(L0.A, m, 0, L0.A.v.get(), H.bP.get(), nullptr, H.bQ.get(), nullptr, nullptr, 0.0, 0.0, s);
+    bat_pcg_pq(n, m, H.bP.get(), H.bQ.get(), partial, sc, s);
+    bat_pcg_update_xr(n, m, H.bP.get(), H.bQ.get(), Xd, H.bR.get(), H.bRold.get(), flexible, partial, sc, tol2, force, s);
+    const std::vector<int> was(hs->active, hs->active + m);
+    GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    ++it;
+    active = 0;
+    for (int j = 0; j < m; ++j) {
+      if (was[j]) its[j] = it;
+      if (hs->status[j] != 0) breakdown = true;
+      active += hs->active[j];
+    }
+    if (breakdown) break;
+  }
+  if (!dev) GIAMG_CUDA(cudaMemcpyAsync(X_out, Xd, sizeof(double) * n * m, cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  bool unconverged = false;
+  for (int j = 0; j < m; ++j) {
+    const double rr = bb[j] > 0.0 ? std::sqrt(hs->rr[j] / bb[j]) : 0.0;
+    if (iters) iters[j] = its[j];
+    if (relres) relres[j] = rr;
+    if (!force && !(rr <= rtol)) unconverged = true;
+  }
+  if (breakdown) throw Error{GIAMG_ERR_BREAKDOWN, "CG breakdown in at least one column"};
+  if (unconverged) throw Error{GIAMG_ERR_MAXITER, "max_iter reached before rtol in at least one column"};
+  return GIAMG_OK;
+}
+
 Ctx* ctx_of(giamg_handle h) {
   GIAMG_CHECK(h != nullptr, GIAMG_ERR_ARG, "NULL handle");
   return reinterpret_cast<Ctx*>(h);
@@ -621,6 +813,10 @@ void giamg_default_options(giamg_options* o) {
   o->force_iters = 0;
   o->device_ptrs = 0;
   o->hash_kind = 0;
+  o->compress_patterns = 1;
+  o->autotune = 0;
+  o->row_form = 0;
+  o->row_threads = 0;
 }
 
 int giamg_setup(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int32_t n_elem,
@@ -645,6 +841,18 @@ int giamg_solve(giamg_handle h, const double* b, double* x, double rtol, int* it
 int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double* b, double* x, double rtol, int* iters,
                    double* relres) {
   return guarded([&] { return solve_impl(*ctx_of(h), precision, force_iters, b, x, rtol, iters, relres); });
+}
+
+int giamg_solve_batch(giamg_handle h, int m, const double* B, double* X, double rtol, int* iters, double* relres) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    return solve_batch_impl(C, C.H->opt.precision, C.H->opt.force_iters, m, B, X, rtol, iters, relres);
+  });
+}
+
+int giamg_solve_batch_ex(giamg_handle h, int precision, int force_iters, int m, const double* B, double* X, double rtol,
+                         int* iters, double* relres) {
+  return guarded([&] { return solve_batch_impl(*ctx_of(h), precision, force_iters, m, B, X, rtol, iters, relres); });
 }
 
 int giamg_solve_stats(giamg_handle h, double* hist, int len, double* true_relres) {
@@ -720,6 +928,27 @@ int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_ptr, int32
     copy_out(col_idx, L.P.ci.get(), (size_t)L.P.nnz, dev, s);
     copy_out(val, L.P.v.get(), (size_t)L.P.nnz, dev, s);
     GIAMG_CUDA(cudaStreamSynchronize(s));
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_templates(giamg_handle h, int level, int64_t* n_templates, int64_t* n_offsets) {
+  return guarded([&] {
+    Level& L = level_of(*ctx_of(h), level);
+    if (n_templates) *n_templates = L.A.pat.on ? L.A.pat.n_templates : 0;
+    if (n_offsets) *n_offsets = L.A.pat.on ? L.A.pat.n_offsets : 0;
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern) {
+  return guarded([&] {
+    Level& L = level_of(*ctx_of(h), level);
+    GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+    const RowVariant& v = precision == 0 ? L.A.var64 : L.A.var32;
+    const double avg = L.A.n ? (double)L.A.nnz / L.A.n : 0.0;
+    if (threads_per_row) *threads_per_row = v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
+    if (pattern) *pattern = v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
     return GIAMG_OK;
   });
 }

@@ -75,12 +75,43 @@ struct DBuf {
   T* get() const { return p; }
 };
 
+// Repeated row patterns: row i's columns are i + toff[tptr[t] + k], k < len(row i), t = tid[i].
+struct Pattern {
+  bool on = false;
+  int64_t n_templates = 0, n_offsets = 0;
+  DBuf<int32_t> tid;
+  DBuf<int64_t> tptr;
+  DBuf<int32_t> toff;
+};
+
+// Row groups: rows with identical column sets; group g holds rows grow[rptr[g] .. rptr[g+1]) and
+// columns gcol[gptr[g] .. gptr[g+1]).
+struct Groups {
+  bool on = false;
+  int64_t n_groups = 0, n_cols = 0;
+  int cmax = 0;
+  DBuf<int64_t> gptr, rptr;
+  DBuf<int32_t> gcol, grow;
+};
+
+// Row-kernel variant chosen for a matrix: threads per row and whether the pattern form is used
+// (one choice per value precision; set by the setup-time tuner, or from the row length).
+struct RowVariant {
+  int tpr = 0;       // 0: not tuned, choose from the average row length
+  bool pat = false;
+  int unroll = 2;    // independent load chains per thread and step (pattern form: 2 or 4)
+  bool group = false;  // row-group form (one CTA per group, x gathered once into shared memory)
+};
+
 struct DCSR {
   int64_t n = 0, m = 0, nnz = 0;
   DBuf<int64_t> rp;
   DBuf<int32_t> ci;
   DBuf<double> v;
   DBuf<float> v32;
+  Pattern pat;  // optional compressed column structure for the row kernels
+  Groups grp;   // optional row groups with identical column sets
+  RowVariant var64, var32;
 };
 
 // ------------------------------------------------------------------ hierarchy
@@ -114,11 +145,16 @@ struct Level {
 
   // coarsest level
   int64_t nc = 0;
-  DBuf<double> L;  // dense Cholesky factor, column-major lower triangle, nc x nc
+  DBuf<double> L;     // dense Cholesky factor, column-major lower triangle, nc x nc
+  DBuf<double> Ainv;  // A^-1 formed from the factor at setup, nc x nc
 
   // work vectors (FP64 and FP32 copies)
   DBuf<double> x, x2, b, r, d;
   DBuf<float> x32, x232, b32, r32, d32;
+  // multi-right-hand-side work blocks (n x bm, row-major), allocated on first use
+  int bm = 0;
+  DBuf<double> bx, bx2, bb, br, bd, bpart;
+  DBuf<float> bx32, bx232, bb32, br32, bd32, bpart32;
 };
 
 struct Scalars {  // PCG scalars kept on the device
@@ -164,6 +200,11 @@ struct Hierarchy {
   int last_iters = 0;
   double last_true_relres = -1.0;
   Prof prof;
+  // multi-right-hand-side PCG work (n x bm)
+  int bm = 0;
+  DBuf<double> bR, bZ, bP, bQ, bRold, bX, bB, bpartial;
+  DBuf<unsigned char> bsc;
+  void* h_bsc = nullptr;
   ~Hierarchy();
 };
 
@@ -205,6 +246,10 @@ void h_prolong32(const Level& L, const float* ec, float* xf, cudaStream_t s);
 int cholesky_factor(double* Lcm, int64_t nc, cudaStream_t s);  // returns GIAMG_OK or NOT_SPD
 void chol_solve(const double* Lcm, int64_t nc, const double* b, double* x, cudaStream_t s);
 void chol_solve32(const double* Lcm, int64_t nc, const float* b, float* x, cudaStream_t s);
+// A^-1 = L^-T L^-1 by the same substitutions applied to the unit vectors (setup), and its use
+void chol_inverse(const double* Lcm, int64_t nc, double* Ainv, cudaStream_t s);
+void inverse_apply(const double* Ainv, int64_t nc, const double* b, double* x, cudaStream_t s);
+void inverse_apply32(const double* Ainv, int64_t nc, const float* b, float* x, cudaStream_t s);
 
 // vectors
 void dot_partial(int64_t n, const double* x, const double* y, double* partial, cudaStream_t s);
@@ -229,6 +274,36 @@ void pcg_update_xr(int64_t n, const double* p, const double* q, double* x, doubl
 void pcg_finish_rr(Scalars* sc, const double* partial, cudaStream_t s);
 void reduce_to(const double* partial, double* out, cudaStream_t s);
 
+// multi-right-hand-side kernels (batch_kernels.cu); modes: 0 SpMM, 1 residual, 2 Chebyshev, 3 add
+void bat_rows_launch64(const DCSR& A, int m, int mode, const double* val, const double* X, const double* B, double* Y,
+                       double* D, const double* dinv, double c1, double c2, cudaStream_t s);
+void bat_rows_launch32(const DCSR& A, int m, int mode, const float* val, const float* X, const float* B, float* Y,
+                       float* D, const float* dinv, float c1, float c2, cudaStream_t s);
+void bat_p_restrict(const Level& L, int m, const double* rf, double* rc, double* part, cudaStream_t s);
+void bat_p_restrict32(const Level& L, int m, const float* rf, float* rc, float* part, cudaStream_t s);
+void bat_p_prolong(const Level& L, int m, const double* ec, double* xf, cudaStream_t s);
+void bat_p_prolong32(const Level& L, int m, const float* ec, float* xf, cudaStream_t s);
+void bat_inverse(const double* Ainv, int64_t nc, int m, const double* B, double* X, cudaStream_t s);
+void bat_inverse32(const double* Ainv, int64_t nc, int m, const float* B, float* X, cudaStream_t s);
+void bat_cheb_first64(int64_t n, int m, const double* B, const double* dinv, double c2, double* X, double* D, cudaStream_t s);
+void bat_cheb_first32(int64_t n, int m, const float* B, const float* dinv, float c2, float* X, float* D, cudaStream_t s);
+void bat_to32(int64_t count, const double* x, float* y, cudaStream_t s);
+void bat_to64(int64_t count, const float* x, double* y, cudaStream_t s);
+size_t batch_scalars_bytes();
+int batch_reduction_blocks();
+void bat_pcg_init(int64_t n, int m, const double* B, double* X, double* R, double* partial, void* sc, cudaStream_t s);
+void bat_pcg_rz(int64_t n, int m, const double* R, const double* Z, const double* Rold, int flexible, int first,
+                double* partial, void* sc, cudaStream_t s);
+void bat_pcg_update_p(int64_t n, int m, const double* Z, double* P, const void* sc, int first, cudaStream_t s);
+void bat_pcg_pq(int64_t n, int m, const double* P, const double* Q, double* partial, void* sc, cudaStream_t s);
+void bat_pcg_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, double* Rold,
+                       int flexible, double* partial, void* sc, double tol2, int force, cudaStream_t s);
+// host view of the batched CG scalars (layout shared with batch_kernels.cu)
+struct BatchScalarsHost {
+  double rho[32], pq[32], alpha[32], beta[32], rr[32], bb[32];
+  int status[32], active[32];
+};
+
 // ------------------------------------------------------------------ setup kernels
 uint32_t host_hash(int kind, int64_t i);
 // exclusive scan of int32 flags/counts into int64 offsets (out has n+1 entries)
@@ -242,6 +317,14 @@ void csr_transpose(const DCSR& A, DCSR& T, cudaStream_t s);
 // index with separately rounded products (matches a sequential Gustavson product bit for bit)
 void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 void csr_to32(DCSR& A, cudaStream_t s);
+// time the row-kernel variants on A (both precisions) and keep the fastest in A.var64 / A.var32
+void tune_rows(DCSR& A, cudaStream_t s);
+// set A.var64 / A.var32 from forced options or the defaults measured best inside the solve
+void choose_rows(DCSR& A, int form, int threads);
+// detect row groups with identical column sets (exact; leaves A.grp off if not worthwhile)
+bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups);
+// detect repeated row patterns (exact; returns false and leaves A.pat off if not worthwhile)
+bool pattern_build(DCSR& A, cudaStream_t s, int64_t max_templates, int64_t max_offsets);
 // diagonal inverse (checks positivity; returns false if a diagonal entry is <= 0 or missing)
 bool diag_inverse(const DCSR& A, double* dinv, float* dinv32, cudaStream_t s);
 // Lanczos estimate of lambda_max(D^-1/2 A D^-1/2)

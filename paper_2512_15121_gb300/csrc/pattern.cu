@@ -1,0 +1,396 @@
+// pattern.cu -- detection of repeated row patterns in a CSR matrix ("pattern-compressed CSR").
+//
+// In an assembled high-order operator on a mesh with a regular numbering, row i's columns are
+// i + o_1, ..., i + o_L for one of a few hundred offset lists (the position of the node inside
+// its element decides the list).  Storing one template id per row instead of one column index
+// per nonzero removes the index stream from the SpMV: for FP32 values that halves the bytes
+// the kernel must read.  Detection is exact: every row is compared with its template's
+// representative; any mismatch, or too many templates, keeps the plain CSR path.  Values, row
+// pointers and columns stay as they are (the setup and export paths use them).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace giamg {
+
+namespace {
+
+constexpr uint64_t kEmpty = ~0ull;
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+inline unsigned blocks(int64_t work) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 65535));
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// hash of the row's length and columns, relative to the row index (patterns) or absolute
+// (row groups with identical column sets)
+__global__ void row_hash(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int absolute,
+                         uint64_t* __restrict__ h) {
+  GRID_STRIDE(i, n) {
+    uint64_t z = mix64((uint64_t)(rp[i + 1] - rp[i]) + 0x9E3779B97F4A7C15ULL);
+    const int64_t base = absolute ? 0 : i;
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t) z = mix64(z ^ (uint64_t)(uint32_t)((int64_t)ci[t] - base));
+    h[i] = z == kEmpty ? z - 1 : z;
+  }
+}
+
+// row groups: every row's columns equal its group representative's columns exactly
+__global__ void verify_groups(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const int32_t* __restrict__ gid, const int64_t* __restrict__ gptr,
+                              const int32_t* __restrict__ gcol, int* __restrict__ bad) {
+  GRID_STRIDE(i, n) {
+    const int32_t g = gid[i];
+    if (g < 0) {
+      atomicAdd(bad, 1);
+      continue;
+    }
+    const int64_t len = rp[i + 1] - rp[i];
+    if (len != gptr[g + 1] - gptr[g]) {
+      atomicAdd(bad, 1);
+      continue;
+    }
+    for (int64_t k = 0; k < len; ++k)
+      if (ci[rp[i] + k] != gcol[gptr[g] + k]) {
+        atomicAdd(bad, 1);
+        break;
+      }
+  }
+}
+
+__global__ void group_fill_cols(int64_t G, const uint32_t* __restrict__ rep_sorted, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ ci, const int64_t* __restrict__ gptr,
+                                int32_t* __restrict__ gcol) {
+  GRID_STRIDE(g, G) {
+    const int64_t r = rep_sorted[g];
+    for (int64_t k = 0; k < gptr[g + 1] - gptr[g]; ++k) gcol[gptr[g] + k] = ci[rp[r] + k];
+  }
+}
+
+__global__ void group_count_rows(int64_t n, const int32_t* __restrict__ gid, int32_t* __restrict__ cnt) {
+  GRID_STRIDE(i, n) atomicAdd(&cnt[gid[i]], 1);
+}
+__global__ void group_fill_rows(int64_t n, const int32_t* __restrict__ gid, const int64_t* __restrict__ rptr,
+                                int32_t* __restrict__ fill, int32_t* __restrict__ grow) {
+  GRID_STRIDE(i, n) {
+    const int32_t g = gid[i];
+    grow[rptr[g] + atomicAdd(&fill[g], 1)] = (int32_t)i;
+  }
+}
+__global__ void group_sort_rows(int64_t G, const int64_t* __restrict__ rptr, int32_t* __restrict__ grow) {
+  GRID_STRIDE(g, G) {
+    const int64_t s = rptr[g], e = rptr[g + 1];
+    for (int64_t i = s + 1; i < e; ++i) {
+      const int32_t v = grow[i];
+      int64_t j = i - 1;
+      while (j >= s && grow[j] > v) {
+        grow[j + 1] = grow[j];
+        --j;
+      }
+      grow[j + 1] = v;
+    }
+  }
+}
+
+// open-addressing table hash -> slot; rep[slot] = smallest row with that hash
+// The table holds at most max_distinct keys (a quarter of its slots); once more distinct keys
+// have been seen every later insert gives up, so a matrix without repetition costs one pass.
+__global__ void table_insert(int64_t n, const uint64_t* __restrict__ h, unsigned long long* keys,
+                             int* rep, int64_t cap, int64_t max_distinct, int* distinct, int* overflow) {
+  GRID_STRIDE(i, n) {
+    if (*(volatile int*)distinct > max_distinct) {
+      *(volatile int*)overflow = 1;
+      continue;
+    }
+    const uint64_t k = h[i];
+    uint64_t s = mix64(k) & (uint64_t)(cap - 1);
+    bool done = false;
+    const int64_t limit = cap < 4096 ? cap : 4096;
+    for (int64_t probe = 0; probe < limit && !done; ++probe) {
+      const unsigned long long prev = atomicCAS(&keys[s], (unsigned long long)kEmpty, (unsigned long long)k);
+      if (prev == kEmpty || prev == k) {
+        if (prev == kEmpty) atomicAdd(distinct, 1);
+        atomicMin(&rep[s], (int)i);
+        done = true;
+      } else {
+        s = (s + 1) & (uint64_t)(cap - 1);
+      }
+    }
+    if (!done) atomicAdd(overflow, 1);
+  }
+}
+
+__global__ void table_find(int64_t n, const uint64_t* __restrict__ h, const unsigned long long* __restrict__ keys,
+                           const int* __restrict__ slot_tid, int64_t cap, int32_t* __restrict__ tid) {
+  GRID_STRIDE(i, n) {
+    const uint64_t k = h[i];
+    uint64_t s = mix64(k) & (uint64_t)(cap - 1);
+    int32_t t = -1;
+    for (int64_t probe = 0; probe < cap; ++probe) {
+      if (keys[s] == k) {
+        t = slot_tid[s];
+        break;
+      }
+      s = (s + 1) & (uint64_t)(cap - 1);
+    }
+    tid[i] = t;
+  }
+}
+
+__global__ void occupied(int64_t cap, const unsigned long long* __restrict__ keys, int32_t* __restrict__ flag) {
+  GRID_STRIDE(s, cap) flag[s] = keys[s] != kEmpty ? 1 : 0;
+}
+
+// representatives of occupied slots, compacted; key for sorting by representative row
+__global__ void compact_reps(int64_t cap, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                             const int* __restrict__ rep, uint32_t* __restrict__ rep_key, int64_t* __restrict__ slot_of) {
+  GRID_STRIDE(s, cap) {
+    if (flag[s]) {
+      rep_key[pos[s]] = (uint32_t)rep[s];
+      slot_of[pos[s]] = s;
+    }
+  }
+}
+
+__global__ void assign_tid(int64_t T, const int64_t* __restrict__ slot_sorted, int* __restrict__ slot_tid) {
+  GRID_STRIDE(t, T) slot_tid[slot_sorted[t]] = (int)t;
+}
+
+__global__ void template_len(int64_t T, const uint32_t* __restrict__ rep_sorted, const int64_t* __restrict__ rp,
+                             int32_t* __restrict__ len) {
+  GRID_STRIDE(t, T) len[t] = (int32_t)(rp[rep_sorted[t] + 1] - rp[rep_sorted[t]]);
+}
+
+__global__ void template_fill(int64_t T, const uint32_t* __restrict__ rep_sorted, const int64_t* __restrict__ rp,
+                              const int32_t* __restrict__ ci, const int64_t* __restrict__ tptr,
+                              int32_t* __restrict__ toff) {
+  GRID_STRIDE(t, T) {
+    const int64_t r = rep_sorted[t];
+    for (int64_t k = 0; k < tptr[t + 1] - tptr[t]; ++k) toff[tptr[t] + k] = (int32_t)((int64_t)ci[rp[r] + k] - r);
+  }
+}
+
+// every row must equal its template exactly
+__global__ void verify(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const int32_t* __restrict__ tid, const int64_t* __restrict__ tptr,
+                       const int32_t* __restrict__ toff, int* __restrict__ bad) {
+  GRID_STRIDE(i, n) {
+    const int32_t t = tid[i];
+    if (t < 0) {
+      atomicAdd(bad, 1);
+      continue;
+    }
+    const int64_t len = rp[i + 1] - rp[i];
+    if (len != tptr[t + 1] - tptr[t]) {
+      atomicAdd(bad, 1);
+      continue;
+    }
+    for (int64_t k = 0; k < len; ++k)
+      if ((int64_t)ci[rp[i] + k] - i != toff[tptr[t] + k]) {
+        atomicAdd(bad, 1);
+        break;
+      }
+  }
+}
+
+}  // namespace
+
+bool pattern_build(DCSR& A, cudaStream_t s, int64_t max_templates, int64_t max_offsets) {
+  Pattern& P = A.pat;
+  P.on = false;
+  const int64_t n = A.n;
+  if (n < 1024 || A.nnz == 0) return false;  // small levels gain nothing
+  int64_t cap = 1;
+  while (cap < 4 * std::min<int64_t>(n, max_templates + 1)) cap <<= 1;
+  DBuf<uint64_t> h;
+  DBuf<unsigned long long> keys;
+  DBuf<int> rep, ovf, slot_tid, bad, distinct;
+  h.alloc(n, s);
+  keys.alloc(cap, s);
+  rep.alloc(cap, s);
+  ovf.alloc(1, s);
+  GIAMG_CUDA(cudaMemsetAsync(keys.get(), 0xff, sizeof(unsigned long long) * cap, s));
+  GIAMG_CUDA(cudaMemsetAsync(rep.get(), 0x7f, sizeof(int) * cap, s));
+  ovf.zero(s);
+  distinct.alloc(1, s);
+  distinct.zero(s);
+  { row_hash<<<blocks(n), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), 0, h.get()); note_launch(); }
+  { table_insert<<<blocks(n), 256, 0, s>>>(n, h.get(), keys.get(), rep.get(), cap, max_templates, distinct.get(), ovf.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  int hovf = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&hovf, ovf.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (hovf) return false;  // more distinct patterns than the table holds: keep CSR
+  DBuf<int32_t> flag;
+  DBuf<int64_t> pos;
+  flag.alloc(cap, s);
+  pos.alloc(cap + 1, s);
+  { occupied<<<blocks(cap), 256, 0, s>>>(cap, keys.get(), flag.get()); note_launch(); }
+  scan_i32_to_i64(flag.get(), pos.get(), cap, s);
+  int64_t T = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&T, pos.get() + cap, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (T > max_templates || T * 4 > n) return false;  // fewer than 4 rows per pattern: no gain
+  // template ids in order of first occurrence (smallest representative row)
+  DBuf<uint32_t> rep_key;
+  DBuf<int64_t> slot_of;
+  rep_key.alloc(T, s);
+  slot_of.alloc(T, s);
+  { compact_reps<<<blocks(cap), 256, 0, s>>>(cap, flag.get(), pos.get(), rep.get(), rep_key.get(), slot_of.get()); note_launch(); }
+  int bits = 1;
+  while (bits < 32 && ((int64_t)1 << bits) < n) ++bits;
+  radix_sort_pairs(rep_key.get(), slot_of.get(), T, bits, s);
+  slot_tid.alloc(cap, s);
+  { assign_tid<<<blocks(T), 256, 0, s>>>(T, slot_of.get(), slot_tid.get()); note_launch(); }
+  DBuf<int32_t> len;
+  len.alloc(T, s);
+  { template_len<<<blocks(T), 256, 0, s>>>(T, rep_key.get(), A.rp.get(), len.get()); note_launch(); }
+  P.tptr.alloc(T + 1, s);
+  scan_i32_to_i64(len.get(), P.tptr.get(), T, s);
+  int64_t total = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&total, P.tptr.get() + T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (total > max_offsets) {
+    P.tptr.release();
+    return false;
+  }
+  P.toff.alloc(std::max<int64_t>(total, 1), s);
+  { template_fill<<<blocks(T), 256, 0, s>>>(T, rep_key.get(), A.rp.get(), A.ci.get(), P.tptr.get(), P.toff.get()); note_launch(); }
+  P.tid.alloc(n, s);
+  { table_find<<<blocks(n), 256, 0, s>>>(n, h.get(), keys.get(), slot_tid.get(), cap, P.tid.get()); note_launch(); }
+  bad.alloc(1, s);
+  bad.zero(s);
+  { verify<<<blocks(n), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), P.tid.get(), P.tptr.get(), P.toff.get(), bad.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  int hbad = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&hbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (hbad) {  // a hash collision between different patterns: keep CSR
+    P.tid.release();
+    P.tptr.release();
+    P.toff.release();
+    return false;
+  }
+  P.n_templates = T;
+  P.n_offsets = total;
+  P.on = true;
+  return true;
+}
+
+// Row groups: rows with identical (absolute) column sets -- in a nodal high-order operator, the
+// interior nodes of one element, the interior nodes of one shared face or edge.  A group's rows
+// form a dense block over its columns, so the row kernels gather x once per group.
+bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
+  Groups& R = A.grp;
+  R.on = false;
+  const int64_t n = A.n;
+  if (n < 1024 || A.nnz == 0) return false;
+  int64_t cap = 1;
+  while (cap < 4 * std::min<int64_t>(n, max_groups + 1)) cap <<= 1;
+  DBuf<uint64_t> h;
+  DBuf<unsigned long long> keys;
+  DBuf<int> rep, ovf, slot_gid, bad, distinct;
+  h.alloc(n, s);
+  keys.alloc(cap, s);
+  rep.alloc(cap, s);
+  ovf.alloc(1, s);
+  distinct.alloc(1, s);
+  GIAMG_CUDA(cudaMemsetAsync(keys.get(), 0xff, sizeof(unsigned long long) * cap, s));
+  GIAMG_CUDA(cudaMemsetAsync(rep.get(), 0x7f, sizeof(int) * cap, s));
+  ovf.zero(s);
+  distinct.zero(s);
+  { row_hash<<<blocks(n), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), 1, h.get()); note_launch(); }
+  { table_insert<<<blocks(n), 256, 0, s>>>(n, h.get(), keys.get(), rep.get(), cap, max_groups, distinct.get(), ovf.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  int hovf = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&hovf, ovf.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (hovf) return false;
+  DBuf<int32_t> flag;
+  DBuf<int64_t> pos;
+  flag.alloc(cap, s);
+  pos.alloc(cap + 1, s);
+  { occupied<<<blocks(cap), 256, 0, s>>>(cap, keys.get(), flag.get()); note_launch(); }
+  scan_i32_to_i64(flag.get(), pos.get(), cap, s);
+  int64_t G = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&G, pos.get() + cap, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (G > max_groups || G * 2 > n) return false;  // groups of fewer than 2 rows on average
+  DBuf<uint32_t> rep_key;
+  DBuf<int64_t> slot_of;
+  rep_key.alloc(G, s);
+  slot_of.alloc(G, s);
+  { compact_reps<<<blocks(cap), 256, 0, s>>>(cap, flag.get(), pos.get(), rep.get(), rep_key.get(), slot_of.get()); note_launch(); }
+  int bits = 1;
+  while (bits < 32 && ((int64_t)1 << bits) < n) ++bits;
+  radix_sort_pairs(rep_key.get(), slot_of.get(), G, bits, s);
+  slot_gid.alloc(cap, s);
+  { assign_tid<<<blocks(G), 256, 0, s>>>(G, slot_of.get(), slot_gid.get()); note_launch(); }
+  DBuf<int32_t> len, gid;
+  len.alloc(G, s);
+  { template_len<<<blocks(G), 256, 0, s>>>(G, rep_key.get(), A.rp.get(), len.get()); note_launch(); }
+  R.gptr.alloc(G + 1, s);
+  scan_i32_to_i64(len.get(), R.gptr.get(), G, s);
+  int64_t total = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&total, R.gptr.get() + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (total * 4 > A.nnz) {  // fewer than 4 rows share a column list on average: no gain
+    R.gptr.release();
+    return false;
+  }
+  R.gcol.alloc(std::max<int64_t>(total, 1), s);
+  { group_fill_cols<<<blocks(G), 256, 0, s>>>(G, rep_key.get(), A.rp.get(), A.ci.get(), R.gptr.get(), R.gcol.get()); note_launch(); }
+  gid.alloc(n, s);
+  { table_find<<<blocks(n), 256, 0, s>>>(n, h.get(), keys.get(), slot_gid.get(), cap, gid.get()); note_launch(); }
+  bad.alloc(1, s);
+  bad.zero(s);
+  { verify_groups<<<blocks(n), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), gid.get(), R.gptr.get(), R.gcol.get(), bad.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  int hbad = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&hbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (hbad) {
+    R.gptr.release();
+    R.gcol.release();
+    return false;
+  }
+  DBuf<int32_t> cnt, fill;
+  cnt.alloc(G, s);
+  fill.alloc(G, s);
+  cnt.zero(s);
+  fill.zero(s);
+  { group_count_rows<<<blocks(n), 256, 0, s>>>(n, gid.get(), cnt.get()); note_launch(); }
+  R.rptr.alloc(G + 1, s);
+  scan_i32_to_i64(cnt.get(), R.rptr.get(), G, s);
+  R.grow.alloc(n, s);
+  { group_fill_rows<<<blocks(n), 256, 0, s>>>(n, gid.get(), R.rptr.get(), fill.get(), R.grow.get()); note_launch(); }
+  { group_sort_rows<<<blocks(G), 256, 0, s>>>(G, R.rptr.get(), R.grow.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  // largest column list (shared-memory size of the kernel)
+  std::vector<int64_t> gp(G + 1);
+  GIAMG_CUDA(cudaMemcpyAsync(gp.data(), R.gptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  int64_t cmax = 0;
+  for (int64_t g = 0; g < G; ++g) cmax = std::max(cmax, gp[g + 1] - gp[g]);
+  if (cmax * 8 > 96 * 1024) {  // the FP64 x block must fit in shared memory
+    R.gptr.release(); R.gcol.release(); R.rptr.release(); R.grow.release();
+    return false;
+  }
+  R.n_groups = G;
+  R.n_cols = total;
+  R.cmax = (int)cmax;
+  R.on = true;
+  return true;
+}
+
+}  // namespace giamg

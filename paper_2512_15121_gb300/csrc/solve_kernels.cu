@@ -7,6 +7,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -40,10 +43,10 @@ __global__ void __launch_bounds__(kThreads) csr_rows(int64_t n, const int64_t* _
     const int64_t s = rp[row], e = rp[row + 1];
     int64_t t = s + lane;
     for (; t + TPR < e; t += 2 * TPR) {
-      acc0 += val[t] * x[ci[t]];
-      acc1 += val[t + TPR] * x[ci[t + TPR]];
+      acc0 = fma(__ldcs(val + t), x[__ldcs(ci + t)], acc0);
+      acc1 = fma(__ldcs(val + t + TPR), x[__ldcs(ci + t + TPR)], acc1);
     }
-    if (t < e) acc0 += val[t] * x[ci[t]];
+    if (t < e) acc0 = fma(__ldcs(val + t), x[__ldcs(ci + t)], acc0);
   }
   V acc = acc0 + acc1;
 #pragma unroll
@@ -63,23 +66,266 @@ __global__ void __launch_bounds__(kThreads) csr_rows(int64_t n, const int64_t* _
   }
 }
 
+// Row kernels on a pattern-compressed matrix: the columns of row i are i + off[k] for the
+// offsets of the row's template, which stay in L1/L2 while the values stream from HBM.
+// TPR threads per row; consecutive threads take consecutive entries, so the x gathers of one
+// instruction fall in a few runs of neighbouring columns.
+template <int TPR, int U, typename V, int MODE>
+__device__ __forceinline__ void pat_body(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ tid,
+                                         const int64_t* __restrict__ tptr, const int32_t* __restrict__ toff,
+                                         const V* __restrict__ val, const V* __restrict__ x, const V* __restrict__ b,
+                                         V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = gt / TPR;
+  const int lane = threadIdx.x % TPR;
+  const bool valid = row < n;
+  V acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = 0;
+  if (valid) {
+    const int64_t s = rp[row];
+    const int len = (int)(rp[row + 1] - s);
+    const int32_t* __restrict__ off = toff + tptr[tid[row]];
+    const V* __restrict__ vr = val + s;
+    const V* __restrict__ xr = x + row;
+    int k = lane;
+    if constexpr (U == 2) {
+      for (; k + TPR < len; k += 2 * TPR) {
+        acc[0] = fma(__ldcs(vr + k), xr[__ldg(off + k)], acc[0]);
+        acc[1] = fma(__ldcs(vr + k + TPR), xr[__ldg(off + k + TPR)], acc[1]);
+      }
+      if (k < len) acc[0] = fma(__ldcs(vr + k), xr[__ldg(off + k)], acc[0]);
+    } else {
+      // U independent (offset -> gather -> fma) chains per step: offsets and values first,
+      // then the gathers, so U memory latencies overlap
+      for (; k + (U - 1) * TPR < len; k += U * TPR) {
+        int o[U];
+        V v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          o[u] = __ldg(off + k + u * TPR);
+          v[u] = __ldcs(vr + k + u * TPR);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = fma(v[u], xr[o[u]], acc[u]);
+      }
+      for (; k < len; k += TPR) acc[0] = fma(__ldcs(vr + k), xr[__ldg(off + k)], acc[0]);
+    }
+  }
+#pragma unroll
+  for (int u = 1; u < U; ++u) acc[0] += acc[u];
+  V a = acc[0];
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, TPR);
+  if (!valid || lane != 0) return;
+  if (MODE == kSpmv) {
+    y[row] = a;
+  } else if (MODE == kAddSpmv) {
+    y[row] += a;
+  } else if (MODE == kResidual) {
+    y[row] = b[row] - a;
+  } else {
+    const V r = b[row] - a;
+    const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * r;
+    d[row] = dn;
+    y[row] = x[row] + dn;
+  }
+}
+
+#define PAT_KERNEL(NAME, V, MODE)                                                                              \
+  template <int TPR, int U>                                                                                   \
+  __global__ void __launch_bounds__(kThreads)                                                                 \
+      NAME(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ tid,                        \
+           const int64_t* __restrict__ tptr, const int32_t* __restrict__ toff, const V* __restrict__ val,     \
+           const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,            \
+           const V* __restrict__ dinv, V c1, V c2) {                                                          \
+    pat_body<TPR, U, V, MODE>(n, rp, tid, tptr, toff, val, x, b, y, d, dinv, c1, c2);                        \
+  }
+PAT_KERNEL(pat_spmv_f64, double, kSpmv)
+PAT_KERNEL(pat_spmv_f32, float, kSpmv)
+PAT_KERNEL(pat_resid_f64, double, kResidual)
+PAT_KERNEL(pat_resid_f32, float, kResidual)
+PAT_KERNEL(pat_cheb_f64, double, kCheb)
+PAT_KERNEL(pat_cheb_f32, float, kCheb)
+PAT_KERNEL(pat_add_f64, double, kAddSpmv)
+PAT_KERNEL(pat_add_f32, float, kAddSpmv)
+
+template <typename V, int MODE>
+struct PatKernel;
+#define PAT_SELECT(V, MODE, NAME)                                                  \
+  template <>                                                                     \
+  struct PatKernel<V, MODE> {                                                     \
+    template <int TPR, int U>                                                     \
+    static constexpr decltype(&NAME<TPR, U>) get() { return &NAME<TPR, U>; }     \
+  };
+PAT_SELECT(double, kSpmv, pat_spmv_f64)
+PAT_SELECT(float, kSpmv, pat_spmv_f32)
+PAT_SELECT(double, kResidual, pat_resid_f64)
+PAT_SELECT(float, kResidual, pat_resid_f32)
+PAT_SELECT(double, kCheb, pat_cheb_f64)
+PAT_SELECT(float, kCheb, pat_cheb_f32)
+PAT_SELECT(double, kAddSpmv, pat_add_f64)
+PAT_SELECT(float, kAddSpmv, pat_add_f32)
+
+// Row-group kernels: one CTA per group of rows with identical column sets; the group's x values
+// are gathered once into shared memory, then every warp streams one row's values from HBM
+// against them (consecutive lanes read consecutive shared words: no bank conflicts).
+template <typename V, int MODE>
+__device__ __forceinline__ void grp_body(const int64_t* __restrict__ gptr, const int32_t* __restrict__ gcol,
+                                         const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow,
+                                         const int64_t* __restrict__ rp, const V* __restrict__ val,
+                                         const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y,
+                                         V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xs = reinterpret_cast<V*>(smem_raw);
+  const int64_t g = blockIdx.x;
+  const int64_t c0 = gptr[g];
+  const int c = (int)(gptr[g + 1] - c0);
+  for (int k = threadIdx.x; k < c; k += blockDim.x) xs[k] = x[__ldg(gcol + c0 + k)];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t t = rptr[g] + warp; t < rptr[g + 1]; t += nw) {
+    const int64_t row = grow[t];
+    const V* __restrict__ vr = val + rp[row];
+    V a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int k = lane;
+    for (; k + 96 < c; k += 128) {
+      a0 = fma(__ldcs(vr + k), xs[k], a0);
+      a1 = fma(__ldcs(vr + k + 32), xs[k + 32], a1);
+      a2 = fma(__ldcs(vr + k + 64), xs[k + 64], a2);
+      a3 = fma(__ldcs(vr + k + 96), xs[k + 96], a3);
+    }
+    for (; k < c; k += 32) a0 = fma(__ldcs(vr + k), xs[k], a0);
+    V a = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane != 0) continue;
+    if (MODE == kSpmv) {
+      y[row] = a;
+    } else if (MODE == kAddSpmv) {
+      y[row] += a;
+    } else if (MODE == kResidual) {
+      y[row] = b[row] - a;
+    } else {
+      const V r = b[row] - a;
+      const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * r;
+      d[row] = dn;
+      y[row] = x[row] + dn;
+    }
+  }
+}
+
+#define GRP_KERNEL(NAME, V, MODE)                                                                          \
+  __global__ void __launch_bounds__(kThreads)                                                             \
+      NAME(const int64_t* __restrict__ gptr, const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr, \
+           const int32_t* __restrict__ grow, const int64_t* __restrict__ rp, const V* __restrict__ val,   \
+           const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,        \
+           const V* __restrict__ dinv, V c1, V c2) {                                                      \
+    grp_body<V, MODE>(gptr, gcol, rptr, grow, rp, val, x, b, y, d, dinv, c1, c2);                        \
+  }
+GRP_KERNEL(grp_spmv_f64, double, kSpmv)
+GRP_KERNEL(grp_spmv_f32, float, kSpmv)
+GRP_KERNEL(grp_resid_f64, double, kResidual)
+GRP_KERNEL(grp_resid_f32, float, kResidual)
+GRP_KERNEL(grp_cheb_f64, double, kCheb)
+GRP_KERNEL(grp_cheb_f32, float, kCheb)
+GRP_KERNEL(grp_add_f64, double, kAddSpmv)
+GRP_KERNEL(grp_add_f32, float, kAddSpmv)
+
+template <typename V, int MODE>
+struct GrpKernel;
+#define GRP_SELECT(V, MODE, NAME)                                      \
+  template <>                                                         \
+  struct GrpKernel<V, MODE> {                                         \
+    static constexpr decltype(&NAME) get() { return &NAME; }         \
+  };
+GRP_SELECT(double, kSpmv, grp_spmv_f64)
+GRP_SELECT(float, kSpmv, grp_spmv_f32)
+GRP_SELECT(double, kResidual, grp_resid_f64)
+GRP_SELECT(float, kResidual, grp_resid_f32)
+GRP_SELECT(double, kCheb, grp_cheb_f64)
+GRP_SELECT(float, kCheb, grp_cheb_f32)
+GRP_SELECT(double, kAddSpmv, grp_add_f64)
+GRP_SELECT(float, kAddSpmv, grp_add_f32)
+
+template <typename V, int MODE>
+void launch_grp(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  auto k = GrpKernel<V, MODE>::get();
+  const size_t sm = sizeof(V) * (size_t)A.grp.cmax;
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
+  k<<<(unsigned)A.grp.n_groups, kThreads, sm, s>>>(A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(),
+                                                   A.grp.grow.get(), A.rp.get(), val, x, b, y, d, dinv, c1, c2);
+  note_launch();
+}
+
+template <int TPR, int U, typename V, int MODE>
+void launch_pat(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  const int64_t n = A.n;
+  auto k = PatKernel<V, MODE>::template get<TPR, U>();
+  k<<<grid_for(n * TPR, kThreads), kThreads, 0, s>>>(n, A.rp.get(), A.pat.tid.get(), A.pat.tptr.get(),
+                                                     A.pat.toff.get(), val, x, b, y, d, dinv, c1, c2);
+  note_launch();
+}
+
+template <int TPR, typename V, int MODE>
+void launch_csr(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  const int64_t n = A.n;
+  csr_rows<TPR, V, MODE><<<grid_for(n * TPR, kThreads), kThreads, 0, s>>>(n, A.rp.get(), A.ci.get(), val, x, b, y,
+                                                                         d, dinv, c1, c2);
+  note_launch();
+}
+
+// default threads per row from the average row length (before or without tuning)
+inline int default_tpr(double avg) { return avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4; }
+
+template <typename V, int MODE>
+void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* val, const V* x, const V* b, V* y, V* d,
+                    const V* dinv, V c1, V c2, cudaStream_t s) {
+  const int tpr = var.tpr ? var.tpr : default_tpr(avg);
+  const bool pat = var.tpr ? var.pat : A.pat.on;
+  if (var.group && A.grp.on) {
+    launch_grp<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
+  } else if (pat && var.unroll == 4) {
+    switch (tpr) {
+      case 32: launch_pat<32, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 16: launch_pat<16, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 8: launch_pat<8, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      default: launch_pat<4, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+    }
+  } else if (pat) {
+    switch (tpr) {
+      case 32: launch_pat<32, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 16: launch_pat<16, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 8: launch_pat<8, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      default: launch_pat<4, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+    }
+  } else {
+    switch (tpr) {
+      case 32: launch_csr<32, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 16: launch_csr<16, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 8: launch_csr<8, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      default: launch_csr<4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+    }
+  }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
 template <typename V, int MODE>
 void launch_rows(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
                  cudaStream_t s, double avg) {
-  const int64_t n = A.n;
-  if (n == 0) return;
-  const int64_t* rp = A.rp.get();
-  const int32_t* ci = A.ci.get();
-  if (avg >= 48) {
-    { csr_rows<32, V, MODE><<<grid_for(n * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
-  } else if (avg >= 20) {
-    { csr_rows<16, V, MODE><<<grid_for(n * 16, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
-  } else if (avg >= 8) {
-    { csr_rows<8, V, MODE><<<grid_for(n * 8, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
-  } else {
-    { csr_rows<4, V, MODE><<<grid_for(n * 4, kThreads), kThreads, 0, s>>>(n, rp, ci, val, x, b, y, d, dinv, c1, c2); note_launch(); }
-  }
-  GIAMG_CUDA(cudaGetLastError());
+  if (A.n == 0) return;
+  // the level's own values use its tuned variant; other matrices (P, R) take the default
+  const bool own = val == (sizeof(V) == 8 ? (const V*)A.v.get() : (const V*)A.v32.get());
+  RowVariant none;
+  const RowVariant& var = own ? (sizeof(V) == 8 ? A.var64 : A.var32) : none;
+  launch_variant<V, MODE>(A, var, avg, val, x, b, y, d, dinv, c1, c2, s);
 }
 
 // ------------------------------------------------------------------ element transfers
@@ -254,6 +500,46 @@ __global__ void chol_solve_kernel(const double* __restrict__ L, int64_t nc, cons
     __syncthreads();
   }
   for (int64_t i = tid; i < nc; i += nt) x[i] = (V)y[i];
+}
+
+// A^-1 from the Cholesky factor: block j applies the forward and backward substitutions of
+// chol_solve_kernel to the unit vector e_j and stores column j of the inverse (column-major).
+__global__ void chol_inverse_kernel(const double* __restrict__ L, int64_t nc, double* __restrict__ Ainv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* y = reinterpret_cast<double*>(smem_raw);
+  const int64_t j = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t i = tid; i < nc; i += nt) y[i] = i == j ? 1.0 : 0.0;
+  __syncthreads();
+  for (int64_t k = j; k < nc; ++k) {  // entries above j stay zero in the forward sweep
+    const double yk = y[k] / L[k * nc + k];
+    for (int64_t i = k + 1 + tid; i < nc; i += nt) y[i] -= L[k * nc + i] * yk;
+    __syncthreads();
+    if (tid == 0) y[k] = yk;
+    __syncthreads();
+  }
+  for (int64_t k = nc - 1; k >= 0; --k) {
+    const double xk = y[k] / L[k * nc + k];
+    for (int64_t i = tid; i < k; i += nt) y[i] -= L[i * nc + k] * xk;
+    __syncthreads();
+    if (tid == 0) y[k] = xk;
+    __syncthreads();
+  }
+  for (int64_t i = tid; i < nc; i += nt) Ainv[j * nc + i] = y[i];
+}
+
+// x = A^-1 b with the explicit inverse (symmetric, so its columns are its rows): one warp per row
+template <typename V>
+__global__ void dense_inverse_apply(const double* __restrict__ Ainv, int64_t nc, const V* __restrict__ b,
+                                    V* __restrict__ x) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (row < nc)
+    for (int64_t k = lane; k < nc; k += 32) s += Ainv[row * nc + k] * (double)b[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (row < nc && lane == 0) x[row] = (V)s;
 }
 
 // ------------------------------------------------------------------ reductions and vectors
@@ -441,6 +727,99 @@ inline unsigned vec_grid(int64_t n) { return (unsigned)std::min<int64_t>(std::ma
 }  // namespace
 
 // ================================================================== launchers
+// Time every row-kernel variant (CSR, pattern with 2 or 4 chains, row groups; 4..32 threads
+// per row) on A with CUDA events and keep the fastest per precision: best of five runs on a
+// non-constant x after one warm-up run.  Only matrices large enough to matter are tuned.
+// GIAMG_TUNE_LOG=1 prints the timings to stderr.
+__global__ void tune_fill(int64_t n, double* x64, float* x32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = 1.0 + 1e-3 * (double)(i % 97);
+    x64[i] = v;
+    x32[i] = (float)v;
+  }
+}
+
+void choose_rows(DCSR& A, int form, int threads) {
+  const double avg = A.n ? (double)A.nnz / A.n : 0.0;
+  for (int prec = 0; prec < 2; ++prec) {
+    RowVariant v;
+    if (form == 0) {
+      // defaults: FP32 rows on the pattern form (halved index traffic); FP64 rows, which are
+      // bound by the 1/64-rate FP64 pipe, on CSR with 16 threads per long row
+      v.pat = prec == 1 && A.pat.on;
+      v.tpr = prec == 1 ? default_tpr(avg) : (avg >= 48 ? 16 : default_tpr(avg));
+    } else {
+      v.pat = form == 2 && A.pat.on;
+      v.group = form == 3 && A.grp.on;
+      v.tpr = v.group ? 32 : default_tpr(avg);
+    }
+    if (threads && !v.group) v.tpr = threads;
+    (prec == 0 ? A.var64 : A.var32) = v;
+  }
+}
+
+void tune_rows(DCSR& A, cudaStream_t s) {
+  if (A.nnz < (1 << 20)) return;
+  const bool log = getenv("GIAMG_TUNE_LOG") != nullptr;
+  DBuf<double> x64, y64;
+  DBuf<float> x32, y32;
+  x64.alloc(A.n, s); y64.alloc(A.n, s); x32.alloc(A.n, s); y32.alloc(A.n, s);
+  { tune_fill<<<vec_grid(A.n), 256, 0, s>>>(A.n, x64.get(), x32.get()); note_launch(); }
+  cudaEvent_t e0, e1;
+  GIAMG_CUDA(cudaEventCreate(&e0));
+  GIAMG_CUDA(cudaEventCreate(&e1));
+  const double avg = (double)A.nnz / A.n;
+  std::vector<RowVariant> cands;
+  for (int tpr : {4, 8, 16, 32}) {
+    RowVariant v;
+    v.tpr = tpr;
+    cands.push_back(v);  // CSR
+    if (A.pat.on) {
+      v.pat = true;
+      v.unroll = 2;
+      cands.push_back(v);
+      v.unroll = 4;
+      cands.push_back(v);
+    }
+  }
+  if (A.grp.on) {
+    RowVariant v;
+    v.tpr = 32;
+    v.group = true;
+    cands.push_back(v);
+  }
+  for (int prec = 0; prec < 2; ++prec) {
+    float best = 1e30f;
+    RowVariant pick;
+    for (const RowVariant& v : cands) {
+      float t = 1e30f;
+      for (int rep = 0; rep < 6; ++rep) {
+        GIAMG_CUDA(cudaEventRecord(e0, s));
+        if (prec == 0)
+          launch_variant<double, kSpmv>(A, v, avg, A.v.get(), x64.get(), nullptr, y64.get(), nullptr, nullptr, 0.0, 0.0, s);
+        else
+          launch_variant<float, kSpmv>(A, v, avg, A.v32.get(), x32.get(), nullptr, y32.get(), nullptr, nullptr, 0.f, 0.f, s);
+        GIAMG_CUDA(cudaEventRecord(e1, s));
+        GIAMG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        GIAMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) t = std::min(t, ms);
+      }
+      if (log)
+        fprintf(stderr, "tune n=%lld nnz=%lld %s form=%s tpr=%d unroll=%d: %.4f ms\n", (long long)A.n,
+                (long long)A.nnz, prec ? "fp32" : "fp64", v.group ? "groups" : v.pat ? "pattern" : "csr", v.tpr,
+                v.unroll, t);
+      if (t < best) {
+        best = t;
+        pick = v;
+      }
+    }
+    (prec == 0 ? A.var64 : A.var32) = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 void spmv(const DCSR& A, const double* x, double* y, cudaStream_t s, double avg) {
   launch_rows<double, kSpmv>(A, A.v.get(), x, nullptr, y, nullptr, nullptr, 0.0, 0.0, s, avg);
 }
@@ -534,6 +913,24 @@ static void chol_smem_attr() {
   GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
   GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
   done = true;
+}
+void chol_inverse(const double* L, int64_t nc, double* Ainv, cudaStream_t s) {
+  chol_smem_attr();
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
+    attr = true;
+  }
+  { chol_inverse_kernel<<<(unsigned)nc, 256, sizeof(double) * nc, s>>>(L, nc, Ainv); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void inverse_apply(const double* Ainv, int64_t nc, const double* b, double* x, cudaStream_t s) {
+  { dense_inverse_apply<double><<<grid_for(nc * 32, 256), 256, 0, s>>>(Ainv, nc, b, x); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void inverse_apply32(const double* Ainv, int64_t nc, const float* b, float* x, cudaStream_t s) {
+  { dense_inverse_apply<float><<<grid_for(nc * 32, 256), 256, 0, s>>>(Ainv, nc, b, x); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
 }
 void chol_solve(const double* L, int64_t nc, const double* b, double* x, cudaStream_t s) {
   chol_smem_attr();

@@ -1,0 +1,358 @@
+"""Continuous-batching solve server over the C ABI.
+
+Requests (an assembled operator, its element map, and 1..32 right-hand sides) arrive over time.
+The server
+
+* caches hierarchies on the device, keyed by (mesh key, order, lambda): a request whose operator
+  is cached skips setup;
+* admits work only while free device memory covers it (a hierarchy's estimated footprint plus a
+  reserve), evicting idle cached hierarchies least recently used first;
+* batches: requests for the same operator that are waiting when a worker slot frees up are
+  solved together as one multi-right-hand-side solve (giamg_solve_batch, up to 32 columns);
+  requests that arrive while a batch runs join the next batch -- continuous batching;
+* overlaps: every cached hierarchy owns a CUDA stream and every worker slot is a host thread,
+  so batches for different operators run concurrently on the device.
+
+A column's arithmetic in the batched kernels does not depend on the other columns, so a request
+gets the same bits alone and in a mix (tests/test_gpu_serve.py checks this).  The clock and the
+free-memory probe are injectable so admission can be tested deterministically on the host.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from typing import Callable
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    key: tuple                      # (mesh key, order, lambda)
+    make_operator: Callable         # () -> dict(n, row_ptr, col, val, elem_dof, p, cheb_degree)
+    rhs: np.ndarray                 # n x r (r <= 32)
+    rtol: float = 1e-8
+    precision: int = 1
+    arrival: float = 0.0
+    # filled in by the server
+    start: float = -1.0
+    finish: float = -1.0
+    x: np.ndarray | None = None
+    iters: np.ndarray | None = None
+    relres: np.ndarray | None = None
+    error: str | None = None
+    batch_id: int = -1
+
+    @property
+    def columns(self) -> int:
+        return int(self.rhs.shape[1])
+
+
+def estimate_bytes(n: int, nnz: int, columns: int = 32) -> int:
+    """Device footprint of a hierarchy plus batch work: the finest CSR (FP64 + FP32 values,
+    indices) about doubled for the coarse levels and the compressed forms, and the n x 32 FP64 /
+    FP32 work blocks of the multi-right-hand-side solve."""
+    matrix = nnz * (8 + 4 + 4) + 16 * n
+    work = n * columns * (12 * 8 + 5 * 4)
+    return int(2.0 * matrix + work)
+
+
+class _Entry:
+    def __init__(self, solver, stream, nbytes):
+        self.solver = solver
+        self.stream = stream
+        self.nbytes = nbytes
+        self.lock = threading.Lock()
+        self.last_used = 0.0
+        self.busy = False
+
+
+class Server:
+    def __init__(self, slots: int = 4, reserve_bytes: int = 2 << 30, max_columns: int = 32,
+                 mem_info: Callable | None = None, clock: Callable | None = None,
+                 solver_factory: Callable | None = None, runner: Callable | None = None, device: int = 0):
+        self.slots = slots
+        self.reserve = reserve_bytes
+        self.max_columns = max_columns
+        self.clock = clock or time.perf_counter
+        self.device = device
+        if mem_info is None:
+            import torch
+            mem_info = lambda: torch.cuda.mem_get_info(device)  # noqa: E731
+        self.mem_info = mem_info
+        self.solver_factory = solver_factory or self._default_factory
+        self.runner = runner or self._default_runner
+        self.cache: dict = {}
+        self.pending: dict = collections.OrderedDict()   # key -> deque of requests
+        self.done: list = []
+        self.cv = threading.Condition()
+        self.closed = False
+        self.stats = collections.Counter()
+        self.batch_seq = 0
+        self._running = 0
+        self._building_bytes = 0
+        self.workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(slots)]
+        for w in self.workers:
+            w.start()
+
+    # ------------------------------------------------------------------ hierarchy cache
+    def _default_factory(self, op: dict):
+        import torch
+        from . import Solver
+        stream = torch.cuda.Stream(device=self.device)
+        dev = torch.device("cuda", self.device)
+        with torch.cuda.stream(stream):
+            t = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
+            S = Solver(op["n"], t(op["row_ptr"]), t(op["col"]), t(op["val"]), t(op["elem_dof"]), op["p"],
+                       stream=stream.cuda_stream, device_ptrs=1, cheb_degree=op.get("cheb_degree", 3))
+        return S, stream
+
+    def _free_bytes(self) -> int:
+        free, _total = self.mem_info()
+        return int(free)
+
+    def _evict_for(self, need: int) -> bool:
+        """Evict idle cached hierarchies (least recently used first) until `need` bytes fit next
+        to the hierarchies that are being built (their memory is not allocated yet)."""
+        while self._free_bytes() - self.reserve - self._building_bytes < need:
+            idle = [(e.last_used, k) for k, e in self.cache.items() if not e.busy]
+            if not idle:
+                return False
+            _, k = min(idle)
+            e = self.cache.pop(k)
+            e.solver.close()
+            self.stats["evictions"] += 1
+        return True
+
+    def _claim(self, key, req: Request):
+        """Under the lock: the cached hierarchy for `key` (marked busy), a new placeholder entry
+        that the caller must build, or None if memory does not allow a new one now."""
+        e = self.cache.get(key)
+        if e is not None:
+            self.stats["cache_hits"] += 1
+            e.busy = True
+            return e, None
+        op = req.make_operator()
+        need = estimate_bytes(op["n"], len(op["val"]), self.max_columns)
+        if not self._evict_for(need):
+            self.stats["admission_waits"] += 1
+            return None, None
+        e = _Entry(None, None, need)
+        e.busy = True
+        self.cache[key] = e
+        self._building_bytes += need
+        return e, op
+
+    def _build(self, key, e: _Entry, op) -> str | None:
+        """Outside the lock: run the solver factory for a claimed placeholder; the error text, or
+        None.  A failed build leaves no cache entry."""
+        try:
+            e.solver, e.stream = self.solver_factory(op)
+            err = None
+        except Exception as ex:
+            err = f"setup failed: {ex}"
+        with self.cv:
+            self._building_bytes -= e.nbytes
+            if err is None:
+                self.stats["setups"] += 1
+            else:
+                self.cache.pop(key, None)
+                self.stats["setup_errors"] += 1
+        return err
+
+    # ------------------------------------------------------------------ requests
+    def submit(self, req: Request):
+        with self.cv:
+            req.arrival = self.clock() if req.arrival <= 0 else req.arrival
+            # requests share a batch only when they share the operator, precision and tolerance
+            self.pending.setdefault((req.key, req.precision, req.rtol), collections.deque()).append(req)
+            self.cv.notify_all()
+
+    def _next_batch(self):
+        """Oldest waiting key whose hierarchy is not busy; its requests up to max_columns."""
+        best = None
+        for key, q in self.pending.items():
+            if not q:
+                continue
+            e = self.cache.get(key[0])
+            if e is not None and e.busy:
+                continue
+            if best is None or q[0].arrival < self.pending[best][0].arrival:
+                best = key
+        if best is None:
+            return None, []
+        q = self.pending[best]
+        batch, cols = [], 0
+        while q and cols + q[0].columns <= self.max_columns:
+            r = q.popleft()
+            batch.append(r)
+            cols += r.columns
+        if not q:
+            del self.pending[best]
+        return best, batch
+
+    def _worker(self):
+        while True:
+            with self.cv:
+                while True:
+                    if self.closed and not any(self.pending.values()):
+                        return
+                    key, batch = self._next_batch()
+                    if batch:
+                        try:
+                            e, op = self._claim(key[0], batch[0])
+                        except Exception as ex:  # the operator could not even be described
+                            self._fail(batch, f"setup failed: {ex}")
+                            continue
+                        if e is None:  # not enough memory now: put the batch back and wait
+                            self.pending.setdefault(key, collections.deque()).extendleft(reversed(batch))
+                            self.pending.move_to_end(key, last=False)
+                            self.cv.wait(timeout=0.01)
+                            continue
+                        self.batch_seq += 1
+                        self._running += 1
+                        bid = self.batch_seq
+                        break
+                    self.cv.wait(timeout=0.05)
+            err = self._build(key[0], e, op) if op is not None else None
+            if err is None:
+                self._run(e, batch, bid)
+            with self.cv:
+                if err is not None:
+                    self._fail(batch, err, bid)
+                e.busy = False
+                self._running -= 1
+                e.last_used = self.clock()
+                if err is None:
+                    self.done.extend(batch)
+                self.cv.notify_all()
+
+    def _fail(self, batch: list, err: str, bid: int = -1):
+        """Under the lock: finish every request of a batch with an error."""
+        t = self.clock()
+        for r in batch:
+            r.start = r.start if r.start >= 0 else t
+            r.finish, r.batch_id, r.error = t, bid, err
+        self.done.extend(batch)
+        self.stats["failed_requests"] += len(batch)
+        self.cv.notify_all()
+
+    def _default_runner(self, e: _Entry, B: np.ndarray, rtol: float, precision: int):
+        import torch
+        with torch.cuda.stream(e.stream):
+            Bd = torch.from_numpy(np.ascontiguousarray(B)).to(f"cuda:{self.device}")
+            X, it, rr = e.solver.solve_batch(Bd, rtol=rtol, precision=precision)
+            return X.cpu().numpy(), it, rr
+
+    def _run(self, e: _Entry, batch: list, bid: int):
+        t0 = self.clock()
+        B = np.concatenate([r.rhs for r in batch], axis=1)
+        prec = batch[0].precision
+        rtol = min(r.rtol for r in batch)
+        try:
+            Xh, it, rr = self.runner(e, B, rtol, prec)
+            err = None
+        except Exception as ex:  # a failed batch fails its requests, not the server
+            Xh, it, rr, err = None, None, None, str(ex)
+        t1 = self.clock()
+        c = 0
+        for r in batch:
+            k = r.columns
+            r.start, r.finish, r.batch_id, r.error = t0, t1, bid, err
+            if err is None:
+                r.x = Xh[:, c:c + k].copy()
+                r.iters = np.asarray(it[c:c + k]).copy()
+                r.relres = np.asarray(rr[c:c + k]).copy()
+            c += k
+        self.stats["batches"] += 1
+        self.stats["columns"] += c
+
+    def drain(self, timeout: float = 600.0):
+        """Wait until every submitted request is done."""
+        t_end = time.perf_counter() + timeout
+        with self.cv:
+            while any(self.pending.values()) or any(e.busy for e in self.cache.values()) or self._running:
+                left = t_end - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError("server did not drain")
+                self.cv.wait(timeout=min(left, 0.05))
+
+    def close(self):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        for w in self.workers:
+            w.join(timeout=60)
+        for e in self.cache.values():
+            e.solver.close()
+        self.cache.clear()
+
+
+def latency_summary(requests: list) -> dict:
+    ok = [r for r in requests if r.finish >= 0 and r.error is None]
+    lat = sorted((r.finish - r.arrival) * 1e3 for r in ok)
+    if not lat:
+        return {}
+    pick = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]  # noqa: E731
+    span = max(r.finish for r in ok) - min(r.arrival for r in ok)
+    cols = sum(r.columns for r in ok)
+    return {"requests": len(lat), "solves": cols, "p50_ms": pick(0.5), "p99_ms": pick(0.99),
+            "solves_per_s": cols / span if span > 0 else None, "makespan_s": span}
+
+
+# ---------------------------------------------------------------------- synthetic request stream
+STREAM_MESHES = (4, 6, 8)
+STREAM_ORDERS = (2, 4, 6)
+STREAM_LAMBDAS = (0.0, 1.0, 1000.0)
+
+
+def synthetic_stream(n_requests: int = 128, seed: int = 7, rate_per_s: float = 200.0, max_rhs: int = 8,
+                     meshes=STREAM_MESHES, orders=STREAM_ORDERS, lambdas=STREAM_LAMBDAS):
+    """Requests for Helmholtz / Poisson operators on jittered hex meshes (mesh seed = mesh size, so
+    a (mesh, order, lambda) triple always names the same operator), 1..max_rhs smooth Fourier
+    right-hand sides seeded by request id, Poisson arrivals (exponential gaps) at rate_per_s."""
+    import fegen
+    rng = np.random.default_rng(seed)
+    ops = {}
+
+    def operator(n, p, lam):
+        key = (n, p, lam)
+        if key not in ops:
+            prob = fegen.make(n, p, mesh="jitter", mesh_seed=n, lam=lam, rhs="none")
+            ops[key] = prob
+        return ops[key]
+
+    t = 0.0
+    reqs = []
+    for rid in range(n_requests):
+        n = int(rng.choice(meshes))
+        p = int(rng.choice(orders))
+        lam = float(rng.choice(lambdas))
+        r = int(rng.integers(1, max_rhs + 1))
+        t += float(rng.exponential(1.0 / rate_per_s))
+        prob = operator(n, p, lam)
+        rhs = np.stack([prob.rhs("fourier", 100000 + 64 * rid + j) for j in range(r)], axis=1)
+        k = 3 if lam > 0 else 2
+
+        def make(prob=prob, k=k):
+            return dict(n=prob.n, row_ptr=prob.row_ptr, col=prob.col, val=prob.val, elem_dof=prob.elem_dof,
+                        p=prob.p, cheb_degree=k)
+        reqs.append(Request(rid=rid, key=(f"jitter{n}^3", p, lam), make_operator=make, rhs=rhs, arrival=t))
+    return reqs, ops
+
+
+def run_stream(server: Server, reqs: list, time_scale: float = 1.0):
+    """Submit the requests at their arrival times (relative to now) and wait for all of them."""
+    t0 = server.clock()
+    offs = [r.arrival for r in reqs]
+    for r, off in zip(reqs, offs):
+        target = t0 + off * time_scale
+        while server.clock() < target:
+            time.sleep(min(0.001, max(0.0, target - server.clock())))
+        r.arrival = 0.0
+        server.submit(r)
+    server.drain()
+    return latency_summary(reqs)

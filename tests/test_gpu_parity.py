@@ -268,3 +268,61 @@ def test_strength_threshold_option_runs_and_matches_oracle():
         if oagg is not None:
             assert np.array_equal(gagg, oagg)
     gpu.close()
+
+
+def test_pattern_compression_matches_plain_csr():
+    # the compressed row kernels group the sums differently: agreement to rounding
+    prob = fegen.make(6, 6, mesh="jitter", lam=10.0)
+    a = g.Solver.from_problem(prob, device=True, compress_patterns=1)
+    c = g.Solver.from_problem(prob, device=True, compress_patterns=0)
+    assert a.templates(0)[0] > 0 and a.templates(1)[0] > 0 and c.templates(0) == (0, 0)
+    b = dev(prob.b)
+    for prec in (0, 1):
+        xa, ia, _ = a.solve(b, rtol=1e-9, precision=prec, force_iters=8)
+        xc, ic, _ = c.solve(b, rtol=1e-9, precision=prec, force_iters=8)
+        tol = 1e-10 if prec == 0 else 1e-5
+        assert torch.linalg.norm(xa - xc) <= tol * torch.linalg.norm(xc), prec
+    a.close()
+    c.close()
+    # a relabelled numbering repeats no pattern: plain CSR is kept
+    rel = fegen.make(6, 4, mesh="jitter", lam=1.0, perm_seed=5)
+    r = g.Solver.from_problem(rel, device=True)
+    assert r.templates(0) == (0, 0)
+    r.close()
+
+
+_forms_oracle = {}
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("threads", [0, 4, 16])
+def test_row_kernel_forms_match_oracle(form, threads):
+    # every row-kernel form (CSR, row patterns, row groups) and thread count on the same problem
+    if "p" not in _forms_oracle:
+        prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
+        _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
+    prob, orc = _forms_oracle["p"]
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, row_form=form, row_threads=threads)
+    try:
+        name = ["csr", "pattern", "groups"][form - 1]
+        for prec in (0, 1):
+            assert gpu.kernel(0, prec)[1] == name
+        rng = np.random.default_rng(7)
+        for l in range(orc.num_levels):
+            n = orc.level_info(l)["n"]
+            x = rng.normal(size=n)
+            y, yo = host(gpu.spmv(l, dev(x))), orc.spmv(l, x)
+            assert np.max(np.abs(y - yo)) <= 1e-12 * np.max(np.abs(yo)), l
+        r = rng.normal(size=prob.n)
+        zo = orc.vcycle(r, 0)
+        assert np.linalg.norm(host(gpu.vcycle(dev(r), 0)) - zo) <= 1e-10 * np.linalg.norm(zo)
+        zo32 = orc.vcycle(r, 1)
+        assert np.linalg.norm(host(gpu.vcycle(dev(r), 1)) - zo32) <= 1e-4 * np.linalg.norm(zo32)
+        xo, ito, _, _, _ = orc.solve(prob.b, rtol=1e-8)
+        x, it, _ = gpu.solve(dev(prob.b), rtol=1e-8, force_iters=ito)
+        assert np.linalg.norm(host(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+        B = np.stack([prob.b, prob.rhs("fourier", 1001)], axis=1)
+        X, its, rr = gpu.solve_batch(torch.from_numpy(B).cuda(), rtol=1e-8, force_iters=ito)
+        assert np.linalg.norm(X.cpu().numpy()[:, 0] - xo) <= 1e-10 * np.linalg.norm(xo)
+    finally:
+        gpu.close()

@@ -1,0 +1,180 @@
+"""Host logic of the solve server with a fake clock, a fake free-memory figure and a fake solver:
+batching of requests for one operator, the column limit, admission by free memory, LRU eviction
+and completion of every request.  No GPU is used."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2512_15121_gb300 import serve
+
+
+class FakeSolver:
+    def __init__(self, key):
+        self.key = key
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+class Memory:
+    """free bytes = capacity - bytes of live fake hierarchies"""
+
+    def __init__(self, capacity):
+        self.capacity = capacity
+        self.live = {}
+        self.lock = threading.Lock()
+
+    def info(self):
+        with self.lock:
+            return self.capacity - sum(self.live.values()), self.capacity
+
+
+def make_request(rid, key, n=100, cols=1):
+    op = dict(n=n, row_ptr=None, col=None, val=np.zeros(10 * n), elem_dof=None, p=2)
+    return serve.Request(rid=rid, key=key, make_operator=lambda: op, rhs=np.full((n, cols), float(rid)))
+
+
+def server_with_fakes(capacity, slots=2, delay=0.002, max_columns=32):
+    mem = Memory(capacity)
+    batches = []
+
+    def factory(op):
+        s = FakeSolver(None)
+        mem.live[id(s)] = serve.estimate_bytes(op["n"], len(op["val"]), max_columns)
+        orig = s.close
+
+        def close():
+            mem.live.pop(id(s), None)
+            orig()
+        s.close = close
+        return s, None
+
+    def runner(e, B, rtol, precision):
+        batches.append(B.shape[1])
+        time.sleep(delay)
+        m = B.shape[1]
+        return B * 2.0, np.full(m, 3, np.int32), np.full(m, 1e-9)
+
+    srv = serve.Server(slots=slots, reserve_bytes=0, max_columns=max_columns, mem_info=mem.info,
+                       solver_factory=factory, runner=runner)
+    return srv, mem, batches
+
+
+def test_every_request_completes_with_its_own_columns():
+    srv, mem, batches = server_with_fakes(capacity=1 << 40)
+    reqs = [make_request(i, key=("mesh", i % 3, 1.0), cols=1 + i % 4) for i in range(40)]
+    for r in reqs:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    for r in reqs:
+        assert r.error is None and r.x.shape == r.rhs.shape
+        assert np.array_equal(r.x, 2.0 * r.rhs)           # the columns come back to their owner
+        assert np.all(r.iters == 3)
+    assert sum(batches) == sum(r.columns for r in reqs)
+    assert max(batches) <= 32
+    assert srv.stats["setups"] == 3 and srv.stats["cache_hits"] >= 1
+
+
+def test_requests_for_one_operator_are_batched():
+    srv, mem, batches = server_with_fakes(capacity=1 << 40, slots=1, delay=0.05)
+    first = make_request(0, ("A", 2, 0.0))
+    srv.submit(first)
+    time.sleep(0.01)  # the first batch is running; these queue up and run together next
+    rest = [make_request(i, ("A", 2, 0.0)) for i in range(1, 9)]
+    for r in rest:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert batches[0] == 1 and batches[1] == 8
+    assert len({r.batch_id for r in rest}) == 1
+
+
+def test_column_limit_splits_batches():
+    srv, mem, batches = server_with_fakes(capacity=1 << 40, slots=1, delay=0.02, max_columns=8)
+    reqs = [make_request(i, ("A", 2, 0.0), cols=3) for i in range(6)]
+    for r in reqs:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert all(b <= 8 for b in batches) and sum(batches) == 18
+
+
+def test_admission_waits_for_memory_and_evicts_idle_hierarchies():
+    one = serve.estimate_bytes(100, 1000, 32)
+    srv, mem, batches = server_with_fakes(capacity=int(1.5 * one), slots=1)
+    reqs = [make_request(i, (f"mesh{i % 3}", 2, 0.0)) for i in range(9)]
+    for r in reqs:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert all(r.error is None for r in reqs)
+    # only one hierarchy fits: switching operators evicts the idle one
+    assert srv.stats["evictions"] >= 2
+    assert len(mem.live) == 0
+
+
+def test_latency_summary():
+    reqs = [make_request(i, ("A", 2, 0.0)) for i in range(4)]
+    for i, r in enumerate(reqs):
+        r.arrival, r.finish = 0.0, 0.001 * (i + 1)
+    s = serve.latency_summary(reqs)
+    assert s["requests"] == 4 and abs(s["p50_ms"] - 3.0) < 1e-9 and abs(s["p99_ms"] - 4.0) < 1e-9
+
+
+def test_failed_setup_fails_its_requests_and_the_server_goes_on():
+    mem = Memory(1 << 40)
+
+    def factory(op):
+        if op["p"] == 7:
+            raise RuntimeError("element order outside 1..12")
+        return FakeSolver(None), None
+
+    def runner(e, B, rtol, precision):
+        m = B.shape[1]
+        return B * 2.0, np.full(m, 3, np.int32), np.full(m, 1e-9)
+
+    srv = serve.Server(slots=2, reserve_bytes=0, mem_info=mem.info, solver_factory=factory, runner=runner)
+    bad_op = dict(n=10, row_ptr=None, col=None, val=np.zeros(100), elem_dof=None, p=7)
+    bad = [serve.Request(rid=100 + i, key=("bad", 7, 0.0), make_operator=lambda: bad_op, rhs=np.ones((10, 1)))
+           for i in range(3)]
+    good = [make_request(i, ("A", 2, 0.0)) for i in range(6)]
+    for r in bad + good:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert all(r.error and "setup failed" in r.error and r.finish >= 0 for r in bad)
+    assert all(r.error is None and np.array_equal(r.x, 2.0 * r.rhs) for r in good)
+    assert srv.stats["setup_errors"] >= 1 and srv.stats["failed_requests"] == 3
+    assert ("bad", 7, 0.0) not in srv.cache and all(w.is_alive() is False for w in srv.workers)
+
+
+def test_setups_of_different_operators_overlap():
+    """A setup runs outside the server lock: two slow builds for two operators run at once."""
+    mem = Memory(1 << 40)
+    active, peak = [0], [0]
+    lock = threading.Lock()
+
+    def factory(op):
+        with lock:
+            active[0] += 1
+            peak[0] = max(peak[0], active[0])
+        time.sleep(0.1)
+        with lock:
+            active[0] -= 1
+        return FakeSolver(None), None
+
+    def runner(e, B, rtol, precision):
+        m = B.shape[1]
+        return B, np.ones(m, np.int32), np.zeros(m)
+
+    srv = serve.Server(slots=2, reserve_bytes=0, mem_info=mem.info, solver_factory=factory, runner=runner)
+    reqs = [make_request(0, ("A", 2, 0.0)), make_request(1, ("B", 2, 0.0))]
+    for r in reqs:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert peak[0] == 2 and srv.stats["setups"] == 2
+    assert all(r.error is None for r in reqs)
