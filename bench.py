@@ -17,9 +17,13 @@ collective on the data path) and rank 0 prints the line with the max over ranks.
 from __future__ import annotations
 
 import argparse
+import collections
+import csv
 import hashlib
+import io
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -49,6 +53,10 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the multi-RHS and serving measurements")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="print a per-kernel summary of an ncu launch list and exit (no GPU work)")
+    ap.add_argument("--split-at", metavar="KERNEL",
+                    help="with --summarize-launches: also a table per segment starting at this kernel")
     return ap.parse_args()
 
 
@@ -125,6 +133,52 @@ def kernel_source_hash():
     with open(os.path.join(ROOT, "paper_2512_15121_gb300", "csrc", "solve_kernels.cu"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def _launch_table(launches):
+    agg = collections.OrderedDict()
+    for name, ns in launches:
+        a = agg.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += ns
+    tot = sum(a[1] for a in agg.values()) or 1.0
+    out = [f"{'launches':>8} {'total_ms':>10} {'share':>7}  kernel", "-" * 70]
+    for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        out.append(f"{c:8d} {t / 1e6:10.3f} {100 * t / tot:6.2f}%  {k}")
+    out.append(f"{sum(a[0] for a in agg.values()):8d} {tot / 1e6:10.3f} 100.00%  (all)")
+    return "\n".join(out)
+
+
+def summarize_launches(path, split=None):
+    """Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) by kernel: launches,
+    total device time and share.  With `split`, also one table per segment of the list, a new
+    segment starting at every launch whose kernel name contains `split`."""
+    with open(path) as f:
+        lines = [l for l in f if l.startswith('"')]
+    launches = []
+    for r in csv.DictReader(io.StringIO("".join(lines))):
+        if r.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        name = re.sub(r"\(.*", "", r["Kernel Name"]).replace("(anonymous namespace)::", "")
+        m = re.search(r"csr_rows<(\d+), (\w+), (\d)>", r["Kernel Name"])
+        if m:
+            name = f"csr_rows<{m.group(1)},{m.group(2)},{['spmv','residual','cheb','add'][int(m.group(3))]}>"
+        v = float(r["Metric Value"])
+        if r["Metric Unit"] in ("usecond", "us"):
+            v *= 1e3
+        elif r["Metric Unit"] in ("msecond", "ms"):
+            v *= 1e6
+        launches.append((name, v))
+    out = ["all launches", _launch_table(launches)]
+    if split:
+        segs = []
+        for name, v in launches:
+            if split in name or not segs:
+                segs.append([])
+            segs[-1].append((name, v))
+        for i, seg in enumerate(segs):
+            out += ["", f"segment {i} (from launch {sum(len(s) for s in segs[:i])})", _launch_table(seg)]
+    return "\n".join(out)
 
 
 def ncu_traffic(workload, mode):
@@ -406,6 +460,9 @@ def cpu_baseline(prob, k, rtol, iters):
 
 def main():
     args = parse()
+    if args.summarize_launches:
+        print(summarize_launches(args.summarize_launches, args.split_at))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
