@@ -88,6 +88,10 @@ typedef struct {
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
                              groups (falls back to CSR where the form is not available) */
   int row_threads;        /* force threads per row (4, 8, 16, 32); 0 automatic */
+  int prefetch_rows;      /* row-pattern kernels: every block prefetches into L2 the values of the
+                             block this many rows ahead; 0 off, -1 (default) automatic */
+  int row_chains;         /* row-pattern kernels: independent load chains per thread (2, 4, 8);
+                             0 (default) automatic */
 } giamg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -163,6 +167,8 @@ GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
 /* Single steps of the solve, on the handle's stream (parity tests call these):
  *   giamg_apply_vcycle: z = V(r), Algorithm 1 from the finest level (precision 0 / 1).
  *   giamg_level_spmv:   y = A_l x.
+ *   giamg_level_spmv32: y = A_l x with A_l's FP32 values, FP32 x and y and FP32 accumulation: the
+ *                       product of the FP32 V-cycle, through the level's FP32 row kernel.
  *   giamg_level_smooth: Chebyshev smoothing of A_l x = b in place (x_is_zero: x enters as 0).
  *   giamg_level_restrict: r_c = R_l r_f (R = P^T; element form on p-levels).
  *   giamg_level_prolong:  x_f += P_l e_c (element form on p-levels).
@@ -171,6 +177,7 @@ GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
  * same triangular solves on the unit vectors. */
 GIAMG_API int giamg_apply_vcycle(giamg_handle h, int precision, const double* r, double* z);
 GIAMG_API int giamg_level_spmv(giamg_handle h, int level, const double* x, double* y);
+GIAMG_API int giamg_level_spmv32(giamg_handle h, int level, const float* x, float* y);
 GIAMG_API int giamg_level_smooth(giamg_handle h, int level, const double* b, double* x, int x_is_zero);
 GIAMG_API int giamg_level_restrict(giamg_handle h, int level, const double* r_f, double* r_c);
 GIAMG_API int giamg_level_prolong(giamg_handle h, int level, const double* e_c, double* x_f);

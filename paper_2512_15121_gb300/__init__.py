@@ -26,7 +26,7 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
            "giamg_solve_batch", "giamg_solve_batch_ex",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
-           "giamg_level_rho", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_smooth",
+           "giamg_level_rho", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
            "giamg_last_error", "giamg_set_device_ptrs", "giamg_profile_enable", "giamg_profile_read",
            "giamg_launch_count", "giamg_true_relres_noalloc"]
@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("strength_theta", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("force_iters", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("hash_kind", ctypes.c_int),
                 ("compress_patterns", ctypes.c_int), ("autotune", ctypes.c_int), ("row_form", ctypes.c_int),
-                ("row_threads", ctypes.c_int)]
+                ("row_threads", ctypes.c_int), ("prefetch_rows", ctypes.c_int), ("row_chains", ctypes.c_int)]
 
 
 _lib = None
@@ -338,6 +338,18 @@ class Solver:
         x = self._in(x)
         y = self._vec(self.level_info(l)["n"])
         _check(lib().giamg_level_spmv(self._h, l, _ptr(x), _ptr(y)))
+        return y
+
+    def spmv32(self, l, x):
+        """y = A_l x in FP32 (the FP32 V-cycle's product)."""
+        if self.device:
+            import torch
+            x = (x if isinstance(x, torch.Tensor) else torch.from_numpy(np.asarray(x))).to("cuda", torch.float32).contiguous()
+            y = torch.empty(self.level_info(l)["n"], dtype=torch.float32, device="cuda")
+        else:
+            x = np.ascontiguousarray(x, np.float32)
+            y = np.empty(self.level_info(l)["n"], np.float32)
+        _check(lib().giamg_level_spmv32(self._h, l, _ptr(x), _ptr(y)))
         return y
 
     def smooth(self, l, b, x=None):

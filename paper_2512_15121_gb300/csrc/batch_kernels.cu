@@ -27,13 +27,13 @@ inline unsigned vec_grid(int64_t n) {
   return (unsigned)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 16);
 }
 
-enum BatchMode { kSpmm = 0, kResid = 1, kCheb = 2, kAdd = 3 };
+enum BatchMode { kSpmm = 0, kResid = 1, kBatCheb = 2, kAdd = 3 };
 
 // One row per group of G lanes; lane j < m owns column j.  PAT: columns from the row's template.
 template <int G, typename V, int MODE, bool PAT>
 __global__ void __launch_bounds__(kThreads)
     bat_rows(int64_t n, int m, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-             const int32_t* __restrict__ tid, const int64_t* __restrict__ tptr, const int32_t* __restrict__ toff,
+             const int32_t* __restrict__ obase, const int32_t* __restrict__ toff,
              const V* __restrict__ val, const V* __restrict__ X, const V* __restrict__ B, V* __restrict__ Y,
              V* __restrict__ D, const V* __restrict__ dinv, V c1, V c2) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t s = rp[row], e = rp[row + 1];
   V acc0 = 0, acc1 = 0;
   if (PAT) {
-    const int32_t* __restrict__ off = toff + tptr[tid[row]];
+    const int32_t* __restrict__ off = toff + obase[row];
     const V* __restrict__ xr = X + row * m + j;
     const int len = (int)(e - s);
     int k = 0;
@@ -81,7 +81,7 @@ template <int G, typename V, int MODE, bool PAT>
 void launch_g(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y, V* D, const V* dinv, V c1, V c2,
               cudaStream_t s) {
   bat_rows<G, V, MODE, PAT><<<grid_for(A.n * G, kThreads), kThreads, 0, s>>>(
-      A.n, m, A.rp.get(), A.ci.get(), A.pat.tid.get(), A.pat.tptr.get(), A.pat.toff.get(), val, X, B, Y, D, dinv, c1, c2);
+      A.n, m, A.rp.get(), A.ci.get(), A.pat.obase.get(), A.pat.toff.get(), val, X, B, Y, D, dinv, c1, c2);
   note_launch();
 }
 
@@ -425,7 +425,7 @@ void bat_rows_launch64(const DCSR& A, int m, int mode, const double* val, const 
   switch (mode) {
     case kSpmm: launch_bat<double, kSpmm>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
     case kResid: launch_bat<double, kResid>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
-    case kCheb: launch_bat<double, kCheb>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    case kBatCheb: launch_bat<double, kBatCheb>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
     default: launch_bat<double, kAdd>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
   }
 }
@@ -434,7 +434,7 @@ void bat_rows_launch32(const DCSR& A, int m, int mode, const float* val, const f
   switch (mode) {
     case kSpmm: launch_bat<float, kSpmm>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
     case kResid: launch_bat<float, kResid>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
-    case kCheb: launch_bat<float, kCheb>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
+    case kBatCheb: launch_bat<float, kBatCheb>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
     default: launch_bat<float, kAdd>(A, m, val, X, B, Y, D, dinv, c1, c2, s); break;
   }
 }

@@ -327,6 +327,9 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   GIAMG_CHECK(opt.row_threads == 0 || opt.row_threads == 4 || opt.row_threads == 8 || opt.row_threads == 16 ||
                   opt.row_threads == 32,
               GIAMG_ERR_ARG, "row_threads must be 0, 4, 8, 16 or 32");
+  GIAMG_CHECK(opt.prefetch_rows >= -1, GIAMG_ERR_ARG, "prefetch_rows must be -1, 0 or positive");
+  GIAMG_CHECK(opt.row_chains == 0 || opt.row_chains == 2 || opt.row_chains == 4 || opt.row_chains == 8, GIAMG_ERR_ARG,
+              "row_chains must be 0, 2, 4 or 8");
   const bool dev = opt.device_ptrs != 0;
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -460,6 +463,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       }
       if (opt.autotune) tune_rows(L.A, s);
       else choose_rows(L.A, opt.row_form, opt.row_threads);
+      set_prefetch(L.A, opt.prefetch_rows, opt.row_chains);
       alloc_work(L, s);
       if (L.kind != GIAMG_LEVEL_COARSEST) {
         L.rho = lanczos_rho(L.A, opt.lanczos_steps, opt.hash_kind, H);
@@ -484,38 +488,42 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
 }
 
 // staging of caller vectors in host mode
-struct InVec {
-  const double* d = nullptr;
-  DBuf<double> buf;
-  InVec(const double* p, int64_t n, bool dev, cudaStream_t s) {
+template <typename T>
+struct InVecT {
+  const T* d = nullptr;
+  DBuf<T> buf;
+  InVecT(const T* p, int64_t n, bool dev, cudaStream_t s) {
     if (dev) d = p;
     else {
       buf.alloc(std::max<int64_t>(n, 1), s);
-      GIAMG_CUDA(cudaMemcpyAsync(buf.get(), p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      GIAMG_CUDA(cudaMemcpyAsync(buf.get(), p, sizeof(T) * n, cudaMemcpyHostToDevice, s));
       d = buf.get();
     }
   }
 };
-struct OutVec {
-  double* d = nullptr;
-  double* host = nullptr;
+template <typename T>
+struct OutVecT {
+  T* d = nullptr;
+  T* host = nullptr;
   int64_t n;
   cudaStream_t s;
-  DBuf<double> buf;
-  OutVec(double* p, int64_t n_, bool dev, cudaStream_t s_, bool load) : n(n_), s(s_) {
+  DBuf<T> buf;
+  OutVecT(T* p, int64_t n_, bool dev, cudaStream_t s_, bool load) : n(n_), s(s_) {
     if (dev) d = p;
     else {
       host = p;
       buf.alloc(std::max<int64_t>(n, 1), s);
       d = buf.get();
-      if (load) GIAMG_CUDA(cudaMemcpyAsync(d, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      if (load) GIAMG_CUDA(cudaMemcpyAsync(d, p, sizeof(T) * n, cudaMemcpyHostToDevice, s));
     }
   }
   void finish() {
-    if (host) GIAMG_CUDA(cudaMemcpyAsync(host, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (host) GIAMG_CUDA(cudaMemcpyAsync(host, d, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
     GIAMG_CUDA(cudaStreamSynchronize(s));
   }
 };
+using InVec = InVecT<double>;
+using OutVec = OutVecT<double>;
 
 int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, double* x_out, double rtol, int* iters,
                double* relres) {
@@ -817,6 +825,8 @@ void giamg_default_options(giamg_options* o) {
   o->autotune = 0;
   o->row_form = 0;
   o->row_threads = 0;
+  o->prefetch_rows = -1;
+  o->row_chains = 0;
 }
 
 int giamg_setup(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int32_t n_elem,
@@ -986,6 +996,20 @@ int giamg_level_spmv(giamg_handle h, int level, const double* x, double* y) {
     InVec xi(x, L.A.n, dev, C.H->stream);
     OutVec yo(y, L.A.n, dev, C.H->stream, false);
     spmv(L.A, xi.d, yo.d, C.H->stream, L.avg_row);
+    yo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_spmv32(giamg_handle h, int level, const float* x, float* y) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(x && y, GIAMG_ERR_ARG, "x and y are required");
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVecT<float> xi(x, L.A.n, dev, C.H->stream);
+    OutVecT<float> yo(y, L.A.n, dev, C.H->stream, false);
+    spmv32(L.A, xi.d, yo.d, C.H->stream, L.avg_row);
     yo.finish();
     return GIAMG_OK;
   });

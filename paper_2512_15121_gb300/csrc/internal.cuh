@@ -82,6 +82,7 @@ struct Pattern {
   DBuf<int32_t> tid;
   DBuf<int64_t> tptr;
   DBuf<int32_t> toff;
+  DBuf<int32_t> obase;  // obase[i] = tptr[tid[i]]: where row i's offsets start in toff
 };
 
 // Row groups: rows with identical column sets; group g holds rows grow[rptr[g] .. rptr[g+1]) and
@@ -99,8 +100,9 @@ struct Groups {
 struct RowVariant {
   int tpr = 0;       // 0: not tuned, choose from the average row length
   bool pat = false;
-  int unroll = 2;    // independent load chains per thread and step (pattern form: 2 or 4)
+  int unroll = 2;    // independent load chains per thread and step (pattern form: 2, 4 or 8)
   bool group = false;  // row-group form (one CTA per group, x gathered once into shared memory)
+  int64_t prefetch = 0;  // pattern form: L2 prefetch distance in rows (0: none)
 };
 
 struct DCSR {
@@ -217,6 +219,9 @@ constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
 // SpMV family on a CSR level (FP64 and FP32 values)
+// row-kernel modes
+enum RowMode { kSpmv = 0, kResidual = 1, kCheb = 2, kAddSpmv = 3 };
+
 void spmv(const DCSR& A, const double* x, double* y, cudaStream_t s, double avg_row);
 void spmv32(const DCSR& A, const float* x, float* y, cudaStream_t s, double avg_row);
 // y = b - A x
@@ -321,6 +326,8 @@ void csr_to32(DCSR& A, cudaStream_t s);
 void tune_rows(DCSR& A, cudaStream_t s);
 // set A.var64 / A.var32 from forced options or the defaults measured best inside the solve
 void choose_rows(DCSR& A, int form, int threads);
+// prefetch_rows -1: automatic, 0: off, > 0: distance in rows; chains 0: keep, else 2, 4 or 8
+void set_prefetch(DCSR& A, int prefetch_rows, int chains);
 // detect row groups with identical column sets (exact; leaves A.grp off if not worthwhile)
 bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups);
 // detect repeated row patterns (exact; returns false and leaves A.pat off if not worthwhile)

@@ -162,6 +162,13 @@ __global__ void compact_reps(int64_t cap, const int32_t* __restrict__ flag, cons
   }
 }
 
+// Start of each row's template offsets, so the row kernels read one index per row instead of
+// the dependent pair tid -> tptr.
+__global__ void row_obase(int64_t n, const int32_t* __restrict__ tid, const int64_t* __restrict__ tptr,
+                          int32_t* __restrict__ obase) {
+  GRID_STRIDE(i, n) obase[i] = (int32_t)tptr[tid[i]];
+}
+
 __global__ void assign_tid(int64_t T, const int64_t* __restrict__ slot_sorted, int* __restrict__ slot_tid) {
   GRID_STRIDE(t, T) slot_tid[slot_sorted[t]] = (int)t;
 }
@@ -281,6 +288,9 @@ bool pattern_build(DCSR& A, cudaStream_t s, int64_t max_templates, int64_t max_o
     P.toff.release();
     return false;
   }
+  P.obase.alloc(n, s);
+  { row_obase<<<blocks(n), 256, 0, s>>>(n, P.tid.get(), P.tptr.get(), P.obase.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
   P.n_templates = T;
   P.n_offsets = total;
   P.on = true;

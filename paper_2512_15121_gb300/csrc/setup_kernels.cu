@@ -846,7 +846,7 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
 }
 
 void csr_to32(DCSR& A, cudaStream_t s) {
-  A.v32.alloc(std::max<int64_t>(A.nnz, 1), s);
+  A.v32.alloc((size_t)A.nnz + 4, s);  // 16 bytes of tail room for L2 prefetches widened to 16 bytes
   if (A.nnz) { to32v<<<blocks_for(A.nnz, 256, 65535), 256, 0, s>>>(A.v.get(), A.v32.get(), A.nnz); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }

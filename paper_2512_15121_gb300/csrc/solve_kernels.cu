@@ -26,7 +26,6 @@ inline unsigned grid_for(int64_t work, int per_block) {
 
 // ------------------------------------------------------------------ CSR row kernels
 // TPR threads cooperate on one row; the group's partial sums are combined with shuffles.
-enum RowMode { kSpmv = 0, kResidual = 1, kCheb = 2, kAddSpmv = 3 };
 
 template <int TPR, typename V, int MODE>
 __global__ void __launch_bounds__(kThreads) csr_rows(int64_t n, const int64_t* __restrict__ rp,
@@ -66,26 +65,47 @@ __global__ void __launch_bounds__(kThreads) csr_rows(int64_t n, const int64_t* _
   }
 }
 
+// Prefetch the bytes [lo, hi) of an array into L2 with one bulk request: lo and hi are widened to
+// 16-byte boundaries, hi clipped to `end` (the array's size rounded down to 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void* base, int64_t lo, int64_t hi, int64_t end) {
+  lo &= ~(int64_t)15;
+  hi = min((hi + 15) & ~(int64_t)15, end);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const char*>(base) + lo),
+                 "r"((uint32_t)(hi - lo))
+                 : "memory");
+}
+
 // Row kernels on a pattern-compressed matrix: the columns of row i are i + off[k] for the
 // offsets of the row's template, which stay in L1/L2 while the values stream from HBM.
 // TPR threads per row; consecutive threads take consecutive entries, so the x gathers of one
 // instruction fall in a few runs of neighbouring columns.
+//
+// Blocks start roughly in row order, so with pf > 0 the first thread of every block prefetches
+// into L2 (one bulk request) the values of the block pf rows ahead: by the time that block runs,
+// its value loads wait on L2 instead of HBM.
 template <int TPR, int U, typename V, int MODE>
-__device__ __forceinline__ void pat_body(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ tid,
-                                         const int64_t* __restrict__ tptr, const int32_t* __restrict__ toff,
+__device__ __forceinline__ void pat_body(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ obase,
+                                         const int32_t* __restrict__ toff,
                                          const V* __restrict__ val, const V* __restrict__ x, const V* __restrict__ b,
-                                         V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2) {
+                                         V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2,
+                                         int64_t pf, int64_t vend) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = gt / TPR;
   const int lane = threadIdx.x % TPR;
   const bool valid = row < n;
+  if (pf > 0 && threadIdx.x == 0) {
+    const int64_t rows = blockDim.x / TPR;
+    const int64_t r0 = (int64_t)blockIdx.x * rows + pf;
+    if (r0 < n) prefetch_l2(val, rp[r0] * (int64_t)sizeof(V), rp[min(r0 + rows, n)] * (int64_t)sizeof(V), vend);
+  }
   V acc[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) acc[u] = 0;
   if (valid) {
     const int64_t s = rp[row];
     const int len = (int)(rp[row + 1] - s);
-    const int32_t* __restrict__ off = toff + tptr[tid[row]];
+    const int32_t* __restrict__ off = toff + obase[row];
     const V* __restrict__ vr = val + s;
     const V* __restrict__ xr = x + row;
     int k = lane;
@@ -96,20 +116,20 @@ __device__ __forceinline__ void pat_body(int64_t n, const int64_t* __restrict__ 
       }
       if (k < len) acc[0] = fma(__ldcs(vr + k), xr[__ldg(off + k)], acc[0]);
     } else {
-      // U independent (offset -> gather -> fma) chains per step: offsets and values first,
-      // then the gathers, so U memory latencies overlap
-      for (; k + (U - 1) * TPR < len; k += U * TPR) {
+      // U independent (offset -> gather -> fma) chains per step, the last step predicated: all
+      // U offsets and values are requested before the gathers, so U latencies overlap
+      for (; k < len; k += U * TPR) {
         int o[U];
         V v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          o[u] = __ldg(off + k + u * TPR);
-          v[u] = __ldcs(vr + k + u * TPR);
+          const bool in = k + u * TPR < len;
+          o[u] = in ? __ldg(off + k + u * TPR) : 0;
+          v[u] = in ? __ldcs(vr + k + u * TPR) : V(0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) acc[u] = fma(v[u], xr[o[u]], acc[u]);
       }
-      for (; k < len; k += TPR) acc[0] = fma(__ldcs(vr + k), xr[__ldg(off + k)], acc[0]);
     }
   }
 #pragma unroll
@@ -135,11 +155,11 @@ __device__ __forceinline__ void pat_body(int64_t n, const int64_t* __restrict__ 
 #define PAT_KERNEL(NAME, V, MODE)                                                                              \
   template <int TPR, int U>                                                                                   \
   __global__ void __launch_bounds__(kThreads)                                                                 \
-      NAME(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ tid,                        \
-           const int64_t* __restrict__ tptr, const int32_t* __restrict__ toff, const V* __restrict__ val,     \
+      NAME(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ obase,                      \
+           const int32_t* __restrict__ toff, const V* __restrict__ val,     \
            const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,            \
-           const V* __restrict__ dinv, V c1, V c2) {                                                          \
-    pat_body<TPR, U, V, MODE>(n, rp, tid, tptr, toff, val, x, b, y, d, dinv, c1, c2);                        \
+           const V* __restrict__ dinv, V c1, V c2, int64_t pf, int64_t vend) {                                \
+    pat_body<TPR, U, V, MODE>(n, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, pf, vend);              \
   }
 PAT_KERNEL(pat_spmv_f64, double, kSpmv)
 PAT_KERNEL(pat_spmv_f32, float, kSpmv)
@@ -265,11 +285,16 @@ void launch_grp(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
 
 template <int TPR, int U, typename V, int MODE>
 void launch_pat(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
-                cudaStream_t s) {
+                int64_t pf, cudaStream_t s) {
   const int64_t n = A.n;
+  // L2 prefetches stay inside the level's own value arrays (other arrays: no prefetch)
+  int64_t vend = 0;
+  if ((const void*)val == (const void*)A.v32.get()) vend = (int64_t)(A.v32.n * sizeof(float)) & ~(int64_t)15;
+  if ((const void*)val == (const void*)A.v.get()) vend = (int64_t)(A.v.n * sizeof(double)) & ~(int64_t)15;
+  if (!vend) pf = 0;
   auto k = PatKernel<V, MODE>::template get<TPR, U>();
-  k<<<grid_for(n * TPR, kThreads), kThreads, 0, s>>>(n, A.rp.get(), A.pat.tid.get(), A.pat.tptr.get(),
-                                                     A.pat.toff.get(), val, x, b, y, d, dinv, c1, c2);
+  k<<<grid_for(n * TPR, kThreads), kThreads, 0, s>>>(n, A.rp.get(), A.pat.obase.get(), A.pat.toff.get(), val, x, b, y,
+                                                     d, dinv, c1, c2, pf, vend);
   note_launch();
 }
 
@@ -292,19 +317,26 @@ void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* v
   const bool pat = var.tpr ? var.pat : A.pat.on;
   if (var.group && A.grp.on) {
     launch_grp<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
+  } else if (pat && var.unroll == 8) {
+    switch (tpr) {
+      case 32: launch_pat<32, 8, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      case 16: launch_pat<16, 8, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      case 8: launch_pat<8, 8, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      default: launch_pat<4, 8, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+    }
   } else if (pat && var.unroll == 4) {
     switch (tpr) {
-      case 32: launch_pat<32, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
-      case 16: launch_pat<16, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
-      case 8: launch_pat<8, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
-      default: launch_pat<4, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 32: launch_pat<32, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      case 16: launch_pat<16, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      case 8: launch_pat<8, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      default: launch_pat<4, 4, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
     }
   } else if (pat) {
     switch (tpr) {
-      case 32: launch_pat<32, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
-      case 16: launch_pat<16, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
-      case 8: launch_pat<8, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
-      default: launch_pat<4, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s); break;
+      case 32: launch_pat<32, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      case 16: launch_pat<16, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      case 8: launch_pat<8, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
+      default: launch_pat<4, 2, V, MODE>(A, val, x, b, y, d, dinv, c1, c2, var.prefetch, s); break;
     }
   } else {
     switch (tpr) {
@@ -756,6 +788,18 @@ void choose_rows(DCSR& A, int form, int threads) {
     if (threads && !v.group) v.tpr = threads;
     (prec == 0 ? A.var64 : A.var32) = v;
   }
+}
+
+// Default L2 prefetch distance of the pattern kernels, about the rows of half the warps resident
+// on the whole GPU at once (152 SMs x 64 warps), measured best among 0 to 4x that on the
+// 16^3, p = 6 operator.
+constexpr int64_t kPrefetchRows = 152 * 32;
+
+void set_prefetch(DCSR& A, int prefetch_rows, int chains) {
+  const int64_t pf = prefetch_rows < 0 ? (A.nnz >= (1 << 22) ? kPrefetchRows : 0) : prefetch_rows;
+  A.var32.prefetch = pf;
+  A.var64.prefetch = pf;
+  if (chains) A.var32.unroll = A.var64.unroll = chains;
 }
 
 void tune_rows(DCSR& A, cudaStream_t s) {

@@ -326,3 +326,39 @@ def test_row_kernel_forms_match_oracle(form, threads):
         assert np.linalg.norm(X.cpu().numpy()[:, 0] - xo) <= 1e-10 * np.linalg.norm(xo)
     finally:
         gpu.close()
+
+
+def fp32_product_bound(rp, ci, v, x):
+    """y = fl32(A) fl32(x) evaluated in FP64 from the FP32-rounded operands (the definition of the
+    FP32 product up to the FP32 accumulation), and the bound n_row * 2^-23 * |fl32(A)||fl32(x)|
+    on the accumulation error of any summation order."""
+    import scipy.sparse as sp
+    n = len(rp) - 1
+    v32 = v.astype(np.float32).astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    A32 = sp.csr_matrix((v32, ci, rp), shape=(n, n))
+    absA = sp.csr_matrix((np.abs(v32), ci, rp), shape=(n, n))
+    lens = np.diff(rp).astype(np.float64)
+    return A32 @ x32, (lens + 1) * 2.0 ** -23 * (absA @ np.abs(x32))
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+def test_fp32_level_product(form):
+    """The FP32 product of every level through the level's FP32 row kernel, against the product of
+    the FP32-rounded operands: within the accumulation bound, row by row."""
+    if "p" not in _forms_oracle:
+        prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
+        _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
+    prob, orc = _forms_oracle["p"]
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, row_form=form)
+    try:
+        rng = np.random.default_rng(11)
+        for l in range(orc.num_levels):
+            rp, ci, v, _ = orc.level(l)
+            x = rng.normal(size=len(rp) - 1)
+            y = gpu.spmv32(l, dev(x)).cpu().numpy().astype(np.float64)
+            ref, bound = fp32_product_bound(rp, ci, v, x)
+            assert np.all(np.abs(y - ref) <= bound), l
+            assert np.max(np.abs(y - ref)) <= 1e-5 * np.max(np.abs(ref)), l
+    finally:
+        gpu.close()
