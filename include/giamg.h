@@ -92,6 +92,11 @@ typedef struct {
                              block this many rows ahead; 0 off, -1 (default) automatic */
   int row_chains;         /* row-pattern kernels: independent load chains per thread (2, 4, 8);
                              0 (default) automatic */
+  int graphs;             /* 1 (default): giamg_solve runs the whole PCG loop as one CUDA graph
+                             (captured on the first solve of each precision) whose convergence
+                             test runs on the device; 0: a host loop with one synchronisation
+                             per iteration.  Both give the same iterations and bits.  The host
+                             loop is used while profiling or when force_iters > max_iter. */
 } giamg_options;
 
 /* Fill *opt with the defaults listed above. */

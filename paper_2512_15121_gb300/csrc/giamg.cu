@@ -22,6 +22,10 @@ void set_error(int code, const std::string& msg) {
 }
 
 Hierarchy::~Hierarchy() {
+  for (SolveGraph& G : graph)
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (capture_stream) cudaStreamDestroy(capture_stream);
+  if (h_gst) cudaFreeHost(h_gst);
   for (Level* L : lev) delete L;
   lev.clear();
   if (h_sc) cudaFreeHost(h_sc);
@@ -525,6 +529,126 @@ struct OutVecT {
 using InVec = InVecT<double>;
 using OutVec = OutVecT<double>;
 
+// The two halves of a PCG iteration (Sec. 2: one product with A and one V-cycle per iteration),
+// shared by the host-driven loop and the loop captured as a CUDA graph.
+// precondition: z = V(r); rho = <z, r> (flexible: <z, r - r_old>); p = z + beta p (p = z first)
+void pcg_precondition(Ctx& C, int precision, int first) {
+  Hierarchy& H = *C.H;
+  const int flexible = precision ? 1 : 0;
+  const double* z = apply_vcycle(C, precision, H.r.get());
+  pcg_dot_rz(H.n, H.r.get(), z, H.rold.get(), flexible, H.partial.get(), H.stream);
+  pcg_finish_rz(H.sc.get(), H.partial.get(), first, flexible, H.stream);
+  pcg_update_p(H.n, z, H.p.get(), H.sc.get(), first, H.stream);
+}
+// step: q = A p; alpha = rho / <p, q>; x += alpha p; r -= alpha q; ||r||^2
+void pcg_step(Ctx& C, int precision, double* x) {
+  Hierarchy& H = *C.H;
+  Level& L0 = *H.lev[0];
+  cudaStream_t s = H.stream;
+  const int pr = prof_begin(H, kProfOuterSpmv);
+  spmv(L0.A, H.p.get(), H.q.get(), s, L0.avg_row);
+  prof_end(H, pr, row_bytes(L0.A, 8, 0));
+  dot_partial(H.n, H.p.get(), H.q.get(), H.partial.get(), s);
+  pcg_finish_pq(H.sc.get(), H.partial.get(), s);
+  pcg_update_xr(H.n, H.p.get(), H.q.get(), x, H.r.get(), H.rold.get(), precision ? 1 : 0, H.sc.get(), H.partial.get(), s);
+  pcg_finish_rr(H.sc.get(), H.partial.get(), s);
+}
+
+// Append a conditional node to the graph being captured on `cs` (after the work captured so far,
+// and before what is captured next); returns its body graph.
+cudaGraph_t add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  GIAMG_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &edges, &nd));
+  GIAMG_CHECK(st == cudaStreamCaptureStatusActive, GIAMG_ERR_CUDA, "stream capture is not active");
+  cudaGraphNodeParams prm{};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  GIAMG_CUDA(cudaGraphAddNode(&node, g, deps, edges, nd, &prm));
+  GIAMG_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return prm.conditional.phGraph_out[0];
+}
+
+// Capture the whole PCG solve for one V-cycle precision as a CUDA graph:
+//   init (r = b, x = 0, ||b||^2); start (relres_0, go = b != 0);
+//   IF go: precondition (first);
+//   WHILE cont: step; check (relres, stopping rule -> cont); IF cont: precondition.
+// The graph reads b from H.gb and writes x to H.gx; rtol and the limit are read from H.gst.
+void capture_solve(Ctx& C, int precision) {
+  Hierarchy& H = *C.H;
+  SolveGraph& G = H.graph[precision];
+  if (!H.capture_stream) GIAMG_CUDA(cudaStreamCreateWithFlags(&H.capture_stream, cudaStreamNonBlocking));
+  const int64_t cap = (int64_t)H.opt.max_iter + 1;
+  if (!H.gb.get()) {
+    H.gb.alloc(H.n, H.stream);
+    H.gx.alloc(H.n, H.stream);
+    H.ghist.alloc(cap, H.stream);
+    H.gst.alloc(1, H.stream);
+    GIAMG_CUDA(cudaMallocHost((void**)&H.h_gst, sizeof(GraphState)));
+  }
+  GIAMG_CUDA(cudaStreamSynchronize(H.stream));  // buffers ready before the capture stream uses them
+  cudaStream_t user = H.stream;
+  cudaStream_t cs = H.capture_stream;
+  cudaGraph_t g = nullptr;
+  struct Restore {  // the launchers use H.stream: point it at the capture stream meanwhile
+    Hierarchy& H;
+    cudaStream_t user;
+    cudaGraph_t& g;
+    ~Restore() {
+      H.stream = user;
+      cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(H.capture_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t partial = nullptr;  // a capture that failed part way: end and drop it
+        cudaStreamEndCapture(H.capture_stream, &partial);
+        if (partial && partial != g) cudaGraphDestroy(partial);
+      }
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+    }
+  } restore{H, user, g};
+  H.stream = cs;
+  GIAMG_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h_first, h_loop, h_more;
+  GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_first, g, 0, cudaGraphCondAssignDefault));
+  GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_loop, g, 0, cudaGraphCondAssignDefault));
+  const long long c0 = g_launches.load();
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pcg_init(H.n, H.gb.get(), H.gx.get(), H.r.get(), H.partial.get(), cs);
+  pcg_finish_bb(H.sc.get(), H.partial.get(), cs);
+  pcg_graph_start(H.sc.get(), H.gst.get(), H.ghist.get(), h_first, h_loop, cs);
+  cudaGraph_t body_first = add_conditional(cs, h_first, cudaGraphCondTypeIf);
+  cudaGraph_t body_loop = add_conditional(cs, h_loop, cudaGraphCondTypeWhile);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &g));
+  const long long c1 = g_launches.load();
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_first, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pcg_precondition(C, precision, 1);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &body_first));
+  const long long c2 = g_launches.load();
+  GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_more, body_loop, 0, cudaGraphCondAssignDefault));
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_loop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pcg_step(C, precision, H.gx.get());
+  pcg_graph_check(H.sc.get(), H.gst.get(), H.ghist.get(), h_loop, h_more, cs);
+  cudaGraph_t body_more = add_conditional(cs, h_more, cudaGraphCondTypeIf);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &body_loop));
+  const long long c3 = g_launches.load();
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_more, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pcg_precondition(C, precision, 0);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &body_more));
+  const long long c4 = g_launches.load();
+  GIAMG_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
+  G.n_init = c1 - c0;
+  G.n_first = c2 - c1;
+  G.n_loop = c3 - c2;
+  G.n_more = c4 - c3;
+  g_launches.fetch_sub(c4 - c0);  // captured, not executed
+}
+
 int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, double* x_out, double rtol, int* iters,
                double* relres) {
   Hierarchy& H = *C.H;
@@ -534,61 +658,75 @@ int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, doubl
   GIAMG_CHECK(b_in && x_out, GIAMG_ERR_ARG, "b and x are required");
   GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
   GIAMG_CHECK(rtol >= 0.0, GIAMG_ERR_ARG, "rtol must be non-negative");
-  InVec b(b_in, n, dev, s);
-  OutVec x(x_out, n, dev, s, false);
-  Level& L0 = *H.lev[0];
-  const int flexible = precision ? 1 : 0;
-  double* partial = H.partial.get();
-  Scalars* sc = H.sc.get();
-  H.hist.clear();
-  pcg_init(n, b.d, x.d, H.r.get(), partial, s);
-  pcg_finish_bb(sc, partial, s);
-  GIAMG_CUDA(cudaMemcpyAsync(H.h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaStreamSynchronize(s));
-  const double bb = H.h_sc->bb;
+  const int limit = force_iters > 0 ? force_iters : H.opt.max_iter;
   int it = 0;
   double rr = 1.0;
   int status = GIAMG_OK;
-  if (bb == 0.0) {
-    H.hist.push_back(0.0);
-    rr = 0.0;
+  // the graph path: profiling off (its events are host-recorded) and the limit within the
+  // capacity of the captured history
+  const bool graph = H.opt.graphs && !H.prof.on && limit <= H.opt.max_iter;
+  if (graph) {
+    if (!H.graph[precision].exec) capture_solve(C, precision);
+    const SolveGraph& G = H.graph[precision];
+    GIAMG_CUDA(cudaMemcpyAsync(H.gb.get(), b_in, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    GraphState& hs = *H.h_gst;
+    hs = GraphState{rtol, 1.0, limit, force_iters > 0 ? 1 : 0, 0, 0};
+    GIAMG_CUDA(cudaMemcpyAsync(H.gst.get(), &hs, sizeof(GraphState), cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaGraphLaunch(G.exec, s));
+    GIAMG_CUDA(cudaMemcpyAsync(&hs, H.gst.get(), sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(x_out, H.gx.get(), sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    vec_copy(n, H.gb.get(), H.tmp.get(), s);  // b and x for the true residual of giamg_solve_stats
+    vec_copy(n, H.gx.get(), H.xw.get(), s);
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    it = hs.it;
+    rr = hs.relres;
+    status = hs.status;
+    H.hist.assign((size_t)it + 1, 0.0);
+    GIAMG_CUDA(cudaMemcpyAsync(H.hist.data(), H.ghist.get(), sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    if (status) H.hist.resize(it);  // breakdown: the last iteration recorded no residual
+    const long long run = G.n_init + (H.hist[0] != 0.0 && limit > 0 ? G.n_first + it * G.n_loop + std::max(it - 1, 0) * G.n_more : 0);
+    g_launches.fetch_add(run);
+    if (status == GIAMG_OK && H.hist[0] != 0.0 && force_iters <= 0 && !(rr <= rtol)) status = GIAMG_ERR_MAXITER;
+    if (H.hist[0] == 0.0) rr = 0.0;
   } else {
-    H.hist.push_back(1.0);
-    const double* z = apply_vcycle(C, precision, H.r.get());
-    pcg_dot_rz(n, H.r.get(), z, H.rold.get(), flexible, partial, s);
-    pcg_finish_rz(sc, partial, 1, flexible, s);
-    pcg_update_p(n, z, H.p.get(), sc, 1, s);
-    const int limit = force_iters > 0 ? force_iters : H.opt.max_iter;
-    while (it < limit) {
-      const int pr = prof_begin(H, kProfOuterSpmv);
-      spmv(L0.A, H.p.get(), H.q.get(), s, L0.avg_row);
-      prof_end(H, pr, row_bytes(L0.A, 8, 0));
-      dot_partial(n, H.p.get(), H.q.get(), partial, s);
-      pcg_finish_pq(sc, partial, s);
-      pcg_update_xr(n, H.p.get(), H.q.get(), x.d, H.r.get(), H.rold.get(), flexible, sc, partial, s);
-      pcg_finish_rr(sc, partial, s);
-      GIAMG_CUDA(cudaMemcpyAsync(H.h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-      GIAMG_CUDA(cudaStreamSynchronize(s));
-      ++it;
-      if (H.h_sc->status != 0) {
-        status = GIAMG_ERR_BREAKDOWN;
-        break;
+    InVec b(b_in, n, dev, s);
+    OutVec x(x_out, n, dev, s, false);
+    Scalars* sc = H.sc.get();
+    H.hist.clear();
+    pcg_init(n, b.d, x.d, H.r.get(), H.partial.get(), s);
+    pcg_finish_bb(sc, H.partial.get(), s);
+    GIAMG_CUDA(cudaMemcpyAsync(H.h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    const double bb = H.h_sc->bb;
+    if (bb == 0.0) {
+      H.hist.push_back(0.0);
+      rr = 0.0;
+    } else {
+      H.hist.push_back(1.0);
+      if (limit > 0) pcg_precondition(C, precision, 1);
+      while (it < limit) {
+        pcg_step(C, precision, x.d);
+        GIAMG_CUDA(cudaMemcpyAsync(H.h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+        GIAMG_CUDA(cudaStreamSynchronize(s));
+        ++it;
+        if (H.h_sc->status != 0) {
+          status = GIAMG_ERR_BREAKDOWN;
+          break;
+        }
+        rr = std::sqrt(H.h_sc->rr / bb);
+        H.hist.push_back(rr);
+        if (force_iters <= 0 && rr <= rtol) break;
+        if (it == limit) break;
+        pcg_precondition(C, precision, 0);
       }
-      rr = std::sqrt(H.h_sc->rr / bb);
-      H.hist.push_back(rr);
-      if (force_iters <= 0 && rr <= rtol) break;
-      if (it == limit) break;
-      z = apply_vcycle(C, precision, H.r.get());
-      pcg_dot_rz(n, H.r.get(), z, H.rold.get(), flexible, partial, s);
-      pcg_finish_rz(sc, partial, 0, flexible, s);
-      pcg_update_p(n, z, H.p.get(), sc, 0, s);
+      if (status == GIAMG_OK && force_iters <= 0 && !(rr <= rtol)) status = GIAMG_ERR_MAXITER;
     }
-    if (status == GIAMG_OK && force_iters <= 0 && !(rr <= rtol)) status = GIAMG_ERR_MAXITER;
+    // keep b and x for the true residual of giamg_solve_stats
+    vec_copy(n, b.d, H.tmp.get(), s);
+    vec_copy(n, x.d, H.xw.get(), s);
+    x.finish();
   }
-  // keep b and x for the true residual of giamg_solve_stats
-  vec_copy(n, b.d, H.tmp.get(), s);
-  vec_copy(n, x.d, H.xw.get(), s);
-  x.finish();
   H.last_iters = it;
   H.last_true_relres = -1.0;
   if (iters) *iters = it;
@@ -826,6 +964,7 @@ void giamg_default_options(giamg_options* o) {
   o->row_form = 0;
   o->row_threads = 0;
   o->prefetch_rows = -1;
+  o->graphs = 1;
   o->row_chains = 0;
 }
 

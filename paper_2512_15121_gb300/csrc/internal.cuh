@@ -165,6 +165,24 @@ struct Scalars {  // PCG scalars kept on the device
   int pad;
 };
 
+// Device-side state of the solve captured as a CUDA graph: the stopping rule's inputs (rtol, the
+// iteration limit, whether the count is forced) and outputs (iterations, last relres, status).
+struct GraphState {
+  double rtol;
+  double relres;
+  int limit;
+  int force;
+  int it;
+  int status;
+};
+
+// One instantiated solve graph (per V-cycle precision) and the kernel launches of its parts, so
+// the launch counter can be advanced by what a run executed.
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long n_init = 0, n_first = 0, n_loop = 0, n_more = 0;
+};
+
 // Opt-in CUDA-event timers by category (they add event records to the stream)
 enum ProfCat {
   kProfL0Rows = 0,
@@ -207,6 +225,12 @@ struct Hierarchy {
   DBuf<double> bR, bZ, bP, bQ, bRold, bX, bB, bpartial;
   DBuf<unsigned char> bsc;
   void* h_bsc = nullptr;
+  // the solve as a CUDA graph (internal right-hand side, solution and relres history)
+  SolveGraph graph[2];
+  cudaStream_t capture_stream = nullptr;
+  DBuf<double> gb, gx, ghist;
+  DBuf<GraphState> gst;
+  GraphState* h_gst = nullptr;  // pinned host copy
   ~Hierarchy();
 };
 
@@ -277,6 +301,11 @@ void pcg_finish_pq(Scalars* sc, const double* partial, cudaStream_t s);
 void pcg_update_xr(int64_t n, const double* p, const double* q, double* x, double* r, double* rold, int flexible,
                    const Scalars* sc, double* partial, cudaStream_t s);
 void pcg_finish_rr(Scalars* sc, const double* partial, cudaStream_t s);
+// control of the graph-captured loop (graph_kernels.cu)
+void pcg_graph_start(const Scalars* sc, GraphState* st, double* hist, cudaGraphConditionalHandle first,
+                     cudaGraphConditionalHandle loop, cudaStream_t s);
+void pcg_graph_check(const Scalars* sc, GraphState* st, double* hist, cudaGraphConditionalHandle loop,
+                     cudaGraphConditionalHandle more, cudaStream_t s);
 void reduce_to(const double* partial, double* out, cudaStream_t s);
 
 // multi-right-hand-side kernels (batch_kernels.cu); modes: 0 SpMM, 1 residual, 2 Chebyshev, 3 add

@@ -362,3 +362,58 @@ def test_fp32_level_product(form):
             assert np.max(np.abs(y - ref)) <= 1e-5 * np.max(np.abs(ref)), l
     finally:
         gpu.close()
+
+
+@pytest.mark.parametrize("name", ["cube4_p4", "jitter8_p2_poisson", "graded345_p8_kappa"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_solve_equals_host_loop(name, precision):
+    """The solve captured as one CUDA graph (device-side stopping rule) and the host-driven loop give
+    the same iterations, relres history and solution bits, and execute the same kernels."""
+    prob, orc, gpu, k = setup_case(name)
+    host_loop = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=0)
+    try:
+        b = dev(prob.b)
+        for force in (None, 3):
+            c0 = g.launch_count()
+            xg, itg, rrg = gpu.solve(b, rtol=1e-8, precision=precision, force_iters=force)
+            c1 = g.launch_count()
+            xh, ith, rrh = host_loop.solve(b, rtol=1e-8, precision=precision, force_iters=force)
+            c2 = g.launch_count()
+            hg, _ = gpu.stats(itg + 1)
+            hh, _ = host_loop.stats(ith + 1)
+            assert itg == ith and rrg == rrh and torch.equal(xg, xh)
+            assert np.array_equal(hg, hh)
+            # the executed kernels: the host loop's plus the graph's start and per-iteration checks
+            assert c1 - c0 == (c2 - c1) + 1 + itg
+    finally:
+        host_loop.close()
+
+
+def test_graph_solve_edge_cases():
+    prob, orc, gpu, k = setup_case("cube4_p4")
+    # b = 0: no iteration, x = 0
+    x, it, rr = gpu.solve(dev(np.zeros(prob.n)), rtol=1e-8)
+    assert it == 0 and rr == 0.0 and torch.count_nonzero(x) == 0
+    # the iteration limit: MAXITER reported, x the iterate after max_iter steps (as the host loop)
+    lim = g.Solver.from_problem(prob, device=True, cheb_degree=k, max_iter=2)
+    ref = g.Solver.from_problem(prob, device=True, cheb_degree=k, max_iter=2, graphs=0)
+    try:
+        xg, itg, rrg = lim.solve(dev(prob.b), rtol=1e-14)
+        xh, ith, rrh = ref.solve(dev(prob.b), rtol=1e-14)
+        assert lim.last_status == g.GIAMG_ERR_MAXITER == ref.last_status
+        assert itg == ith == 2 and rrg == rrh and torch.equal(xg, xh)
+        # more forced iterations than the captured history holds: the host loop takes over
+        xf, itf, _ = lim.solve(dev(prob.b), rtol=1e-8, force_iters=4)
+        xr, itr, _ = ref.solve(dev(prob.b), rtol=1e-8, force_iters=4)
+        assert itf == itr == 4 and torch.equal(xf, xr)
+    finally:
+        lim.close()
+        ref.close()
+    # host pointers through the graph path
+    gpu.set_device_ptrs(False)
+    try:
+        xh, ith, _ = gpu.solve(prob.b, rtol=1e-8)
+    finally:
+        gpu.set_device_ptrs(True)
+    xd, itd, _ = gpu.solve(dev(prob.b), rtol=1e-8)
+    assert ith == itd and np.array_equal(xh, xd.cpu().numpy())
