@@ -265,6 +265,9 @@ __device__ __forceinline__ void column_block_sum(double v, int m, double* sh, do
 struct BatchScalars {
   double rho[32], pq[32], alpha[32], beta[32], rr[32], bb[32];
   int status[32], active[32];
+  double tol2;  // rtol^2, and whether the iteration count is forced: written before each solve
+  int force;
+  int pad;
 };
 
 __global__ void __launch_bounds__(kRedThreads) bat_init(int64_t n, int m, const double* __restrict__ B,
@@ -364,14 +367,48 @@ __global__ void bat_finish_pq(BatchScalars* sc, const double* partial, int block
 }
 
 // after the update: record ||r_j||^2 and retire columns that reached the tolerance
-__global__ void bat_finish_rr(BatchScalars* sc, const double* partial, int blocks, int m, double tol2, int force) {
+__global__ void bat_finish_rr(BatchScalars* sc, const double* partial, int blocks, int m) {
   const int j = threadIdx.x;
   if (j >= m) return;
   const double rr = column_total(partial, blocks, j);
   if (!sc->active[j]) return;
   sc->rr[j] = rr;
   if (!(rr == rr) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
-  if (sc->status[j] != 0 || (!force && rr <= tol2 * sc->bb[j])) sc->active[j] = 0;
+  if (sc->status[j] != 0 || (!sc->force && rr <= sc->tol2 * sc->bb[j])) sc->active[j] = 0;
+}
+
+// The loop captured as a CUDA graph: per-column iteration counts (a column counts the iterations
+// it entered active), and the loop condition (some column active, the limit not reached, no
+// breakdown) set on the graph's conditional handles.
+__global__ void bat_graph_start(const BatchScalars* __restrict__ sc, int m, BatchGraphState* __restrict__ st,
+                                cudaGraphConditionalHandle first, cudaGraphConditionalHandle loop) {
+  int any = 0;
+  for (int j = 0; j < m; ++j) {
+    st->its[j] = 0;
+    st->was[j] = sc->active[j];
+    any |= st->was[j];
+  }
+  st->it = 0;
+  st->breakdown = 0;
+  const unsigned go = (any && st->limit > 0) ? 1u : 0u;
+  cudaGraphSetConditional(first, go);
+  cudaGraphSetConditional(loop, go);
+}
+__global__ void bat_graph_check(const BatchScalars* __restrict__ sc, int m, BatchGraphState* __restrict__ st,
+                                cudaGraphConditionalHandle loop, cudaGraphConditionalHandle more) {
+  const int it = st->it + 1;
+  st->it = it;
+  int any = 0, bd = 0;
+  for (int j = 0; j < m; ++j) {
+    if (st->was[j]) st->its[j] = it;
+    st->was[j] = sc->active[j];
+    any |= st->was[j];
+    bd |= sc->status[j] != 0;
+  }
+  st->breakdown = bd;
+  const unsigned cont = (any && it < st->limit && !bd) ? 1u : 0u;
+  cudaGraphSetConditional(loop, cont);
+  cudaGraphSetConditional(more, cont);
 }
 
 __global__ void bat_update_p(int64_t n, int m, const double* __restrict__ Z, double* __restrict__ P,
@@ -525,9 +562,19 @@ void bat_pcg_pq(int64_t n, int m, const double* P, const double* Q, double* part
   GIAMG_CUDA(cudaGetLastError());
 }
 void bat_pcg_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, double* Rold,
-                       int flexible, double* partial, void* sc, double tol2, int force, cudaStream_t s) {
+                       int flexible, double* partial, void* sc, cudaStream_t s) {
   { bat_update_xr<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, P, Q, X, R, Rold, flexible, (const BatchScalars*)sc, partial); note_launch(); }
-  { bat_finish_rr<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m, tol2, force); note_launch(); }
+  { bat_finish_rr<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_graph_start_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle first,
+                            cudaGraphConditionalHandle loop, cudaStream_t s) {
+  { bat_graph_start<<<1, 1, 0, s>>>((const BatchScalars*)sc, m, st, first, loop); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+void bat_graph_check_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle loop,
+                            cudaGraphConditionalHandle more, cudaStream_t s) {
+  { bat_graph_check<<<1, 1, 0, s>>>((const BatchScalars*)sc, m, st, loop, more); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
 

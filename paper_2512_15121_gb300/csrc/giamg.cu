@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -24,8 +25,12 @@ void set_error(int code, const std::string& msg) {
 Hierarchy::~Hierarchy() {
   for (SolveGraph& G : graph)
     if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto& per_m : bgraph)
+    for (SolveGraph& G : per_m)
+      if (G.exec) cudaGraphExecDestroy(G.exec);
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (h_gst) cudaFreeHost(h_gst);
+  if (h_bgst) cudaFreeHost(h_bgst);
   for (Level* L : lev) delete L;
   lev.clear();
   if (h_sc) cudaFreeHost(h_sc);
@@ -740,6 +745,12 @@ int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, doubl
 void alloc_batch(Hierarchy& H, int m) {
   if (H.bm >= m) return;
   cudaStream_t s = H.stream;
+  for (auto& per_m : H.bgraph)  // captured graphs hold the old buffers
+    for (SolveGraph& G : per_m)
+      if (G.exec) {
+        GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
+        G = SolveGraph{};
+      }
   for (Level* Lp : H.lev) {
     Level& L = *Lp;
     const size_t nm = (size_t)std::max<int64_t>(L.A.n, 1) * m;
@@ -834,6 +845,90 @@ const double* apply_bvcycle(Ctx& C, int precision, int m, const double* r) {
   return H.bZ.get();
 }
 
+// The halves of a multi-right-hand-side iteration, shared by the host loop and the graph.
+void bat_precondition(Ctx& C, int precision, int m, int first) {
+  Hierarchy& H = *C.H;
+  const double* Z = apply_bvcycle(C, precision, m, H.bR.get());
+  bat_pcg_rz(H.n, m, H.bR.get(), Z, H.bRold.get(), precision ? 1 : 0, first, H.bpartial.get(), H.bsc.get(), H.stream);
+  bat_pcg_update_p(H.n, m, Z, H.bP.get(), H.bsc.get(), first, H.stream);
+}
+void bat_step(Ctx& C, int precision, int m, double* X) {
+  Hierarchy& H = *C.H;
+  Level& L0 = *H.lev[0];
+  cudaStream_t s = H.stream;
+  bat_rows_launch64(L0.A, m, 0, L0.A.v.get(), H.bP.get(), nullptr, H.bQ.get(), nullptr, nullptr, 0.0, 0.0, s);
+  bat_pcg_pq(H.n, m, H.bP.get(), H.bQ.get(), H.bpartial.get(), H.bsc.get(), s);
+  bat_pcg_update_xr(H.n, m, H.bP.get(), H.bQ.get(), X, H.bR.get(), H.bRold.get(), precision ? 1 : 0, H.bpartial.get(),
+                    H.bsc.get(), s);
+}
+
+// Capture the multi-right-hand-side solve for (precision, m) as one CUDA graph, shaped like the
+// single-vector one: init; start; IF go: precondition (first); WHILE cont: step; check;
+// IF cont: precondition.  It reads B from H.bB and writes X to H.bX.
+void capture_batch(Ctx& C, int precision, int m) {
+  Hierarchy& H = *C.H;
+  SolveGraph& G = H.bgraph[precision][m];
+  if (!H.capture_stream) GIAMG_CUDA(cudaStreamCreateWithFlags(&H.capture_stream, cudaStreamNonBlocking));
+  if (!H.bgst.get()) {
+    H.bgst.alloc(1, H.stream);
+    GIAMG_CUDA(cudaMallocHost((void**)&H.h_bgst, sizeof(BatchGraphState)));
+  }
+  GIAMG_CUDA(cudaStreamSynchronize(H.stream));
+  cudaStream_t user = H.stream;
+  cudaStream_t cs = H.capture_stream;
+  cudaGraph_t g = nullptr;
+  struct Restore {
+    Hierarchy& H;
+    cudaStream_t user;
+    cudaGraph_t& g;
+    ~Restore() {
+      H.stream = user;
+      cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(H.capture_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t partial = nullptr;
+        cudaStreamEndCapture(H.capture_stream, &partial);
+        if (partial && partial != g) cudaGraphDestroy(partial);
+      }
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+    }
+  } restore{H, user, g};
+  H.stream = cs;
+  GIAMG_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h_first, h_loop, h_more;
+  GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_first, g, 0, cudaGraphCondAssignDefault));
+  GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_loop, g, 0, cudaGraphCondAssignDefault));
+  const long long c0 = g_launches.load();
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  bat_pcg_init(H.n, m, H.bB.get(), H.bX.get(), H.bR.get(), H.bpartial.get(), H.bsc.get(), cs);
+  bat_graph_start_launch(H.bsc.get(), m, H.bgst.get(), h_first, h_loop, cs);
+  cudaGraph_t body_first = add_conditional(cs, h_first, cudaGraphCondTypeIf);
+  cudaGraph_t body_loop = add_conditional(cs, h_loop, cudaGraphCondTypeWhile);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &g));
+  const long long c1 = g_launches.load();
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_first, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  bat_precondition(C, precision, m, 1);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &body_first));
+  const long long c2 = g_launches.load();
+  GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_more, body_loop, 0, cudaGraphCondAssignDefault));
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_loop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  bat_step(C, precision, m, H.bX.get());
+  bat_graph_check_launch(H.bsc.get(), m, H.bgst.get(), h_loop, h_more, cs);
+  cudaGraph_t body_more = add_conditional(cs, h_more, cudaGraphCondTypeIf);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &body_loop));
+  const long long c3 = g_launches.load();
+  GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_more, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  bat_precondition(C, precision, m, 0);
+  GIAMG_CUDA(cudaStreamEndCapture(cs, &body_more));
+  const long long c4 = g_launches.load();
+  GIAMG_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
+  G.n_init = c1 - c0;
+  G.n_first = c2 - c1;
+  G.n_loop = c3 - c2;
+  G.n_more = c4 - c3;
+  g_launches.fetch_sub(c4 - c0);
+}
+
 int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double* B_in, double* X_out, double rtol,
                      int* iters, double* relres) {
   Hierarchy& H = *C.H;
@@ -845,55 +940,70 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
   GIAMG_CHECK(rtol >= 0.0, GIAMG_ERR_ARG, "rtol must be non-negative");
   alloc_batch(H, m);
   const bool dev = H.opt.device_ptrs != 0;
-  const double* Bd = B_in;
-  double* Xd = X_out;
-  if (!dev) {
-    GIAMG_CUDA(cudaMemcpyAsync(H.bB.get(), B_in, sizeof(double) * n * m, cudaMemcpyHostToDevice, s));
-    Bd = H.bB.get();
-    Xd = H.bX.get();
-  }
-  Level& L0 = *H.lev[0];
-  const int flexible = precision ? 1 : 0;
   BatchScalarsHost* hs = (BatchScalarsHost*)H.h_bsc;
   void* sc = H.bsc.get();
-  double* partial = H.bpartial.get();
-  const double tol2 = rtol * rtol;
   const int force = force_iters > 0 ? 1 : 0;
-  bat_pcg_init(n, m, Bd, Xd, H.bR.get(), partial, sc, s);
-  GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaStreamSynchronize(s));
-  std::vector<double> bb(m);
-  std::vector<int> its(m, 0);
-  for (int j = 0; j < m; ++j) bb[j] = hs->bb[j];
-  int active = 0;
-  for (int j = 0; j < m; ++j) active += hs->active[j];
   const int limit = force ? force_iters : H.opt.max_iter;
+  // the stopping rule's parameters live on the device (both paths read them there)
+  hs->tol2 = rtol * rtol;
+  hs->force = force;
+  GIAMG_CUDA(cudaMemcpyAsync((char*)sc + offsetof(BatchScalarsHost, tol2), &hs->tol2, sizeof(double) + 2 * sizeof(int),
+                             cudaMemcpyHostToDevice, s));
+  std::vector<int> its(m, 0);
   int it = 0;
   bool breakdown = false;
-  while (active > 0 && it < limit) {
-    const double* Z = apply_bvcycle(C, precision, m, H.bR.get());
-    bat_pcg_rz(n, m, H.bR.get(), Z, H.bRold.get(), flexible, it == 0 ? 1 : 0, partial, sc, s);
-    bat_pcg_update_p(n, m, Z, H.bP.get(), sc, it == 0 ? 1 : 0, s);
-    bat_rows_launch64(L0.A, m, 0, L0.A.v.get(), H.bP.get(), nullptr, H.bQ.get(), nullptr, nullptr, 0.0, 0.0, s);
-    bat_pcg_pq(n, m, H.bP.get(), H.bQ.get(), partial, sc, s);
-    bat_pcg_update_xr(n, m, H.bP.get(), H.bQ.get(), Xd, H.bR.get(), H.bRold.get(), flexible, partial, sc, tol2, force, s);
-    const std::vector<int> was(hs->active, hs->active + m);
+  if (H.opt.graphs && !H.prof.on) {
+    if (!H.bgraph[precision][m].exec) capture_batch(C, precision, m);
+    const SolveGraph& G = H.bgraph[precision][m];
+    GIAMG_CUDA(cudaMemcpyAsync(H.bB.get(), B_in, sizeof(double) * n * m, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    BatchGraphState& gs = *H.h_bgst;
+    gs.limit = limit;
+    GIAMG_CUDA(cudaMemcpyAsync(&H.bgst.get()->limit, &gs.limit, sizeof(int), cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaGraphLaunch(G.exec, s));
+    GIAMG_CUDA(cudaMemcpyAsync(&gs, H.bgst.get(), sizeof(BatchGraphState), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(X_out, H.bX.get(), sizeof(double) * n * m, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    it = gs.it;
+    breakdown = gs.breakdown != 0;
+    for (int j = 0; j < m; ++j) its[j] = gs.its[j];
+    const bool ran = it > 0;
+    g_launches.fetch_add(G.n_init + (ran ? G.n_first + it * G.n_loop + (it - 1) * G.n_more : 0));
+  } else {
+    const double* Bd = B_in;
+    double* Xd = X_out;
+    if (!dev) {
+      GIAMG_CUDA(cudaMemcpyAsync(H.bB.get(), B_in, sizeof(double) * n * m, cudaMemcpyHostToDevice, s));
+      Bd = H.bB.get();
+      Xd = H.bX.get();
+    }
+    bat_pcg_init(n, m, Bd, Xd, H.bR.get(), H.bpartial.get(), sc, s);
     GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
     GIAMG_CUDA(cudaStreamSynchronize(s));
-    ++it;
-    active = 0;
-    for (int j = 0; j < m; ++j) {
-      if (was[j]) its[j] = it;
-      if (hs->status[j] != 0) breakdown = true;
-      active += hs->active[j];
+    int active = 0;
+    for (int j = 0; j < m; ++j) active += hs->active[j];
+    if (active > 0 && limit > 0) bat_precondition(C, precision, m, 1);
+    while (active > 0 && it < limit) {
+      bat_step(C, precision, m, Xd);
+      const std::vector<int> was(hs->active, hs->active + m);
+      GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
+      GIAMG_CUDA(cudaStreamSynchronize(s));
+      ++it;
+      active = 0;
+      for (int j = 0; j < m; ++j) {
+        if (was[j]) its[j] = it;
+        if (hs->status[j] != 0) breakdown = true;
+        active += hs->active[j];
+      }
+      if (breakdown || active == 0 || it == limit) break;
+      bat_precondition(C, precision, m, 0);
     }
-    if (breakdown) break;
+    if (!dev) GIAMG_CUDA(cudaMemcpyAsync(X_out, Xd, sizeof(double) * n * m, cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
   }
-  if (!dev) GIAMG_CUDA(cudaMemcpyAsync(X_out, Xd, sizeof(double) * n * m, cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaStreamSynchronize(s));
   bool unconverged = false;
   for (int j = 0; j < m; ++j) {
-    const double rr = bb[j] > 0.0 ? std::sqrt(hs->rr[j] / bb[j]) : 0.0;
+    const double rr = hs->bb[j] > 0.0 ? std::sqrt(hs->rr[j] / hs->bb[j]) : 0.0;
     if (iters) iters[j] = its[j];
     if (relres) relres[j] = rr;
     if (!force && !(rr <= rtol)) unconverged = true;

@@ -176,6 +176,12 @@ struct GraphState {
   int status;
 };
 
+// Device-side state of the multi-right-hand-side solve captured as a CUDA graph.
+struct BatchGraphState {
+  int it, limit, breakdown, pad;
+  int its[32], was[32];
+};
+
 // One instantiated solve graph (per V-cycle precision) and the kernel launches of its parts, so
 // the launch counter can be advanced by what a run executed.
 struct SolveGraph {
@@ -231,6 +237,9 @@ struct Hierarchy {
   DBuf<double> gb, gx, ghist;
   DBuf<GraphState> gst;
   GraphState* h_gst = nullptr;  // pinned host copy
+  SolveGraph bgraph[2][33];       // multi-right-hand-side solve graphs by precision and m
+  DBuf<BatchGraphState> bgst;
+  BatchGraphState* h_bgst = nullptr;
   ~Hierarchy();
 };
 
@@ -331,11 +340,18 @@ void bat_pcg_rz(int64_t n, int m, const double* R, const double* Z, const double
 void bat_pcg_update_p(int64_t n, int m, const double* Z, double* P, const void* sc, int first, cudaStream_t s);
 void bat_pcg_pq(int64_t n, int m, const double* P, const double* Q, double* partial, void* sc, cudaStream_t s);
 void bat_pcg_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, double* Rold,
-                       int flexible, double* partial, void* sc, double tol2, int force, cudaStream_t s);
+                       int flexible, double* partial, void* sc, cudaStream_t s);
+void bat_graph_start_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle first,
+                            cudaGraphConditionalHandle loop, cudaStream_t s);
+void bat_graph_check_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle loop,
+                            cudaGraphConditionalHandle more, cudaStream_t s);
 // host view of the batched CG scalars (layout shared with batch_kernels.cu)
 struct BatchScalarsHost {
   double rho[32], pq[32], alpha[32], beta[32], rr[32], bb[32];
   int status[32], active[32];
+  double tol2;
+  int force;
+  int pad;
 };
 
 // ------------------------------------------------------------------ setup kernels

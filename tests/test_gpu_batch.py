@@ -114,3 +114,22 @@ def test_batch_argument_errors():
     for m in (0, 33):
         rc = g.lib().giamg_solve_batch_ex(gpu._h, 0, 0, m, g._ptr(Bd), g._ptr(Bd), 1e-8, g._ptr(it), g._ptr(rr))
         assert rc == g.GIAMG_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_graph_equals_host_loop(precision):
+    """The batch solve captured as one CUDA graph and the host-driven loop: same per-column
+    iterations, relres and solution bits; graphs are captured per column count and recaptured
+    after the work buffers grow."""
+    prob, B, orc, gpu = case("jitter8_p2_hlevels", 32)
+    host_loop = g.Solver.from_problem(prob, device=True, cheb_degree=2, graphs=0)
+    try:
+        for m in (5, 32, 5, 1):
+            Bd = torch.from_numpy(np.ascontiguousarray(B[:, :m])).cuda()
+            for force in (None, 4):
+                Xg, itg, rrg = gpu.solve_batch(Bd, rtol=1e-8, precision=precision, force_iters=force)
+                Xh, ith, rrh = host_loop.solve_batch(Bd, rtol=1e-8, precision=precision, force_iters=force)
+                assert np.array_equal(itg, ith) and np.array_equal(rrg, rrh), m
+                assert torch.equal(Xg, Xh), m
+    finally:
+        host_loop.close()
