@@ -133,3 +133,19 @@ def test_batch_graph_equals_host_loop(precision):
                 assert torch.equal(Xg, Xh), m
     finally:
         host_loop.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_column_bits_independent_of_width(precision):
+    """A column's arithmetic does not depend on how many columns share the batch (the group width
+    of the batched row kernels changes with m): the same right-hand side gives the same bits in
+    batches of 1, 3, 9 and 20 columns."""
+    prob, B, orc, gpu = case("jitter5_p4", 32)
+    ref = None
+    for m in (1, 3, 9, 20):
+        X, it, rr = gpu.solve_batch(torch.from_numpy(np.ascontiguousarray(B[:, :m])).cuda(), rtol=1e-8,
+                                    precision=precision)
+        if ref is None:
+            ref = (X[:, 0].clone(), int(it[0]))
+        else:
+            assert int(it[0]) == ref[1] and torch.equal(X[:, 0], ref[0]), m
