@@ -86,17 +86,21 @@ typedef struct {
                              the fastest; 0 (default): the variants measured best inside the solve
                              (FP32 rows: pattern form; FP64 rows: CSR with 16 threads per row) */
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
-                             groups (falls back to CSR where the form is not available) */
+                             groups, 4 hybrid (groups of at least 16 rows by the group kernel, the
+                             other rows by the row-pattern kernel); each falls back to CSR where
+                             the form is not available */
   int row_threads;        /* force threads per row (4, 8, 16, 32); 0 automatic */
   int prefetch_rows;      /* row-pattern kernels: every block prefetches into L2 the values of the
                              block this many rows ahead; 0 off, -1 (default) automatic */
   int row_chains;         /* row-pattern kernels: independent load chains per thread (2, 4, 8);
                              0 (default) automatic */
-  int graphs;             /* 1 (default): giamg_solve runs the whole PCG loop as one CUDA graph
-                             (captured on the first solve of each precision) whose convergence
-                             test runs on the device; 0: a host loop with one synchronisation
-                             per iteration.  Both give the same iterations and bits.  The host
-                             loop is used while profiling or when force_iters > max_iter. */
+  int graphs;             /* 1 (default): a solve runs the whole PCG loop as one CUDA graph whose
+                             convergence test runs on the device, captured at the second solve
+                             of a shape (precision; number of right-hand sides) so one-off shapes
+                             pay no capture; 2: captured at the first solve; 0: a host loop with
+                             one synchronisation per iteration.  All give the same iterations
+                             and bits.  The host loop is used while profiling or when
+                             force_iters > max_iter. */
 } giamg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -163,7 +167,8 @@ GIAMG_API int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_
  * level uses plain CSR). */
 GIAMG_API int giamg_level_templates(giamg_handle h, int level, int64_t* n_templates, int64_t* n_offsets);
 /* Row-kernel variant used on A_l for precision 0 (FP64) or 1 (FP32): threads per row and the
- * form (*pattern: 0 CSR, 1 row patterns, 2 row groups with identical column sets), chosen by the
+ * form (*pattern: 0 CSR, 1 row patterns, 2 row groups with identical column sets, 3 hybrid of
+ * big row groups and row patterns), chosen by the
  * setup-time tuner when autotune is set. */
 GIAMG_API int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern);
 /* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */

@@ -321,7 +321,7 @@ class Solver:
     def kernel(self, l, precision):
         t, p = ctypes.c_int(), ctypes.c_int()
         _check(lib().giamg_level_kernel(self._h, l, precision, ctypes.byref(t), ctypes.byref(p)))
-        return t.value, ["csr", "pattern", "groups"][p.value]
+        return t.value, ["csr", "pattern", "groups", "hybrid"][p.value]
 
     def rho_hat(self, l):
         r = ctypes.c_double()

@@ -332,11 +332,12 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   GIAMG_CHECK(opt.max_levels >= 1 && opt.max_levels <= 64, GIAMG_ERR_ARG, "max_levels must be in [1, 64]");
   GIAMG_CHECK(opt.lanczos_steps >= 1, GIAMG_ERR_ARG, "lanczos_steps must be >= 1");
   GIAMG_CHECK(opt.precision == 0 || opt.precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
-  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 3, GIAMG_ERR_ARG, "row_form must be in 0..3");
+  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 4, GIAMG_ERR_ARG, "row_form must be in 0..4");
   GIAMG_CHECK(opt.row_threads == 0 || opt.row_threads == 4 || opt.row_threads == 8 || opt.row_threads == 16 ||
                   opt.row_threads == 32,
               GIAMG_ERR_ARG, "row_threads must be 0, 4, 8, 16 or 32");
   GIAMG_CHECK(opt.prefetch_rows >= -1, GIAMG_ERR_ARG, "prefetch_rows must be -1, 0 or positive");
+  GIAMG_CHECK(opt.graphs >= 0 && opt.graphs <= 2, GIAMG_ERR_ARG, "graphs must be 0, 1 or 2");
   GIAMG_CHECK(opt.row_chains == 0 || opt.row_chains == 2 || opt.row_chains == 4 || opt.row_chains == 8, GIAMG_ERR_ARG,
               "row_chains must be 0, 2, 4 or 8");
   const bool dev = opt.device_ptrs != 0;
@@ -669,9 +670,10 @@ int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, doubl
   int status = GIAMG_OK;
   // the graph path: profiling off (its events are host-recorded) and the limit within the
   // capacity of the captured history
-  const bool graph = H.opt.graphs && !H.prof.on && limit <= H.opt.max_iter;
+  SolveGraph& SG = H.graph[precision];
+  const bool graph = H.opt.graphs && !H.prof.on && limit <= H.opt.max_iter && (SG.exec || ++SG.uses >= (H.opt.graphs == 2 ? 1 : 2));
   if (graph) {
-    if (!H.graph[precision].exec) capture_solve(C, precision);
+    if (!SG.exec) capture_solve(C, precision);
     const SolveGraph& G = H.graph[precision];
     GIAMG_CUDA(cudaMemcpyAsync(H.gb.get(), b_in, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     GraphState& hs = *H.h_gst;
@@ -952,8 +954,9 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
   std::vector<int> its(m, 0);
   int it = 0;
   bool breakdown = false;
-  if (H.opt.graphs && !H.prof.on) {
-    if (!H.bgraph[precision][m].exec) capture_batch(C, precision, m);
+  SolveGraph& BG = H.bgraph[precision][m];
+  if (H.opt.graphs && !H.prof.on && (BG.exec || ++BG.uses >= (H.opt.graphs == 2 ? 1 : 2))) {
+    if (!BG.exec) capture_batch(C, precision, m);
     const SolveGraph& G = H.bgraph[precision][m];
     GIAMG_CUDA(cudaMemcpyAsync(H.bB.get(), B_in, sizeof(double) * n * m, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     BatchGraphState& gs = *H.h_bgst;
@@ -1207,7 +1210,7 @@ int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_pe
     const RowVariant& v = precision == 0 ? L.A.var64 : L.A.var32;
     const double avg = L.A.n ? (double)L.A.nnz / L.A.n : 0.0;
     if (threads_per_row) *threads_per_row = v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
-    if (pattern) *pattern = v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
+    if (pattern) *pattern = v.hybrid ? 3 : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
     return GIAMG_OK;
   });
 }

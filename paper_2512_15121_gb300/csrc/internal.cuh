@@ -93,7 +93,14 @@ struct Groups {
   int cmax = 0;
   DBuf<int64_t> gptr, rptr;
   DBuf<int32_t> gcol, grow;
+  // hybrid form: the groups of at least kHybridRows rows (big) and every other row (rest,
+  // ascending); needs the row-pattern form for the rest
+  bool hyb = false;
+  int64_t n_big = 0, n_rest = 0;
+  double big_cols = 0.0;  // average column count of the rows in big groups
+  DBuf<int32_t> big, rest;
 };
+constexpr int kHybridRows = 16;
 
 // Row-kernel variant chosen for a matrix: threads per row and whether the pattern form is used
 // (one choice per value precision; set by the setup-time tuner, or from the row length).
@@ -102,6 +109,7 @@ struct RowVariant {
   bool pat = false;
   int unroll = 2;    // independent load chains per thread and step (pattern form: 2, 4 or 8)
   bool group = false;  // row-group form (one CTA per group, x gathered once into shared memory)
+  bool hybrid = false;  // big row groups by the group kernel, the other rows by the pattern kernel
   int64_t prefetch = 0;  // pattern form: L2 prefetch distance in rows (0: none)
 };
 
@@ -186,6 +194,7 @@ struct BatchGraphState {
 // the launch counter can be advanced by what a run executed.
 struct SolveGraph {
   cudaGraphExec_t exec = nullptr;
+  int uses = 0;  // solves of this shape so far (graphs = 1 captures from the second one)
   long long n_init = 0, n_first = 0, n_loop = 0, n_more = 0;
 };
 

@@ -400,6 +400,39 @@ bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
   R.n_cols = total;
   R.cmax = (int)cmax;
   R.on = true;
+  // hybrid form: big groups (at least kHybridRows rows) and the rows of all other groups
+  if (A.pat.on) {
+    std::vector<int64_t> rp_h(G + 1);
+    std::vector<int32_t> rows(n);
+    GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(rows.data(), R.grow.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> big, rest;
+    double big_nnz = 0.0, big_rows = 0.0;
+    for (int64_t g = 0; g < G; ++g) {
+      const int64_t r = rp_h[g + 1] - rp_h[g];
+      if (r >= kHybridRows) {
+        big.push_back((int32_t)g);
+        big_rows += (double)r;
+        big_nnz += (double)r * (double)(gp[g + 1] - gp[g]);
+      } else {
+        rest.insert(rest.end(), rows.begin() + rp_h[g], rows.begin() + rp_h[g + 1]);
+      }
+    }
+    std::sort(rest.begin(), rest.end());
+    if (!big.empty()) {
+      R.big.alloc(big.size(), s);
+      GIAMG_CUDA(cudaMemcpyAsync(R.big.get(), big.data(), sizeof(int32_t) * big.size(), cudaMemcpyHostToDevice, s));
+      R.rest.alloc(std::max<size_t>(rest.size(), 1), s);
+      if (!rest.empty())
+        GIAMG_CUDA(cudaMemcpyAsync(R.rest.get(), rest.data(), sizeof(int32_t) * rest.size(), cudaMemcpyHostToDevice, s));
+      GIAMG_CUDA(cudaStreamSynchronize(s));
+      R.n_big = (int64_t)big.size();
+      R.n_rest = (int64_t)rest.size();
+      R.big_cols = big_rows > 0 ? big_nnz / big_rows : 0.0;
+      R.hyb = true;
+    }
+  }
   return true;
 }
 

@@ -84,16 +84,20 @@ __device__ __forceinline__ void prefetch_l2(const void* base, int64_t lo, int64_
 // Blocks start roughly in row order, so with pf > 0 the first thread of every block prefetches
 // into L2 (one bulk request) the values of the block pf rows ahead: by the time that block runs,
 // its value loads wait on L2 instead of HBM.
-template <int TPR, int U, typename V, int MODE>
+template <int TPR, int U, typename V, int MODE, bool LIST = false>
 __device__ __forceinline__ void pat_body(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ obase,
                                          const int32_t* __restrict__ toff,
                                          const V* __restrict__ val, const V* __restrict__ x, const V* __restrict__ b,
                                          V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2,
-                                         int64_t pf, int64_t vend) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t row = gt / TPR;
+                                         int64_t pf, int64_t vend, const int32_t* __restrict__ list = nullptr,
+                                         int64_t block0 = 0) {
+  // LIST: the group of threads t takes row list[t] of the n listed rows; block0: blocks before
+  // this one that do other work in the same launch
+  const int64_t gt = ((int64_t)blockIdx.x - block0) * blockDim.x + threadIdx.x;
+  const int64_t idx = gt / TPR;
   const int lane = threadIdx.x % TPR;
-  const bool valid = row < n;
+  const bool valid = idx < n;
+  const int64_t row = LIST ? (valid ? (int64_t)list[idx] : 0) : idx;
   if (pf > 0 && threadIdx.x == 0) {
     const int64_t rows = blockDim.x / TPR;
     const int64_t r0 = (int64_t)blockIdx.x * rows + pf;
@@ -186,6 +190,101 @@ PAT_SELECT(double, kCheb, pat_cheb_f64)
 PAT_SELECT(float, kCheb, pat_cheb_f32)
 PAT_SELECT(double, kAddSpmv, pat_add_f64)
 PAT_SELECT(float, kAddSpmv, pat_add_f32)
+
+// The hybrid form in one launch.  Blocks 0 .. n_big-1 take the big row groups: one CTA per group
+// gathers the group's x values into shared memory once; every warp then takes rows of the group,
+// and each lane issues the loads of 8 of the row's values (stride 32) before their products, so
+// a warp keeps 8 x 128 bytes of the value stream in flight with no dependent load in between.
+// The later blocks run the row-pattern kernel over the list of the other rows; they start after
+// the group blocks and fill the tail of the launch.
+template <typename V, int MODE>
+__device__ __forceinline__ void hyb_body(const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,
+                                         const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr,
+                                         const int32_t* __restrict__ grow, const int64_t* __restrict__ rp,
+                                         const V* __restrict__ val, const V* __restrict__ x, const V* __restrict__ b,
+                                         V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xs = reinterpret_cast<V*>(smem_raw);
+  const int64_t g = big[blockIdx.x];
+  const int64_t c0 = gptr[g];
+  const int c = (int)(gptr[g + 1] - c0);
+  for (int k = threadIdx.x; k < c; k += blockDim.x) xs[k] = x[__ldg(gcol + c0 + k)];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t t_end = rptr[g + 1];
+  for (int64_t t = rptr[g] + warp; t < t_end; t += nw) {
+    const int64_t row = grow[t];
+    const V* __restrict__ vr = val + rp[row];
+    V a[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < c; k0 += 256) {
+      V v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int kk = k0 + lane + 32 * u;
+        v[u] = kk < c ? __ldcs(vr + kk) : V(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int kk = k0 + lane + 32 * u;
+        a[u & 3] = fma(v[u], xs[kk < c ? kk : 0], a[u & 3]);
+      }
+    }
+    V acc = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane != 0) continue;
+    if (MODE == kSpmv) {
+      y[row] = acc;
+    } else if (MODE == kAddSpmv) {
+      y[row] += acc;
+    } else if (MODE == kResidual) {
+      y[row] = b[row] - acc;
+    } else {
+      const V r = b[row] - acc;
+      const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * r;
+      d[row] = dn;
+      y[row] = x[row] + dn;
+    }
+  }
+}
+
+#define HYB_KERNEL(NAME, V, MODE)                                                                              \
+  __global__ void __launch_bounds__(kThreads)                                                                 \
+      NAME(int64_t n_big, const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,                  \
+           const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow, \
+           int64_t n_rest, const int32_t* __restrict__ rest, const int32_t* __restrict__ obase,               \
+           const int32_t* __restrict__ toff, const int64_t* __restrict__ rp, const V* __restrict__ val,       \
+           const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,            \
+           const V* __restrict__ dinv, V c1, V c2) {                                                          \
+    if ((int64_t)blockIdx.x < n_big)                                                                          \
+      hyb_body<V, MODE>(big, gptr, gcol, rptr, grow, rp, val, x, b, y, d, dinv, c1, c2);                     \
+    else                                                                                                      \
+      pat_body<32, 2, V, MODE, true>(n_rest, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, 0, 0, rest, n_big); \
+  }
+HYB_KERNEL(hyb_spmv_f64, double, kSpmv)
+HYB_KERNEL(hyb_spmv_f32, float, kSpmv)
+HYB_KERNEL(hyb_resid_f64, double, kResidual)
+HYB_KERNEL(hyb_resid_f32, float, kResidual)
+HYB_KERNEL(hyb_cheb_f64, double, kCheb)
+HYB_KERNEL(hyb_cheb_f32, float, kCheb)
+HYB_KERNEL(hyb_add_f64, double, kAddSpmv)
+HYB_KERNEL(hyb_add_f32, float, kAddSpmv)
+
+template <typename V, int MODE>
+struct HybKernel;
+#define HYB_SELECT(V, MODE, H)                           \
+  template <>                                           \
+  struct HybKernel<V, MODE> {                           \
+    static constexpr decltype(&H) get() { return &H; }  \
+  };
+HYB_SELECT(double, kSpmv, hyb_spmv_f64)
+HYB_SELECT(float, kSpmv, hyb_spmv_f32)
+HYB_SELECT(double, kResidual, hyb_resid_f64)
+HYB_SELECT(float, kResidual, hyb_resid_f32)
+HYB_SELECT(double, kCheb, hyb_cheb_f64)
+HYB_SELECT(float, kCheb, hyb_cheb_f32)
+HYB_SELECT(double, kAddSpmv, hyb_add_f64)
+HYB_SELECT(float, kAddSpmv, hyb_add_f32)
 
 // Row-group kernels: one CTA per group of rows with identical column sets; the group's x values
 // are gathered once into shared memory, then every warp streams one row's values from HBM
@@ -283,6 +382,23 @@ void launch_grp(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   note_launch();
 }
 
+template <typename V, int MODE>
+void launch_hyb(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  auto k = HybKernel<V, MODE>::get();
+  const size_t sm = sizeof(V) * (size_t)A.grp.cmax;
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
+  const int64_t rest_blocks = (A.grp.n_rest * 32 + kThreads - 1) / kThreads;
+  k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
+      A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
+      A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(), A.rp.get(), val, x, b, y, d, dinv, c1, c2);
+  note_launch();
+}
+
 template <int TPR, int U, typename V, int MODE>
 void launch_pat(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
                 int64_t pf, cudaStream_t s) {
@@ -315,7 +431,9 @@ void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* v
                     const V* dinv, V c1, V c2, cudaStream_t s) {
   const int tpr = var.tpr ? var.tpr : default_tpr(avg);
   const bool pat = var.tpr ? var.pat : A.pat.on;
-  if (var.group && A.grp.on) {
+  if (var.hybrid && A.grp.hyb && A.pat.on) {
+    launch_hyb<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
+  } else if (var.group && A.grp.on) {
     launch_grp<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
   } else if (pat && var.unroll == 8) {
     switch (tpr) {
@@ -776,16 +894,22 @@ void choose_rows(DCSR& A, int form, int threads) {
   for (int prec = 0; prec < 2; ++prec) {
     RowVariant v;
     if (form == 0) {
-      // defaults: FP32 rows on the pattern form (halved index traffic); FP64 rows, which are
-      // bound by the 1/64-rate FP64 pipe, on CSR with 16 threads per long row
+      // defaults: FP32 rows on the hybrid form (big row groups with x in shared memory, the
+      // other rows on the pattern form) where there are enough big groups to fill the GPU for
+      // many waves and their rows are long (measured faster from 12^3 elements at p = 6 and on
+      // the 12^3, p = 8 operator; slower at 8^3 and at p = 4), else the pattern form (halved
+      // index traffic); FP64 rows, which are bound by the 1/64-rate FP64 pipe, on CSR with 16
+      // threads per long row
       v.pat = prec == 1 && A.pat.on;
-      v.tpr = prec == 1 ? default_tpr(avg) : (avg >= 48 ? 16 : default_tpr(avg));
+      v.hybrid = prec == 1 && A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
+      v.tpr = prec == 1 ? (v.hybrid ? 32 : default_tpr(avg)) : (avg >= 48 ? 16 : default_tpr(avg));
     } else {
-      v.pat = form == 2 && A.pat.on;
+      v.pat = (form == 2 || form == 4) && A.pat.on;
       v.group = form == 3 && A.grp.on;
-      v.tpr = v.group ? 32 : default_tpr(avg);
+      v.hybrid = form == 4 && A.grp.hyb && A.pat.on;
+      v.tpr = v.group || v.hybrid ? 32 : default_tpr(avg);
     }
-    if (threads && !v.group) v.tpr = threads;
+    if (threads && !v.group && !v.hybrid) v.tpr = threads;
     (prec == 0 ? A.var64 : A.var32) = v;
   }
 }

@@ -73,8 +73,10 @@ class _Entry:
 class Server:
     def __init__(self, slots: int = 4, reserve_bytes: int = 2 << 30, max_columns: int = 32,
                  mem_info: Callable | None = None, clock: Callable | None = None,
-                 solver_factory: Callable | None = None, runner: Callable | None = None, device: int = 0):
+                 solver_factory: Callable | None = None, runner: Callable | None = None, device: int = 0,
+                 solver_options: dict | None = None):
         self.slots = slots
+        self.solver_options = dict(solver_options or {})
         self.reserve = reserve_bytes
         self.max_columns = max_columns
         self.clock = clock or time.perf_counter
@@ -106,8 +108,10 @@ class Server:
         dev = torch.device("cuda", self.device)
         with torch.cuda.stream(stream):
             t = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
+            opts = dict(self.solver_options)
+            opts.setdefault("cheb_degree", op.get("cheb_degree", 3))
             S = Solver(op["n"], t(op["row_ptr"]), t(op["col"]), t(op["val"]), t(op["elem_dof"]), op["p"],
-                       stream=stream.cuda_stream, device_ptrs=1, cheb_degree=op.get("cheb_degree", 3))
+                       stream=stream.cuda_stream, device_ptrs=1, **opts)
         return S, stream
 
     def _free_bytes(self) -> int:
@@ -149,12 +153,14 @@ class Server:
     def _build(self, key, e: _Entry, op) -> str | None:
         """Outside the lock: run the solver factory for a claimed placeholder; the error text, or
         None.  A failed build leaves no cache entry."""
+        t0 = time.perf_counter()
         try:
             e.solver, e.stream = self.solver_factory(op)
             err = None
         except Exception as ex:
             err = f"setup failed: {ex}"
         with self.cv:
+            self.stats["setup_ms"] += (time.perf_counter() - t0) * 1e3
             self._building_bytes -= e.nbytes
             if err is None:
                 self.stats["setups"] += 1
@@ -241,14 +247,23 @@ class Server:
         self.cv.notify_all()
 
     def _default_runner(self, e: _Entry, B: np.ndarray, rtol: float, precision: int):
+        """One multi-right-hand-side solve.  The batch is padded with zero columns to the next
+        power of two (a zero column retires before the first iteration, and a column's bits do not
+        depend on the batch width), so each hierarchy sees at most six batch shapes and reuses
+        their captured CUDA graphs."""
         import torch
+        m = B.shape[1]
+        mp = 1 << (m - 1).bit_length()
+        if mp > m:
+            B = np.concatenate([B, np.zeros((B.shape[0], mp - m))], axis=1)
         with torch.cuda.stream(e.stream):
             Bd = torch.from_numpy(np.ascontiguousarray(B)).to(f"cuda:{self.device}")
             X, it, rr = e.solver.solve_batch(Bd, rtol=rtol, precision=precision)
-            return X.cpu().numpy(), it, rr
+            return X[:, :m].cpu().numpy(), it[:m], rr[:m]
 
     def _run(self, e: _Entry, batch: list, bid: int):
         t0 = self.clock()
+        w0 = time.perf_counter()
         B = np.concatenate([r.rhs for r in batch], axis=1)
         prec = batch[0].precision
         rtol = min(r.rtol for r in batch)
@@ -267,8 +282,10 @@ class Server:
                 r.iters = np.asarray(it[c:c + k]).copy()
                 r.relres = np.asarray(rr[c:c + k]).copy()
             c += k
-        self.stats["batches"] += 1
-        self.stats["columns"] += c
+        with self.cv:
+            self.stats["batches"] += 1
+            self.stats["columns"] += c
+            self.stats["solve_ms"] += (time.perf_counter() - w0) * 1e3
 
     def drain(self, timeout: float = 600.0):
         """Wait until every submitted request is done."""

@@ -121,7 +121,8 @@ def test_batch_graph_equals_host_loop(precision):
     """The batch solve captured as one CUDA graph and the host-driven loop: same per-column
     iterations, relres and solution bits; graphs are captured per column count and recaptured
     after the work buffers grow."""
-    prob, B, orc, gpu = case("jitter8_p2_hlevels", 32)
+    prob, B, orc, _ = case("jitter8_p2_hlevels", 32)
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=2, graphs=2)
     host_loop = g.Solver.from_problem(prob, device=True, cheb_degree=2, graphs=0)
     try:
         for m in (5, 32, 5, 1):
@@ -132,6 +133,7 @@ def test_batch_graph_equals_host_loop(precision):
                 assert np.array_equal(itg, ith) and np.array_equal(rrg, rrh), m
                 assert torch.equal(Xg, Xh), m
     finally:
+        gpu.close()
         host_loop.close()
 
 

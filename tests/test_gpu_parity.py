@@ -294,17 +294,18 @@ def test_pattern_compression_matches_plain_csr():
 _forms_oracle = {}
 
 
-@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("form", [1, 2, 3, 4])
 @pytest.mark.parametrize("threads", [0, 4, 16])
 def test_row_kernel_forms_match_oracle(form, threads):
-    # every row-kernel form (CSR, row patterns, row groups) and thread count on the same problem
+    # every row-kernel form (CSR, row patterns, row groups, hybrid) and thread count on the same
+    # problem
     if "p" not in _forms_oracle:
         prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
         _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
     prob, orc = _forms_oracle["p"]
     gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, row_form=form, row_threads=threads)
     try:
-        name = ["csr", "pattern", "groups"][form - 1]
+        name = ["csr", "pattern", "groups", "hybrid"][form - 1]
         for prec in (0, 1):
             assert gpu.kernel(0, prec)[1] == name
         rng = np.random.default_rng(7)
@@ -342,7 +343,7 @@ def fp32_product_bound(rp, ci, v, x):
     return A32 @ x32, (lens + 1) * 2.0 ** -23 * (absA @ np.abs(x32))
 
 
-@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("form", [1, 2, 3, 4])
 def test_fp32_level_product(form):
     """The FP32 product of every level through the level's FP32 row kernel, against the product of
     the FP32-rounded operands: within the accumulation bound, row by row."""
@@ -369,7 +370,8 @@ def test_fp32_level_product(form):
 def test_graph_solve_equals_host_loop(name, precision):
     """The solve captured as one CUDA graph (device-side stopping rule) and the host-driven loop give
     the same iterations, relres history and solution bits, and execute the same kernels."""
-    prob, orc, gpu, k = setup_case(name)
+    prob, orc, _, k = setup_case(name)
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=2)  # graph from the first solve
     host_loop = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=0)
     try:
         b = dev(prob.b)
@@ -386,16 +388,18 @@ def test_graph_solve_equals_host_loop(name, precision):
             # the executed kernels: the host loop's plus the graph's start and per-iteration checks
             assert c1 - c0 == (c2 - c1) + 1 + itg
     finally:
+        gpu.close()
         host_loop.close()
 
 
 def test_graph_solve_edge_cases():
-    prob, orc, gpu, k = setup_case("cube4_p4")
+    prob, orc, _, k = setup_case("cube4_p4")
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=2)
     # b = 0: no iteration, x = 0
     x, it, rr = gpu.solve(dev(np.zeros(prob.n)), rtol=1e-8)
     assert it == 0 and rr == 0.0 and torch.count_nonzero(x) == 0
     # the iteration limit: MAXITER reported, x the iterate after max_iter steps (as the host loop)
-    lim = g.Solver.from_problem(prob, device=True, cheb_degree=k, max_iter=2)
+    lim = g.Solver.from_problem(prob, device=True, cheb_degree=k, max_iter=2, graphs=2)
     ref = g.Solver.from_problem(prob, device=True, cheb_degree=k, max_iter=2, graphs=0)
     try:
         xg, itg, rrg = lim.solve(dev(prob.b), rtol=1e-14)
@@ -417,3 +421,21 @@ def test_graph_solve_edge_cases():
         gpu.set_device_ptrs(True)
     xd, itd, _ = gpu.solve(dev(prob.b), rtol=1e-8)
     assert ith == itd and np.array_equal(xh, xd.cpu().numpy())
+    gpu.close()
+
+
+def test_graph_captured_from_the_second_solve():
+    """graphs = 1 (default): the first solve of a shape runs the host loop, later ones the graph;
+    the launch count shows which ran (the graph adds its start and check kernels)."""
+    prob, orc, _, k = setup_case("cube4_p4")
+    s = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+    try:
+        b = dev(prob.b)
+        counts = []
+        for _ in range(3):
+            c0 = g.launch_count()
+            x, it, _ = s.solve(b, rtol=1e-8)
+            counts.append(g.launch_count() - c0)
+        assert counts[1] == counts[2] == counts[0] + 1 + it
+    finally:
+        s.close()
