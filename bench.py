@@ -38,6 +38,7 @@ WORKLOAD_TEXT = {
     "helmholtz_16cube_jitter_p6": "Helmholtz lambda=10, unit cube, 16^3 hex jittered +-0.2h (seed 1), GLL p=6",
     "helmholtz_4cube_p4": "Helmholtz lambda=1, unit cube, 4^3 hex, GLL p=4",
     "helmholtz_8cube_jitter_p6": "Helmholtz lambda=10, unit cube, 8^3 hex jittered +-0.2h (seed 1), GLL p=6",
+    "helmholtz_12cube_jitter_p6": "Helmholtz lambda=10, unit cube, 12^3 hex jittered +-0.2h (seed 1), GLL p=6",
     "poisson_24cube_jitter_p4": "Poisson lambda=0, unit cube, 24^3 hex jittered (seed 2), GLL p=4",
     "helmholtz_12cube_graded_p8": "Helmholtz lambda=1000, kappa=1+0.5sin(2pi x), 12^3 hex graded to z=0, GLL p=8",
 }

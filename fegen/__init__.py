@@ -185,6 +185,10 @@ WORKLOADS = {
     # the same operator and order on an 8^3 mesh (117,649 dofs, 5.1e7 nonzeros: larger than L2),
     # used for detailed kernel profiles
     "helmholtz_8cube_jitter_p6": dict(n=8, p=6, mesh="jitter", mesh_seed=1, lam=10.0, rhs="manufactured", k=3),
+    # and on a 12^3 mesh (389,017 dofs, 1.7e8 nonzeros, about 3.5 GB on the device with the
+    # hierarchy): the smallest of these on which the hybrid row form is the default, for its
+    # detailed profiles
+    "helmholtz_12cube_jitter_p6": dict(n=12, p=6, mesh="jitter", mesh_seed=1, lam=10.0, rhs="manufactured", k=3),
     # pressure Poisson on a jittered 24^3 mesh, p = 4: 912,673 dofs, 32 Fourier right-hand sides
     "poisson_24cube_jitter_p4": dict(n=24, p=4, mesh="jitter", mesh_seed=2, lam=0.0,
                                      rhs="fourier", k=2),
