@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the multi-RHS and serving measurements")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="run only the 512-request serving stream (36 operators up to 12^3, p = 8) and print it")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print a per-kernel summary of an ncu launch list and exit (no GPU work)")
     ap.add_argument("--split-at", metavar="KERNEL",
@@ -479,6 +481,45 @@ def measure_serving(n_requests=128, rate=150.0):
     return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()}
 
 
+def measure_serving_full(n_requests=512, load=0.8):
+    """The larger serving stream: 512 requests on jittered 4^3 / 8^3 / 12^3 meshes, p in
+    {2, 4, 6, 8}, lambda in {0, 1, 1000} (36 operators, up to 912,673 dofs and 7.97e8 nonzeros),
+    1..8 right-hand sides (the seeded Fourier fields at the nodes).  First the capacity: every
+    request submitted at once to a fresh server; then the same stream with Poisson arrivals at
+    `load` times that capacity, again on a fresh server (setups included in both)."""
+    import dataclasses
+    from paper_2512_15121_gb300 import serve
+    warm, _ = serve.synthetic_stream(16, seed=99, rate_per_s=1e6, meshes=(4,), orders=(2, 4, 8))
+    w = serve.Server(slots=4)
+    serve.run_stream(w, warm)
+    w.close()
+    t0 = time.perf_counter()
+    # arrival offsets for rate 1/s; run_stream scales them by time_scale = 1 / rate
+    reqs, ops = serve.synthetic_stream(n_requests, seed=7, rate_per_s=1.0, meshes=(4, 8, 12), orders=(2, 4, 6, 8),
+                                       lambdas=(0.0, 1.0, 1000.0), rhs_kind="nodal")
+    gen_s = time.perf_counter() - t0
+    offsets = [r.arrival for r in reqs]
+    cols = sum(r.columns for r in reqs)
+
+    def run(time_scale):
+        rs = [dataclasses.replace(r, arrival=off) for r, off in zip(reqs, offsets)]
+        srv = serve.Server(slots=4)
+        st = serve.run_stream(srv, rs, time_scale=time_scale)
+        srv.close()
+        st.update({k: int(v) for k, v in srv.stats.items()})
+        st["errors"] = sum(r.error is not None for r in rs)
+        return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+
+    cap = run(0.0)
+    capacity = cap["solves_per_s"]
+    rate = load * capacity * n_requests / cols  # requests per second
+    loaded = run(1.0 / rate)
+    loaded["rate_per_s"] = round(rate, 2)
+    return {"requests": n_requests, "solves": cols, "operators": len(ops), "generation_s": round(gen_s, 1),
+            "mix": "jittered 4^3/8^3/12^3, p in {2,4,6,8}, lambda in {0,1,1000}, 1-8 nodal Fourier RHS, FP32 V-cycle",
+            "capacity": cap, f"at_{load}x_capacity": loaded}
+
+
 def cpu_baseline(prob, k, rtol, iters):
     """The oracle as it stands, on the host cores: two CG iterations (FP32 V-cycle, flexible CG)
     on the full workload, scaled to the GPU's iteration count."""
@@ -497,6 +538,9 @@ def main():
     args = parse()
     if args.summarize_launches:
         print(summarize_launches(args.summarize_launches, args.split_at))
+        return
+    if args.serving_full:
+        print(json.dumps({"serving_full": measure_serving_full()}))
         return
     if args.impl == "reference":
         run_reference(args)

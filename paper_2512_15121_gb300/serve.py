@@ -327,10 +327,12 @@ STREAM_LAMBDAS = (0.0, 1.0, 1000.0)
 
 
 def synthetic_stream(n_requests: int = 128, seed: int = 7, rate_per_s: float = 200.0, max_rhs: int = 8,
-                     meshes=STREAM_MESHES, orders=STREAM_ORDERS, lambdas=STREAM_LAMBDAS):
+                     meshes=STREAM_MESHES, orders=STREAM_ORDERS, lambdas=STREAM_LAMBDAS, rhs_kind: str = "fourier"):
     """Requests for Helmholtz / Poisson operators on jittered hex meshes (mesh seed = mesh size, so
     a (mesh, order, lambda) triple always names the same operator), 1..max_rhs smooth Fourier
-    right-hand sides seeded by request id, Poisson arrivals (exponential gaps) at rate_per_s."""
+    right-hand sides seeded by request id (rhs_kind "fourier": loaded by quadrature; "nodal": the
+    same fields evaluated at the nodes, for large streams), Poisson arrivals (exponential gaps) at
+    rate_per_s."""
     import fegen
     rng = np.random.default_rng(seed)
     ops = {}
@@ -351,7 +353,8 @@ def synthetic_stream(n_requests: int = 128, seed: int = 7, rate_per_s: float = 2
         r = int(rng.integers(1, max_rhs + 1))
         t += float(rng.exponential(1.0 / rate_per_s))
         prob = operator(n, p, lam)
-        rhs = np.stack([prob.rhs("fourier", 100000 + 64 * rid + j) for j in range(r)], axis=1)
+        load = prob.rhs_nodal if rhs_kind == "nodal" else (lambda sd, prob=prob: prob.rhs("fourier", sd))
+        rhs = np.stack([load(100000 + 64 * rid + j) for j in range(r)], axis=1)
         k = 3 if lam > 0 else 2
 
         def make(prob=prob, k=k):

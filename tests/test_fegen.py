@@ -115,3 +115,19 @@ def test_graded_mesh_aspect_ratio():
     assert abs(h[0] - 1.0 / 120.0) < 1e-12
     assert abs(h.sum() - 1.0) < 1e-12
     assert abs(h[1] / h[0] - 1.37618) < 1e-4
+
+
+def test_nodal_fourier_rhs():
+    """rhs_nodal: the Fourier field at the nodes, zero on Dirichlet rows, seeded; against a direct
+    evaluation of the defining sum at a few nodes."""
+    import numpy as np
+    prob = fegen.make(3, 2, mesh="jitter", lam=1.0, rhs="none")
+    f = prob.rhs_nodal(5)
+    assert np.array_equal(f, prob.rhs_nodal(5)) and not np.array_equal(f, prob.rhs_nodal(6))
+    assert np.all(f[prob.boundary != 0] == 0.0)
+    c = np.random.default_rng(5).standard_normal((4, 4, 4))
+    for i in np.flatnonzero(prob.boundary == 0)[:5]:
+        x, y, z = prob.coords[i]
+        ref = sum(c[a, b, d] * np.sin((a + 1) * np.pi * x) * np.sin((b + 1) * np.pi * y) * np.sin((d + 1) * np.pi * z)
+                  for a in range(4) for b in range(4) for d in range(4))
+        assert abs(f[i] - ref) <= 1e-12 * max(1.0, abs(ref))
