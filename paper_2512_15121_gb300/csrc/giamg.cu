@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -319,6 +322,23 @@ void read_host(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t 
   GIAMG_CUDA(cudaStreamSynchronize(s));
 }
 
+// Opt-in setup timing (environment GIAMG_SETUP_LOG set): wall time of each setup phase, taken
+// after a synchronisation of the stream, printed to stderr.
+struct SetupClock {
+  bool on = getenv("GIAMG_SETUP_LOG") != nullptr;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  explicit SetupClock(cudaStream_t st) : s(st) {}
+  void mark(const char* what, int level = -1) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "setup %-22s level %2d %9.2f ms\n", what, level,
+            std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int32_t n_elem,
                 const int32_t* elem_dof, const int32_t* elem_order, const double* coords, const giamg_options* optp,
                 void* stream) {
@@ -364,6 +384,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   Ctx* C = new Ctx();
   C->H = new Hierarchy();
   Hierarchy& H = *C->H;
+  SetupClock clk(s);
   try {
     H.opt = opt;
     H.stream = s;
@@ -411,6 +432,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     GIAMG_CHECK(diag_inverse(L0->A, L0->dinv.get(), L0->dinv32.get(), s), GIAMG_ERR_NOT_SPD,
                 "A has a non-positive or missing diagonal entry");
 
+    clk.mark("input, validation");
     // p-coarsening (Algorithms 2-4, 7) down to order 1
     while (H.lev.back()->order > 1 && (int)H.lev.size() < opt.max_levels) {
       Level& F = *H.lev.back();
@@ -419,8 +441,10 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       F.q = next_order(F.order);
       F.n_elem = n_elem;
       p_level_build(F, *Cl, s);
+      clk.mark("p-level map and P", (int)H.lev.size() - 1);
       Cl->order = F.q;
       galerkin(F, Cl->A, false, s);
+      clk.mark("p-level RAP", (int)H.lev.size() - 1);
       F.kind = GIAMG_LEVEL_P;
       Cl->avg_row = Cl->A.n ? (double)Cl->A.nnz / Cl->A.n : 0.0;
       Cl->dinv.alloc(std::max<int64_t>(Cl->A.n, 1), s);
@@ -433,6 +457,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     while (H.lev.back()->A.n > opt.coarse_max && (int)H.lev.size() < opt.max_levels) {
       Level& F = *H.lev.back();
       const int64_t n_agg = h_level_aggregate(F, opt.strength_theta, opt.hash_kind, s);
+      clk.mark("MIS-2, aggregates", (int)H.lev.size() - 1);
       if ((double)n_agg > 0.9 * (double)F.A.n) {
         F.agg.release();
         F.n_next = 0;
@@ -441,6 +466,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       h_level_prolongation(F, s);
       Level* Cl = new Level();
       galerkin(F, Cl->A, true, s);
+      clk.mark("SA-P and RAP", (int)H.lev.size() - 1);
       F.kind = GIAMG_LEVEL_H;
       Cl->order = 0;
       Cl->avg_row = Cl->A.n ? (double)Cl->A.nnz / Cl->A.n : 0.0;
@@ -462,14 +488,18 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
                 "coarsest matrix is not positive definite");
     Lc.Ainv.alloc((size_t)Lc.nc * Lc.nc, s);
     chol_inverse(Lc.L.get(), Lc.nc, Lc.Ainv.get(), s);
+    clk.mark("coarsest Cholesky");
     // smoother bounds, FP32 copies, work vectors
     C->ex.resize(H.lev.size());
     for (size_t l = 0; l < H.lev.size(); ++l) {
       Level& L = *H.lev[l];
       csr_to32(L.A, s);
+      clk.mark("FP32 copy", (int)l);
       if (opt.compress_patterns) {
         pattern_build(L.A, s, 1 << 16, 1 << 24);
+        clk.mark("row patterns", (int)l);
         groups_build(L.A, s, 1 << 22);
+        clk.mark("row groups, hybrid", (int)l);
       }
       if (opt.autotune) tune_rows(L.A, s);
       else choose_rows(L.A, opt.row_form, opt.row_threads);
@@ -477,6 +507,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       alloc_work(L, s);
       if (L.kind != GIAMG_LEVEL_COARSEST) {
         L.rho = lanczos_rho(L.A, opt.lanczos_steps, opt.hash_kind, H);
+        clk.mark("Lanczos", (int)l);
         GIAMG_CHECK(L.rho > 0.0 && std::isfinite(L.rho), GIAMG_ERR_NOT_SPD, "Lanczos bound is not positive");
         C->ex[l].cheb = cheb_coeffs(L.rho, opt.cheb_lo, opt.cheb_hi, opt.cheb_degree);
       }
