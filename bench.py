@@ -387,7 +387,15 @@ def run_ours(args):
         by = sum(res["prof"][c][2] for c in range(5))
         return round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None
 
-    extras = {} if args.no_extras else {"batch": measure_batch(g, torch), "serving": measure_serving()}
+    extras = {}
+    if not args.no_extras:
+        from paper_2512_15121_gb300 import tune
+        best_k, tk = tune.tune_cheb_degree(S, b, degrees=(1, 2, 3, 4, 5), precision=1, rtol=args.rtol)
+        extras["cheb_degree_tuning"] = {"best": best_k, "paper_default": k,
+                                        "ms": {t.degree: round(t.ms, 3) for t in tk},
+                                        "iters": {t.degree: t.iterations for t in tk}}
+        S.set_cheb_degree(k)
+        extras.update({"batch": measure_batch(g, torch), "serving": measure_serving()})
 
     value = max_over_ranks(td, mixed["p50"])
     ms_per_step = max_over_ranks(td, mixed["wall"] / args.steps)

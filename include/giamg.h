@@ -173,6 +173,11 @@ GIAMG_API int giamg_level_templates(giamg_handle h, int level, int64_t* n_templa
 GIAMG_API int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern);
 /* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */
 GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
+/* Change the degree k of every level's Chebyshev smoother (Sec. 2) after setup: the hierarchy
+ * and the Lanczos bounds are kept, only the polynomial's coefficients change, so the result is
+ * the handle giamg_setup would have built with cheb_degree = degree.  degree in [1, 64]
+ * (GIAMG_ERR_ARG otherwise).  Synchronises the handle's stream first. */
+GIAMG_API int giamg_set_cheb_degree(giamg_handle h, int degree);
 
 /* Single steps of the solve, on the handle's stream (parity tests call these):
  *   giamg_apply_vcycle: z = V(r), Algorithm 1 from the finest level (precision 0 / 1).

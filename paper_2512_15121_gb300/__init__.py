@@ -26,7 +26,7 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
            "giamg_solve_batch", "giamg_solve_batch_ex",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
-           "giamg_level_rho", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
+           "giamg_level_rho", "giamg_set_cheb_degree", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
            "giamg_last_error", "giamg_set_device_ptrs", "giamg_profile_enable", "giamg_profile_read",
            "giamg_launch_count", "giamg_true_relres_noalloc"]
@@ -322,6 +322,11 @@ class Solver:
         t, p = ctypes.c_int(), ctypes.c_int()
         _check(lib().giamg_level_kernel(self._h, l, precision, ctypes.byref(t), ctypes.byref(p)))
         return t.value, ["csr", "pattern", "groups", "hybrid"][p.value]
+
+    def set_cheb_degree(self, k: int):
+        """Smoother degree k on every level, keeping the hierarchy (giamg_set_cheb_degree)."""
+        _check(lib().giamg_set_cheb_degree(self._h, int(k)))
+        self.opts.cheb_degree = int(k)
 
     def rho_hat(self, l):
         r = ctypes.c_double()

@@ -1246,6 +1246,32 @@ int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_pe
   });
 }
 
+int giamg_set_cheb_degree(giamg_handle h, int degree) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Hierarchy& H = *C.H;
+    GIAMG_CHECK(degree >= 1 && degree <= 64, GIAMG_ERR_ARG, "cheb_degree must be in [1, 64]");
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));  // no solve of the old polynomial in flight
+    H.opt.cheb_degree = degree;
+    for (size_t l = 0; l < H.lev.size(); ++l)
+      if (H.lev[l]->kind != GIAMG_LEVEL_COARSEST)
+        C.ex[l].cheb = cheb_coeffs(H.lev[l]->rho, H.opt.cheb_lo, H.opt.cheb_hi, degree);
+    // the captured solve graphs hold the old coefficients as kernel arguments
+    for (SolveGraph& G : H.graph)
+      if (G.exec) {
+        GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
+        G = SolveGraph{};
+      }
+    for (auto& per_m : H.bgraph)
+      for (SolveGraph& G : per_m)
+        if (G.exec) {
+          GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
+          G = SolveGraph{};
+        }
+    return GIAMG_OK;
+  });
+}
+
 int giamg_level_rho(giamg_handle h, int level, double* rho_hat) {
   return guarded([&] {
     GIAMG_CHECK(rho_hat, GIAMG_ERR_ARG, "rho_hat is NULL");

@@ -439,3 +439,60 @@ def test_graph_captured_from_the_second_solve():
         assert counts[1] == counts[2] == counts[0] + 1 + it
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_cheb_degree_equals_fresh_setup(precision):
+    """Changing the smoother degree after setup gives the handle a fresh setup with that degree
+    would build: same iterations and solution bits (graph path, which is recaptured)."""
+    prob, orc, _, k = setup_case("jitter6_p6")
+    s = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=2)
+    try:
+        b = dev(prob.b)
+        s.solve(b, rtol=1e-8, precision=precision)  # a graph of the old degree exists
+        for deg in (1, 2, 5):
+            s.set_cheb_degree(deg)
+            x, it, rr = s.solve(b, rtol=1e-8, precision=precision)
+            fresh = g.Solver.from_problem(prob, device=True, cheb_degree=deg, graphs=2)
+            try:
+                xf, itf, rrf = fresh.solve(b, rtol=1e-8, precision=precision)
+            finally:
+                fresh.close()
+            assert it == itf and rr == rrf and torch.equal(x, xf), deg
+    finally:
+        s.close()
+
+
+def test_set_cheb_degree_matches_oracle_and_errors():
+    prob, orc, _, k = setup_case("cube4_p4")
+    s = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+    try:
+        s.set_cheb_degree(5)
+        o5 = oracle.Hierarchy.from_problem(prob, cheb_degree=5)
+        try:
+            xo, ito, _, _, _ = o5.solve(prob.b, rtol=1e-8)
+        finally:
+            o5.close()
+        x, it, _ = s.solve(dev(prob.b), rtol=1e-8, force_iters=ito)
+        assert np.linalg.norm(host(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+        with pytest.raises(g.GiamgError):
+            s.set_cheb_degree(0)
+    finally:
+        s.close()
+
+
+def test_tune_cheb_degree():
+    from paper_2512_15121_gb300 import tune
+    prob, orc, _, k = setup_case("jitter6_p6")
+    s = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+    try:
+        best, timings = tune.tune_cheb_degree(s, dev(prob.b), degrees=(1, 2, 3), reps=2, warmup=1)
+        assert best in (1, 2, 3) and [t.degree for t in timings] == [1, 2, 3]
+        assert all(t.ms > 0 and t.iterations > 0 for t in timings)
+        chosen = next(t for t in timings if t.degree == best)
+        assert chosen.relres <= 1e-8 and chosen.ms == min(t.ms for t in timings if t.relres <= 1e-8)
+        assert s.opts.cheb_degree == best
+        # fewer iterations with a higher degree (the polynomial smooths more per V-cycle)
+        assert timings[2].iterations <= timings[0].iterations
+    finally:
+        s.close()
