@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int),
-                ("strength_theta", ctypes.c_double), ("hash_kind", ctypes.c_int)]
+                ("strength_theta", ctypes.c_double), ("hash_kind", ctypes.c_int), ("p_schedule", ctypes.c_int)]
 
 
 class _CSR(ctypes.Structure):
@@ -65,6 +65,8 @@ def _lib():
             L.orc_hash.restype = ctypes.c_uint32
             L.orc_gll_nodes.argtypes = [i32, vp]
             L.orc_next_order.argtypes = [i32]
+            L.orc_next_order_sched.argtypes = [i32, i32]
+            L.orc_anchor_index.argtypes = [i32, i32, i32, ctypes.POINTER(i32)]
             L.orc_p1d.argtypes = [i32, i32, vp]
             L.orc_spgemm.argtypes = [ctypes.POINTER(_CSR)] * 3
             L.orc_transpose.argtypes = [ctypes.POINTER(_CSR)] * 2
@@ -128,8 +130,15 @@ def gll_nodes(p: int) -> np.ndarray:
     return x
 
 
-def next_order(p: int) -> int:
-    return _lib().orc_next_order(p)
+def next_order(p: int, schedule: int = 0) -> int:
+    return _lib().orc_next_order_sched(p, schedule)
+
+
+def anchor_index(p: int, q: int, s: int):
+    """(fine index, tie) labelling coarse index s: see orc_anchor_index."""
+    tie = ctypes.c_int()
+    a = _lib().orc_anchor_index(p, q, s, ctypes.byref(tie))
+    return a, bool(tie.value)
 
 
 def p1d(p: int, q: int) -> np.ndarray:

@@ -133,6 +133,46 @@ int orc_next_order(int p) {
   return 1;
 }
 
+/* The other p schedules (the paper compares coarsening by one and by two, Sec. 3.2). */
+int orc_next_order_sched(int p, int schedule) {
+  if (p <= 1) return 1;
+  if (schedule == 1) return p - 1;
+  if (schedule == 2) return p > 2 ? p - 2 : 1;
+  return orc_next_order(p);
+}
+
+/* Labels of coarse nodes by fine nodes (Algorithm 2, generalised to any q < p).  With r = p/q
+   whole, coarse node s is labelled by fine node r s.  Otherwise by the fine node nearest to the
+   fraction s p / q of the edge; when s p / q is half way between two fine nodes, both are
+   candidates and orc_coarse_anchor keeps the one with the smaller global id, a choice that does
+   not depend on how an element is oriented (reflecting an edge maps the two candidates onto
+   each other).  Since p / q > 1, different coarse nodes never share a candidate. */
+int orc_anchor_index(int p, int q, int s, int* tie) {
+  const int f = (s * p) / q, rem = (s * p) % q;
+  *tie = 0;
+  if (rem == 0) return f;
+  if (2 * rem < q) return f;
+  if (2 * rem > q) return f + 1;
+  *tie = 1;
+  return f;  /* candidates f and f + 1 */
+}
+
+/* the fine dof labelling coarse local node (i, j, k): the smallest global id among the
+   candidates of the three directions */
+static int32_t orc_coarse_anchor(int p, int q, const int32_t* df_arr, int i, int j, int k) {
+  int ti, tj, tk;
+  const int ai = orc_anchor_index(p, q, i, &ti), aj = orc_anchor_index(p, q, j, &tj), ak = orc_anchor_index(p, q, k, &tk);
+  const int n1 = p + 1;
+  int32_t best = INT32_MAX;
+  for (int di = 0; di <= ti; ++di)
+    for (int dj = 0; dj <= tj; ++dj)
+      for (int dk = 0; dk <= tk; ++dk) {
+        const int32_t g = df_arr[(n1 * n1) * (ai + di) + n1 * (aj + dj) + (ak + dk)];
+        if (g < best) best = g;
+      }
+  return best;
+}
+
 /* P1D[a][b] = l_b^(q)(xi_a^(p)): order-q Lagrange basis on the order-q GLL nodes evaluated at
    the order-p GLL nodes, product formula multiplied in ascending m. */
 void orc_p1d(int p, int q, double* tab) {
@@ -245,13 +285,14 @@ int orc_transpose(const orc_csr* A, orc_csr* T) {
 }
 
 /* ======================================================================= p-coarsening */
-/* Algorithm 2 with a nodal stride: the coarse local node (i,j,k), i,j,k <= q, is the fine
-   local node (ri, rj, rk), r = p/q; the dof ids are copied in coarse local order. */
+/* Algorithm 2 with nodal labels: the coarse local node (i,j,k), i,j,k <= q, is labelled by the
+   fine node of orc_coarse_anchor ((ri, rj, rk) when r = p/q is whole); the labels are copied in
+   coarse local order. */
 static void orc_extract_next_dof(int p, int q, const int32_t* df_arr, int32_t* dc_arr) {
-  int r = p / q, n1 = p + 1, c = 0;
+  int c = 0;
   for (int i = 0; i <= q; ++i)
     for (int j = 0; j <= q; ++j)
-      for (int k = 0; k <= q; ++k) dc_arr[c++] = df_arr[(n1 * n1) * (r * i) + n1 * (r * j) + (r * k)];
+      for (int k = 0; k <= q; ++k) dc_arr[c++] = orc_coarse_anchor(p, q, df_arr, i, j, k);
 }
 
 /* Algorithm 3: collect the retained fine dofs over all elements (skipping those already
@@ -695,6 +736,7 @@ void orc_default_options(orc_options* o) {
   o->max_levels = 16;
   o->strength_theta = 0.0;
   o->hash_kind = 0;
+  o->p_schedule = 0;
 }
 
 static int orc_copy_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, const double* v, orc_csr* A) {
@@ -754,7 +796,7 @@ int orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, 
   while (h->lev[h->nlev - 1].order > 1 && h->nlev < opt->max_levels) {
     orc_level* f = &h->lev[h->nlev - 1];
     orc_level* c = &h->lev[h->nlev];
-    int pf = f->order, q = orc_next_order(pf);
+    int pf = f->order, q = orc_next_order_sched(pf, opt->p_schedule);
     int64_t n_c;
     int32_t* collect = orc_dof_next(f->A.n, n_elem, pf, q, f->l2g, &n_c);
     c->l2g = orc_l2g_next(f->A.n, n_elem, pf, q, f->l2g, collect, n_c);

@@ -45,6 +45,8 @@ typedef struct {
   int max_levels;
   double strength_theta; /* 0: structural strength graph */
   int hash_kind;         /* 0: SplitMix64-based hash; 1: identity hash h(i) = i */
+  int p_schedule;        /* 0: halving (q = p/2, odd p: largest proper divisor), 1: q = p - 1,
+                            2: q = p - 2 (at least 1) */
 } orc_options;
 
 typedef struct orc_hier orc_hier;
@@ -55,6 +57,11 @@ void orc_default_options(orc_options* o);
 uint32_t orc_hash(int kind, int64_t i);
 void orc_gll_nodes(int p, double* xi);
 int orc_next_order(int p);
+int orc_next_order_sched(int p, int schedule);
+/* fine local index (per direction) that labels coarse local index s (0..q) of an order-q
+   element inside an order-p one: s p / q when that is whole, else the nearer index; *tie is set
+   when s p / q lies half way (both neighbours then label it, see orc_coarse_anchor) */
+int orc_anchor_index(int p, int q, int s, int* tie);
 void orc_p1d(int p, int q, double* tab /* [(p+1)][(q+1)] */);
 int orc_spgemm(const orc_csr* A, const orc_csr* B, orc_csr* C);
 int orc_transpose(const orc_csr* A, orc_csr* T);

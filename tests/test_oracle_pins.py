@@ -488,3 +488,124 @@ def test_results_do_not_depend_on_thread_count():
         assert r.returncode == 0, r.stderr
         outs.append(r.stdout.strip())
     assert outs[0] == outs[1]
+
+
+# ----------------------------------------------------------------------------- other p schedules
+def test_p_schedules_by_one_and_two():
+    assert [oracle.next_order(p, 1) for p in range(1, 9)] == [1, 1, 2, 3, 4, 5, 6, 7]
+    assert [oracle.next_order(p, 2) for p in range(1, 9)] == [1, 1, 1, 2, 3, 4, 5, 6]
+
+
+@pytest.mark.parametrize("p", range(2, 13))
+def test_coarse_labels_injective_symmetric_and_exact_for_whole_ratios(p):
+    """Labels per direction: whole ratios give r s; otherwise the nearest fine index, both
+    neighbours at exactly half way; distinct coarse indices never share a candidate; reflecting
+    the edge (s -> q - s) reflects the candidates (a -> p - a)."""
+    for q in range(1, p):
+        cands = []
+        for s in range(q + 1):
+            a, tie = oracle.anchor_index(p, q, s)
+            c = {a, a + 1} if tie else {a}
+            if p % q == 0:
+                assert not tie and a == (p // q) * s
+            else:
+                x = s * p / q
+                assert all(abs(ci - x) <= 0.5 for ci in c) and (tie == (abs(x - a) == 0.5))
+            cands.append(c)
+        assert all(not (cands[s] & cands[t]) for s in range(q + 1) for t in range(s))
+        assert all({p - ci for ci in cands[q - s]} == cands[s] for s in range(q + 1))
+
+
+def _coarse_positions(prob, H, level):
+    """Physical position of every (element, coarse local node) of `level`: the trilinear image of
+    the order-q GLL point in the element's own local frame (its corners are fine dofs)."""
+    p = prob.p
+    q = H.level_info(level)["order"]
+    nlc = (q + 1) ** 3
+    l2g = np.empty((prob.n_elem, nlc), np.int32)
+    oracle._lib().orc_level_extra(H._h, level, None, oracle._p(l2g))
+    xq = (oracle.gll_nodes(q) + 1.0) / 2.0
+    n1 = p + 1
+    corners = [(a * p) * n1 * n1 + (b * p) * n1 + (c * p) for a in (0, 1) for b in (0, 1) for c in (0, 1)]
+    t = np.arange(nlc)
+    u, v, w = xq[t // (q + 1) ** 2], xq[(t // (q + 1)) % (q + 1)], xq[t % (q + 1)]
+    wts = np.stack([(u if a else 1 - u) * (v if b else 1 - v) * (w if c else 1 - w)
+                    for a in (0, 1) for b in (0, 1) for c in (0, 1)], axis=1)  # nlc x 8
+    C = prob.coords[prob.elem_dof[:, corners]]  # n_elem x 8 x 3, the element's local frame
+    return l2g, np.einsum("tc,ecd->etd", wts, C)
+
+
+@pytest.mark.parametrize("p,schedule", [(5, 1), (5, 2), (7, 1), (4, 1), (6, 2)])
+def test_coarse_numbering_conforms_under_relabelling_and_symmetries(p, schedule):
+    """Every element sharing a coarse dof places it at the same point, and different points get
+    different dofs: on a jittered mesh with relabelled global ids and per-element index
+    symmetries (reflections and axis permutations of the local order)."""
+    # a third level keeps the oracle's dense coarsest factorisation small
+    prob = fegen.make(3 if p <= 6 else 2, p, mesh="jitter", lam=1.0, perm_seed=3, sym_seed=4, rhs="none")
+    H = oracle.Hierarchy.from_problem(prob, p_schedule=schedule, coarse_max=1, max_levels=3)
+    n_c = H.level_info(1)["n"]
+    l2g, pos = _coarse_positions(prob, H, 1)
+    ref = np.full((n_c, 3), np.nan)
+    ref[l2g.ravel()] = pos.reshape(-1, 3)  # one of the copies of each dof
+    assert not np.isnan(ref).any()
+    assert np.max(np.abs(ref[l2g] - pos)) < 1e-12  # every copy agrees
+    assert len({tuple(np.round(x, 10)) for x in ref}) == n_c
+
+
+@pytest.mark.parametrize("p,schedule", [(5, 1), (5, 2), (7, 1), (3, 1)])
+def test_prolongation_reproduces_degree_q_fields_other_schedules(p, schedule):
+    """P interpolates order-q fields exactly.  On a jittered (trilinear) mesh a physical field of
+    degree d_x, d_y, d_z is a reference field of degree d_x + d_y + d_z per direction, so those with
+    that sum <= q are reproduced; on a uniform mesh every field of degree <= q per direction."""
+    prob = fegen.make(2, p, mesh="jitter", lam=1.0, sym_seed=2, rhs="none")
+    H = oracle.Hierarchy.from_problem(prob, p_schedule=schedule, coarse_max=1, max_levels=3)
+    q = H.level_info(1)["order"]
+    assert q == oracle.next_order(p, schedule)
+    l2g, pos = _coarse_positions(prob, H, 1)
+    Xc = np.empty((H.level_info(1)["n"], 3))
+    Xc[l2g.ravel()] = pos.reshape(-1, 3)
+    rp, ci, v, m = H.prolongation(0)
+    P = sp.csr_matrix((v, ci, rp), shape=(prob.n, m))
+    assert np.allclose(P @ np.ones(m), 1.0, atol=1e-13)
+    for a, b, c in [(1, 0, 0), (0, 1, 1), (1, 1, 1), (2, 0, 1)]:
+        if a + b + c > q:
+            continue
+        f = lambda X: X[:, 0] ** a * X[:, 1] ** b * X[:, 2] ** c
+        assert np.max(np.abs(P @ f(Xc) - f(prob.coords))) < 1e-12, (a, b, c)
+    uni = fegen.make(2, p, mesh="uniform", lam=1.0, rhs="none")
+    Hu = oracle.Hierarchy.from_problem(uni, p_schedule=schedule, coarse_max=1, max_levels=3)
+    l2g, pos = _coarse_positions(uni, Hu, 1)
+    Xc = np.empty((Hu.level_info(1)["n"], 3))
+    Xc[l2g.ravel()] = pos.reshape(-1, 3)
+    rp, ci, v, m = Hu.prolongation(0)
+    P = sp.csr_matrix((v, ci, rp), shape=(uni.n, m))
+    f = lambda X: X[:, 0] ** q * X[:, 1] ** (q - 1) * X[:, 2] + X[:, 2] ** q
+    assert np.max(np.abs(P @ f(Xc) - f(uni.coords))) < 1e-12
+
+
+@pytest.mark.parametrize("mesh,p,schedule,kappa,lam", [("jitter", 5, 1, 0, 1.0), ("jitter", 5, 2, 1, 10.0),
+                                                       ("graded", 3, 1, 0, 1000.0), ("uniform", 7, 1, 0, 1.0)])
+def test_rap_equals_direct_assembly_other_schedules(mesh, p, schedule, kappa, lam):
+    """With p/q not whole the coarse space is still the order-q space on the mesh, so R A P is
+    the order-q operator assembled with the fine rule (the labels keep fegen's order)."""
+    n = 2
+    fine = fegen.make(n, p, mesh=mesh, lam=lam, kappa=kappa, dirichlet=False, rhs="none")
+    H = oracle.Hierarchy.from_problem(fine, coarse_max=1, p_schedule=schedule, max_levels=3)
+    q = H.level_info(1)["order"]
+    direct = fegen.make(n, q, mesh=mesh, lam=lam, kappa=kappa, nq=p + 2, dirichlet=False, rhs="none")
+    rp, ci, v, _ = H.level(1)
+    Ac = sp.csr_matrix((v, ci, rp), shape=(direct.n, direct.n)).toarray()
+    Ad = direct.scipy().toarray()
+    assert np.max(np.abs(Ac - Ad)) <= 1e-12 * np.max(np.abs(Ad))
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_pcg_other_schedules_match_dense_direct_solve(schedule):
+    prob = fegen.make(2, 5, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob, p_schedule=schedule)
+    orders = [H.level_info(l)["order"] for l in range(H.num_levels)]
+    assert orders[:2] == [5, oracle.next_order(5, schedule)]
+    x, it, rr, _, st = H.solve(prob.b, rtol=1e-10)
+    assert st == "ok"
+    xd = np.linalg.solve(prob.scipy().toarray(), prob.b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
