@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the multi-RHS and serving measurements")
+    ap.add_argument("--schedules", action="store_true",
+                    help="compare the p schedules (halving, by one, by two) on two 16^3 operators and print them")
     ap.add_argument("--serving-full", action="store_true",
                     help="run only the 512-request serving stream (36 operators up to 12^3, p = 8) and print it")
     ap.add_argument("--summarize-launches", metavar="CSV",
@@ -528,6 +530,50 @@ def measure_serving_full(n_requests=512, load=0.8):
             "capacity": cap, f"at_{load}x_capacity": loaded}
 
 
+def measure_schedules(steps=10, warmup=3):
+    """The p schedules compared (the paper compares coarsening by one and by two): halving, by one
+    and by two on the 16^3 p = 6 benchmark operator and on a 16^3 p = 5 one; levels, iterations,
+    solve time (FP32 V-cycle in FP64 FCG and FP64 PCG, CUDA-event medians) and setup time."""
+    import statistics
+    import torch
+    import fegen
+    import paper_2512_15121_gb300 as g
+    out = {}
+    for name, cfg, k in (("helmholtz_16cube_jitter_p6", fegen.WORKLOADS["helmholtz_16cube_jitter_p6"], 3),
+                         ("helmholtz_16cube_jitter_p5", dict(n=16, p=5, mesh="jitter", mesh_seed=1, lam=10.0,
+                                                             rhs="manufactured"), 3)):
+        cfg = {key: v for key, v in cfg.items() if key != "k"}
+        prob = fegen.make(**cfg)
+        b = torch.from_numpy(prob.b).cuda()
+        res = {}
+        for sched, label in ((0, "halving"), (1, "by_one"), (2, "by_two")):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S = g.Solver.from_problem(prob, device=True, cheb_degree=k, p_schedule=sched)
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            row = {"levels": [[S.level_info(l)["n"], S.level_info(l)["order"]] for l in range(S.num_levels)],
+                   "setup_ms": round(setup_ms, 1)}
+            for prec, key in ((1, "mixed"), (0, "fp64")):
+                for _ in range(warmup):
+                    S.solve(b, rtol=1e-8, precision=prec)
+                ts = []
+                for _ in range(steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    _, it, rr = S.solve(b, rtol=1e-8, precision=prec)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                row[key] = {"iters": int(it), "relres": rr, "ms": round(statistics.median(ts), 3),
+                            "ms_per_iter": round(statistics.median(ts) / it, 3)}
+            S.close()
+            res[label] = row
+        out[name] = res
+        prob.close()
+    return out
+
+
 def cpu_baseline(prob, k, rtol, iters):
     """The oracle as it stands, on the host cores: two CG iterations (FP32 V-cycle, flexible CG)
     on the full workload, scaled to the GPU's iteration count."""
@@ -546,6 +592,9 @@ def main():
     args = parse()
     if args.summarize_launches:
         print(summarize_launches(args.summarize_launches, args.split_at))
+        return
+    if args.schedules:
+        print(json.dumps({"schedules": measure_schedules()}))
         return
     if args.serving_full:
         print(json.dumps({"serving_full": measure_serving_full()}))

@@ -101,6 +101,10 @@ typedef struct {
                              one synchronisation per iteration.  All give the same iterations
                              and bits.  The host loop is used while profiling or when
                              force_iters > max_iter. */
+  int p_schedule;         /* order sequence of the p-levels: 0 (default) halving, q = p/2 (odd p:
+                             its largest proper divisor); 1 by one, q = p - 1; 2 by two,
+                             q = p - 2 (at least 1).  When p/q is not whole, coarse nodes are
+                             numbered by their nearest fine nodes (ties: the smaller global id) */
 } giamg_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -43,8 +43,11 @@ Hierarchy::~Hierarchy() {
 
 namespace {
 
-int next_order(int p) {
+// p schedule: 0 halving (q = p/2; odd p: its largest proper divisor), 1 by one, 2 by two
+int next_order(int p, int schedule) {
   if (p <= 1) return 1;
+  if (schedule == 1) return p - 1;
+  if (schedule == 2) return p > 2 ? p - 2 : 1;
   if (p % 2 == 0) return p / 2;
   for (int d = p / 2; d >= 1; --d)
     if (p % d == 0) return d;
@@ -358,6 +361,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
               GIAMG_ERR_ARG, "row_threads must be 0, 4, 8, 16 or 32");
   GIAMG_CHECK(opt.prefetch_rows >= -1, GIAMG_ERR_ARG, "prefetch_rows must be -1, 0 or positive");
   GIAMG_CHECK(opt.graphs >= 0 && opt.graphs <= 2, GIAMG_ERR_ARG, "graphs must be 0, 1 or 2");
+  GIAMG_CHECK(opt.p_schedule >= 0 && opt.p_schedule <= 2, GIAMG_ERR_ARG, "p_schedule must be 0, 1 or 2");
   GIAMG_CHECK(opt.row_chains == 0 || opt.row_chains == 2 || opt.row_chains == 4 || opt.row_chains == 8, GIAMG_ERR_ARG,
               "row_chains must be 0, 2, 4 or 8");
   const bool dev = opt.device_ptrs != 0;
@@ -438,7 +442,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       Level& F = *H.lev.back();
       Level* Cl = new Level();
       F.p = F.order;
-      F.q = next_order(F.order);
+      F.q = next_order(F.order, opt.p_schedule);
       F.n_elem = n_elem;
       p_level_build(F, *Cl, s);
       clk.mark("p-level map and P", (int)H.lev.size() - 1);
@@ -1109,6 +1113,7 @@ void giamg_default_options(giamg_options* o) {
   o->row_threads = 0;
   o->prefetch_rows = -1;
   o->graphs = 1;
+  o->p_schedule = 0;
   o->row_chains = 0;
 }
 

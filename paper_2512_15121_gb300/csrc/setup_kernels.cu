@@ -446,25 +446,46 @@ __global__ void lanczos_next(int64_t n, double* __restrict__ v, double* __restri
 }
 
 // ================================================================== p-level construction
+// The fine node labelling coarse local node (i, j, k) of element e (Algorithm 2 with nodal
+// labels, any q < p).  Per direction, coarse index s is labelled by fine index s p / q when that
+// is whole (r = p/q whole: the node (ri, rj, rk)), else by the nearer fine index; at exactly half
+// way both neighbours are candidates, and the candidate with the smallest global id wins -- the
+// same node seen from every element sharing it, whatever its orientation.  p / q > 1 keeps the
+// candidates of different coarse nodes apart.
+__device__ __forceinline__ int anchor_axis(int p, int q, int s, int& ties) {
+  const int f = (s * p) / q, rem = (s * p) % q;
+  ties = (rem != 0 && 2 * rem == q) ? 1 : 0;
+  return (rem != 0 && 2 * rem > q) ? f + 1 : f;
+}
+__device__ __forceinline__ int32_t coarse_anchor(const int32_t* __restrict__ le, int p, int q, int i, int j, int k) {
+  const int n1 = p + 1;
+  int ti, tj, tk;
+  const int ai = anchor_axis(p, q, i, ti), aj = anchor_axis(p, q, j, tj), ak = anchor_axis(p, q, k, tk);
+  int32_t best = le[(n1 * n1) * ai + n1 * aj + ak];
+  for (int di = 0; di <= ti; ++di)
+    for (int dj = 0; dj <= tj; ++dj)
+      for (int dk = 0; dk <= tk; ++dk) best = min(best, le[(n1 * n1) * (ai + di) + n1 * (aj + dj) + (ak + dk)]);
+  return best;
+}
 __global__ void mark_anchors(int32_t n_elem, int p, int q, const int32_t* __restrict__ l2g, int32_t* __restrict__ flag) {
-  const int n1 = p + 1, m1 = q + 1, r = p / q;
+  const int n1 = p + 1, m1 = q + 1;
   const int64_t nlc = (int64_t)m1 * m1 * m1, nlf = (int64_t)n1 * n1 * n1;
   GRID_STRIDE(t, (int64_t)n_elem * nlc) {
     const int64_t e = t / nlc;
     const int b = (int)(t % nlc);
     const int i = b / (m1 * m1), j = (b / m1) % m1, k = b % m1;
-    flag[l2g[e * nlf + (int64_t)(n1 * n1) * (r * i) + n1 * (r * j) + r * k]] = 1;
+    flag[coarse_anchor(l2g + e * nlf, p, q, i, j, k)] = 1;
   }
 }
 __global__ void coarse_map(int32_t n_elem, int p, int q, const int32_t* __restrict__ l2g, const int64_t* __restrict__ rank,
                            int32_t* __restrict__ l2g_c) {
-  const int n1 = p + 1, m1 = q + 1, r = p / q;
+  const int n1 = p + 1, m1 = q + 1;
   const int64_t nlc = (int64_t)m1 * m1 * m1, nlf = (int64_t)n1 * n1 * n1;
   GRID_STRIDE(t, (int64_t)n_elem * nlc) {
     const int64_t e = t / nlc;
     const int b = (int)(t % nlc);
     const int i = b / (m1 * m1), j = (b / m1) % m1, k = b % m1;
-    l2g_c[t] = (int32_t)rank[l2g[e * nlf + (int64_t)(n1 * n1) * (r * i) + n1 * (r * j) + r * k]];
+    l2g_c[t] = (int32_t)rank[coarse_anchor(l2g + e * nlf, p, q, i, j, k)];
   }
 }
 __global__ void owner_min(int64_t slots, int nlf, const int32_t* __restrict__ l2g, int32_t* __restrict__ owner) {

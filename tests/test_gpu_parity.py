@@ -31,6 +31,9 @@ CASES = {
     "jitter6_p4_relabelled": dict(n=6, p=4, mesh="jitter", lam=1.0, perm_seed=5, sym_seed=6, k=3),
     "jitter12_p2_ragged": dict(n=(12, 11, 13), p=2, mesh="jitter", lam=1.0, k=2),
     "cube2_p3_odd": dict(n=2, p=3, mesh="uniform", lam=1.0, k=3),
+    # non-halving p schedules: coarse nodes labelled by their nearest fine nodes
+    "jitter4_p5_by_one": dict(n=4, p=5, mesh="jitter", lam=1.0, perm_seed=5, sym_seed=6, k=3, opts=dict(p_schedule=1)),
+    "jitter3_p7_by_two": dict(n=3, p=7, mesh="jitter", lam=10.0, k=2, opts=dict(p_schedule=2)),
 }
 
 _cache = {}
@@ -40,9 +43,10 @@ def setup_case(name):
     if name not in _cache:
         cfg = dict(CASES[name])
         k = cfg.pop("k")
+        opts = cfg.pop("opts", {})
         prob = fegen.make(**cfg)
-        orc = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
-        gpu = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+        orc = oracle.Hierarchy.from_problem(prob, cheb_degree=k, **opts)
+        gpu = g.Solver.from_problem(prob, device=True, cheb_degree=k, **opts)
         _cache[name] = (prob, orc, gpu, k)
     return _cache[name]
 
