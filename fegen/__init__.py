@@ -51,7 +51,7 @@ class _Params(ctypes.Structure):
                 ("grade_first", ctypes.c_double), ("kappa_kind", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("dirichlet", ctypes.c_int),
                 ("rhs_kind", ctypes.c_int), ("rhs_seed", ctypes.c_uint64),
-                ("perm_seed", ctypes.c_uint64), ("sym_seed", ctypes.c_uint64)]
+                ("perm_seed", ctypes.c_uint64), ("sym_seed", ctypes.c_uint64), ("basis", ctypes.c_int)]
 
 
 def _lib():
@@ -151,12 +151,15 @@ class Problem:
 def make(n: int | tuple = 4, p: int = 4, mesh: str = "uniform", lam: float = 1.0, kappa: int = 0,
          mesh_seed: int = 1, jitter: float = 0.2, grade_first: float = 0.0, nq: int = 0,
          dirichlet: bool = True, rhs: str = "manufactured", rhs_seed: int = 1000,
-         perm_seed: int = 0, sym_seed: int = 0, with_values: bool = True) -> Problem:
-    """Assemble -div(kappa grad u) + lam u = f on an n^3 (or nx*ny*nz) hex mesh of order p."""
+         perm_seed: int = 0, sym_seed: int = 0, with_values: bool = True, basis: str = "nodal") -> Problem:
+    """Assemble -div(kappa grad u) + lam u = f on an n^3 (or nx*ny*nz) hex mesh of order p, in the
+    nodal GLL basis or the modal (hierarchical) one.  For the modal basis, `coords` holds the GLL
+    lattice positions the modes are numbered by, not nodes of the functions."""
     nx, ny, nz = (n, n, n) if isinstance(n, int) else tuple(n)
     L = _lib()
     prm = _Params(nx, ny, nz, p, nq, MESH[mesh], jitter, mesh_seed, grade_first, kappa, lam,
-                  1 if dirichlet else 0, RHS[rhs], rhs_seed, perm_seed, sym_seed)
+                  1 if dirichlet else 0, RHS[rhs], rhs_seed, perm_seed, sym_seed,
+                  {"nodal": 0, "modal": 1}[basis])
     ctx = ctypes.c_void_p()
     rc = L.fegen_create(ctypes.byref(prm), ctypes.byref(ctx))
     if rc != 0:
@@ -178,7 +181,7 @@ def make(n: int | tuple = 4, p: int = 4, mesh: str = "uniform", lam: float = 1.0
     prob = Problem(nx, ny, nz, p, N, NNZ, row_ptr, col, val, elem_dof, coords, bnd, None,
                    dict(n=(nx, ny, nz), p=p, mesh=mesh, lam=lam, kappa=kappa, mesh_seed=mesh_seed,
                         jitter=jitter, nq=nq, dirichlet=dirichlet, rhs=rhs, rhs_seed=rhs_seed,
-                        perm_seed=perm_seed, sym_seed=sym_seed), ctx)
+                        perm_seed=perm_seed, sym_seed=sym_seed, basis=basis), ctx)
     if rhs != "none":
         prob.b = prob.rhs(rhs, rhs_seed)
     return prob

@@ -139,6 +139,36 @@ static double fg_lagrange_d(int p, const double* xi, int a, double t) {
   return s;
 }
 
+/* Jacobi polynomial P_n^(a,b)(x) by its three-term recurrence. */
+static double fg_jacobi(int n, double a, double b, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0, p1 = 0.5 * ((a + b + 2.0) * x + (a - b));
+  for (int k = 2; k <= n; ++k) {
+    const double c = 2.0 * k + a + b;
+    const double a1 = 2.0 * k * (k + a + b) * (c - 2.0);
+    const double a2 = (c - 1.0) * (c * (c - 2.0) * x + a * a - b * b);
+    const double a3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * c;
+    const double p2 = (a2 * p1 - a3 * p0) / a1;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+/* hierarchical 1D modes at local index m of order p, and their derivatives */
+static double fg_modal(int p, int m, double x) {
+  if (m == 0) return 0.5 * (1.0 - x);
+  if (m == p) return 0.5 * (1.0 + x);
+  return 0.25 * (1.0 - x) * (1.0 + x) * fg_jacobi(m - 1, 1.0, 1.0, x);
+}
+static double fg_modal_d(int p, int m, double x) {
+  if (m == 0) return -0.5;
+  if (m == p) return 0.5;
+  /* d/dx P_n^(1,1) = (n + 3)/2 P_(n-1)^(2,2) */
+  const int n = m - 1;
+  const double dp = n > 0 ? 0.5 * (n + 3.0) * fg_jacobi(n - 1, 2.0, 2.0, x) : 0.0;
+  return -0.5 * x * fg_jacobi(n, 1.0, 1.0, x) + 0.25 * (1.0 - x) * (1.0 + x) * dp;
+}
+
 /* ---------------------------------------------------------------- context */
 struct fegen_ctx {
   fegen_params prm;
@@ -426,6 +456,8 @@ static double fg_grade_ratio(int n, double h0) {
 int fegen_create(const fegen_params* prm, fegen_ctx** out) {
   *out = NULL;
   if (prm->p < 1 || prm->p > FEGEN_MAXP || prm->nx < 1 || prm->ny < 1 || prm->nz < 1) return -1;
+  if (prm->basis != FEGEN_BASIS_NODAL && prm->basis != FEGEN_BASIS_MODAL) return -1;
+  if (prm->basis == FEGEN_BASIS_MODAL && prm->sym_seed) return -1;
   fegen_ctx* c = (fegen_ctx*)calloc(1, sizeof(fegen_ctx));
   if (!c) return -4;
   c->prm = *prm;
@@ -476,8 +508,13 @@ int fegen_create(const fegen_params* prm, fegen_ctx** out) {
   fg_gauss(c->nq, c->qx, c->qw);
   for (int q = 0; q < c->nq; ++q)
     for (int a = 0; a < n1; ++a) {
-      c->B[q * n1 + a] = fg_lagrange(p, c->xi, a, c->qx[q]);
-      c->D[q * n1 + a] = fg_lagrange_d(p, c->xi, a, c->qx[q]);
+      if (prm->basis == FEGEN_BASIS_MODAL) {
+        c->B[q * n1 + a] = fg_modal(p, a, c->qx[q]);
+        c->D[q * n1 + a] = fg_modal_d(p, a, c->qx[q]);
+      } else {
+        c->B[q * n1 + a] = fg_lagrange(p, c->xi, a, c->qx[q]);
+        c->D[q * n1 + a] = fg_lagrange_d(p, c->xi, a, c->qx[q]);
+      }
     }
 
   /* numbering: structured id s = (I N1y + J) N1z + K, output id = perm[s] */

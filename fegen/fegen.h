@@ -11,6 +11,7 @@
 #define FEGEN_MAXQ 16
 
 enum { FEGEN_MESH_UNIFORM = 0, FEGEN_MESH_JITTER = 1, FEGEN_MESH_GRADED = 2 };
+enum { FEGEN_BASIS_NODAL = 0, FEGEN_BASIS_MODAL = 1 };
 enum { FEGEN_RHS_NONE = 0, FEGEN_RHS_MANUFACTURED = 1, FEGEN_RHS_FOURIER = 2, FEGEN_RHS_ONE = 3 };
 
 typedef struct {
@@ -28,6 +29,11 @@ typedef struct {
   uint64_t rhs_seed;
   uint64_t perm_seed;    /* 0: natural global numbering; else a seeded random relabelling */
   uint64_t sym_seed;     /* 0: structured local order; else a seeded cube symmetry per element */
+  int basis;             /* FEGEN_BASIS_NODAL: Lagrange on the GLL points; FEGEN_BASIS_MODAL: the
+                            hierarchical modes -- 1D local index 0 and p the vertex modes (1 - x)/2
+                            and (1 + x)/2, index a in 1..p-1 the bubble of degree a + 1,
+                            (1 - x)(1 + x)/4 P^(1,1)_(a-1)(x); elements must share one orientation
+                            (no sym_seed), as the odd bubbles change sign under reflection */
 } fegen_params;
 
 typedef struct fegen_ctx fegen_ctx;

@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int),
-                ("strength_theta", ctypes.c_double), ("hash_kind", ctypes.c_int), ("p_schedule", ctypes.c_int)]
+                ("strength_theta", ctypes.c_double), ("hash_kind", ctypes.c_int), ("p_schedule", ctypes.c_int),
+                ("basis", ctypes.c_int)]
 
 
 class _CSR(ctypes.Structure):

@@ -133,6 +133,21 @@ int orc_next_order(int p) {
   return 1;
 }
 
+/* Modal (hierarchical) bases: the order-q modes are the order-p modes of degree <= q, so the
+   paper's prefix extraction (Algorithm 2) keeps them and Algorithm 7 puts a 1 at each: coarse 1D
+   mode b is fine mode b for b < q (vertex mode at -1, bubbles of degree 2..q) and fine mode p for
+   b = q (vertex mode at +1). */
+static int orc_modal_index(int p, int q, int b) { return b == q ? p : b; }
+
+void orc_p1d_basis(int p, int q, int basis, double* tab) {
+  if (basis != 1) {
+    orc_p1d(p, q, tab);
+    return;
+  }
+  for (int a = 0; a <= p; ++a)
+    for (int b = 0; b <= q; ++b) tab[a * (q + 1) + b] = a == orc_modal_index(p, q, b) ? 1.0 : 0.0;
+}
+
 /* The other p schedules (the paper compares coarsening by one and by two, Sec. 3.2). */
 int orc_next_order_sched(int p, int schedule) {
   if (p <= 1) return 1;
@@ -159,10 +174,12 @@ int orc_anchor_index(int p, int q, int s, int* tie) {
 
 /* the fine dof labelling coarse local node (i, j, k): the smallest global id among the
    candidates of the three directions */
-static int32_t orc_coarse_anchor(int p, int q, const int32_t* df_arr, int i, int j, int k) {
+static int32_t orc_coarse_anchor(int p, int q, int basis, const int32_t* df_arr, int i, int j, int k) {
+  const int n1 = p + 1;
+  if (basis == 1)
+    return df_arr[(n1 * n1) * orc_modal_index(p, q, i) + n1 * orc_modal_index(p, q, j) + orc_modal_index(p, q, k)];
   int ti, tj, tk;
   const int ai = orc_anchor_index(p, q, i, &ti), aj = orc_anchor_index(p, q, j, &tj), ak = orc_anchor_index(p, q, k, &tk);
-  const int n1 = p + 1;
   int32_t best = INT32_MAX;
   for (int di = 0; di <= ti; ++di)
     for (int dj = 0; dj <= tj; ++dj)
@@ -288,23 +305,23 @@ int orc_transpose(const orc_csr* A, orc_csr* T) {
 /* Algorithm 2 with nodal labels: the coarse local node (i,j,k), i,j,k <= q, is labelled by the
    fine node of orc_coarse_anchor ((ri, rj, rk) when r = p/q is whole); the labels are copied in
    coarse local order. */
-static void orc_extract_next_dof(int p, int q, const int32_t* df_arr, int32_t* dc_arr) {
+static void orc_extract_next_dof(int p, int q, int basis, const int32_t* df_arr, int32_t* dc_arr) {
   int c = 0;
   for (int i = 0; i <= q; ++i)
     for (int j = 0; j <= q; ++j)
-      for (int k = 0; k <= q; ++k) dc_arr[c++] = orc_coarse_anchor(p, q, df_arr, i, j, k);
+      for (int k = 0; k <= q; ++k) dc_arr[c++] = orc_coarse_anchor(p, q, basis, df_arr, i, j, k);
 }
 
 /* Algorithm 3: collect the retained fine dofs over all elements (skipping those already
    collected), then sort.  Membership is kept in a flag array over the fine dofs. */
-static int32_t* orc_dof_next(int64_t n_f, int32_t n_elem, int p, int q, const int32_t* l2g, int64_t* n_c) {
+static int32_t* orc_dof_next(int64_t n_f, int32_t n_elem, int p, int q, int basis, const int32_t* l2g, int64_t* n_c) {
   int nlf = (p + 1) * (p + 1) * (p + 1), nlc = (q + 1) * (q + 1) * (q + 1);
   uint8_t* in = (uint8_t*)calloc((size_t)n_f, 1);
   int32_t* collect = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_f);
   int32_t* dc = (int32_t*)malloc(sizeof(int32_t) * (size_t)nlc);
   int64_t c = 0;
   for (int32_t e = 0; e < n_elem; ++e) {
-    orc_extract_next_dof(p, q, l2g + (size_t)e * nlf, dc);
+    orc_extract_next_dof(p, q, basis, l2g + (size_t)e * nlf, dc);
     for (int d = 0; d < nlc; ++d) {
       if (in[dc[d]]) continue;
       in[dc[d]] = 1;
@@ -319,7 +336,7 @@ static int32_t* orc_dof_next(int64_t n_f, int32_t n_elem, int p, int q, const in
 
 /* Algorithm 4: l2g_next(e, dof) = hash_l2g(extracted fine dof), hash_l2g the position of a
    fine dof in the sorted collect array. */
-static int32_t* orc_l2g_next(int64_t n_f, int32_t n_elem, int p, int q, const int32_t* l2g,
+static int32_t* orc_l2g_next(int64_t n_f, int32_t n_elem, int p, int q, int basis, const int32_t* l2g,
                              const int32_t* collect, int64_t n_c) {
   int nlf = (p + 1) * (p + 1) * (p + 1), nlc = (q + 1) * (q + 1) * (q + 1);
   int32_t* hash = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_f);
@@ -328,7 +345,7 @@ static int32_t* orc_l2g_next(int64_t n_f, int32_t n_elem, int p, int q, const in
   int32_t* nxt = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_elem * nlc);
   int32_t* dc = (int32_t*)malloc(sizeof(int32_t) * (size_t)nlc);
   for (int32_t e = 0; e < n_elem; ++e) {
-    orc_extract_next_dof(p, q, l2g + (size_t)e * nlf, dc);
+    orc_extract_next_dof(p, q, basis, l2g + (size_t)e * nlf, dc);
     for (int d = 0; d < nlc; ++d) nxt[(size_t)e * nlc + d] = hash[dc[d]];
   }
   free(hash); free(dc);
@@ -342,11 +359,11 @@ typedef struct { int32_t row, col, elem; double val; } orc_coo;
    P1D[a1][b1] * P1D[a2][b2] * P1D[a3][b3] (multiplied left to right); the list is sorted by
    (row, column) and duplicates are removed keeping the first element's entry.  The sort is a
    stable bucket sort by row followed by a stable insertion sort by column inside each row. */
-static int orc_comp_prol(int64_t n_f, int64_t n_c, int32_t n_elem, int p, int q, const int32_t* l2g,
+static int orc_comp_prol(int64_t n_f, int64_t n_c, int32_t n_elem, int p, int q, int basis, const int32_t* l2g,
                          const int32_t* l2g_next, orc_csr* P, double* max_dup_diff) {
   int n1 = p + 1, m1 = q + 1, nlf = n1 * n1 * n1, nlc = m1 * m1 * m1;
   double tab[(ORC_MAXP + 1) * (ORC_MAXP + 1)];
-  orc_p1d(p, q, tab);
+  orc_p1d_basis(p, q, basis, tab);
   /* count entries per row */
   int64_t* cnt = (int64_t*)calloc((size_t)n_f + 1, sizeof(int64_t));
   for (int32_t e = 0; e < n_elem; ++e)
@@ -737,6 +754,7 @@ void orc_default_options(orc_options* o) {
   o->strength_theta = 0.0;
   o->hash_kind = 0;
   o->p_schedule = 0;
+  o->basis = 0;
 }
 
 static int orc_copy_csr(int64_t n, int64_t m, const int64_t* rp, const int32_t* ci, const double* v, orc_csr* A) {
@@ -798,11 +816,11 @@ int orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, 
     orc_level* c = &h->lev[h->nlev];
     int pf = f->order, q = orc_next_order_sched(pf, opt->p_schedule);
     int64_t n_c;
-    int32_t* collect = orc_dof_next(f->A.n, n_elem, pf, q, f->l2g, &n_c);
-    c->l2g = orc_l2g_next(f->A.n, n_elem, pf, q, f->l2g, collect, n_c);
+    int32_t* collect = orc_dof_next(f->A.n, n_elem, pf, q, opt->basis, f->l2g, &n_c);
+    c->l2g = orc_l2g_next(f->A.n, n_elem, pf, q, opt->basis, f->l2g, collect, n_c);
     free(collect);
     double dd = 0.0;
-    rc = orc_comp_prol(f->A.n, n_c, n_elem, pf, q, f->l2g, c->l2g, &f->P, &dd);
+    rc = orc_comp_prol(f->A.n, n_c, n_elem, pf, q, opt->basis, f->l2g, c->l2g, &f->P, &dd);
     if (rc) { orc_free(h); return rc; }
     if (dd > h->max_dup_diff) h->max_dup_diff = dd;
     rc = orc_galerkin(&f->A, &f->P, &f->R, &c->A);

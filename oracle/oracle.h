@@ -47,6 +47,8 @@ typedef struct {
   int hash_kind;         /* 0: SplitMix64-based hash; 1: identity hash h(i) = i */
   int p_schedule;        /* 0: halving (q = p/2, odd p: largest proper divisor), 1: q = p - 1,
                             2: q = p - 2 (at least 1) */
+  int basis;             /* 0: nodal GLL Lagrange basis; 1: modal (hierarchical) basis, local 1D
+                            index 0 and p the vertex modes, 1..p-1 the bubbles of degree 2..p */
 } orc_options;
 
 typedef struct orc_hier orc_hier;
@@ -63,6 +65,9 @@ int orc_next_order_sched(int p, int schedule);
    when s p / q lies half way (both neighbours then label it, see orc_coarse_anchor) */
 int orc_anchor_index(int p, int q, int s, int* tie);
 void orc_p1d(int p, int q, double* tab /* [(p+1)][(q+1)] */);
+/* the 1D prolongation table of a basis: orc_p1d for the nodal basis; for the modal basis the
+   injection P1D[a][b] = 1 when fine mode a is coarse mode b (a = b for b < q, a = p for b = q) */
+void orc_p1d_basis(int p, int q, int basis, double* tab);
 int orc_spgemm(const orc_csr* A, const orc_csr* B, orc_csr* C);
 int orc_transpose(const orc_csr* A, orc_csr* T);
 void orc_csr_free(orc_csr* A);

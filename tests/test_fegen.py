@@ -131,3 +131,42 @@ def test_nodal_fourier_rhs():
         ref = sum(c[a, b, d] * np.sin((a + 1) * np.pi * x) * np.sin((b + 1) * np.pi * y) * np.sin((d + 1) * np.pi * z)
                   for a in range(4) for b in range(4) for d in range(4))
         assert abs(f[i] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6])
+def test_modal_basis_spans_the_nodal_space(p):
+    """The hierarchical modes span the same space Q_p as the GLL Lagrange basis, so the Galerkin
+    solutions are the same function: the energy x^T b = integral of f u_h and the L2 error of the
+    manufactured solution agree between the two discretisations."""
+    a = fegen.make(3, p, mesh="jitter", lam=1.0)
+    b = fegen.make(3, p, mesh="jitter", lam=1.0, basis="modal")
+    xa = sla.spsolve(a.scipy().tocsc(), a.b)
+    xb = sla.spsolve(b.scipy().tocsc(), b.b)
+    assert abs(xa @ a.b - xb @ b.b) <= 1e-12 * abs(xa @ a.b)
+    assert abs(a.l2_error(xa) - b.l2_error(xb)) <= 1e-9 * a.l2_error(xa)
+    assert (a.n, a.nnz) == (b.n, b.nnz)
+
+
+@pytest.mark.parametrize("p,q", [(4, 2), (5, 4), (6, 3), (3, 1)])
+def test_modal_operator_is_hierarchical(p, q):
+    """The order-q modal operator is the principal submatrix of the order-p one on the modes of
+    degree <= q (same quadrature rule): per direction, coarse lattice index e q + i is fine index
+    e p + i for i < q and e p + p for i = q."""
+    n = 2
+    fine = fegen.make(n, p, mesh="jitter", lam=1.0, kappa=1, dirichlet=False, rhs="none", basis="modal")
+    coarse = fegen.make(n, q, mesh="jitter", lam=1.0, kappa=1, nq=p + 2, dirichlet=False, rhs="none", basis="modal")
+    Nc, Nf = n * q + 1, n * p + 1
+    ic = np.arange(Nc)
+    # lattice index e q + i (0 <= i < q) of coarse element e, and the last vertex at n q
+    e, i = np.minimum(ic // q, n - 1), ic - np.minimum(ic // q, n - 1) * q
+    fmap = e * p + np.where(i == q, p, i)
+    I, J, K = np.meshgrid(fmap, fmap, fmap, indexing="ij")
+    kept = ((I * Nf + J) * Nf + K).ravel()
+    Kf = fine.scipy().tocsr()[kept][:, kept].toarray()
+    Kc = coarse.scipy().toarray()
+    assert np.max(np.abs(Kf - Kc)) <= 1e-12 * np.max(np.abs(Kc))
+
+
+def test_modal_basis_rejects_element_symmetries():
+    with pytest.raises(RuntimeError):
+        fegen.make(2, 3, basis="modal", sym_seed=5)

@@ -609,3 +609,58 @@ def test_pcg_other_schedules_match_dense_direct_solve(schedule):
     assert st == "ok"
     xd = np.linalg.solve(prob.scipy().toarray(), prob.b)
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+# ----------------------------------------------------------------------------- modal basis
+def _modal_kept(n, p, q):
+    """Fine structured ids of the order-q modes: per direction, coarse lattice index e q + i is
+    fine index e p + i for i < q, and e p + p for i = q."""
+    ic = np.arange(n * q + 1)
+    e = np.minimum(ic // q, n - 1)
+    i = ic - e * q
+    fmap = e * p + np.where(i == q, p, i)
+    Nf = n * p + 1
+    I, J, K = np.meshgrid(fmap, fmap, fmap, indexing="ij")
+    return ((I * Nf + J) * Nf + K).ravel()
+
+
+@pytest.mark.parametrize("p,schedule", [(4, 0), (6, 0), (5, 1), (7, 2), (3, 0)])
+def test_modal_injection_rap_is_the_principal_submatrix(p, schedule):
+    """Modal basis (the paper's setting): Algorithm 2 keeps the prefix of modes of degree <= q,
+    Algorithm 7 puts a 1 at each kept mode, so P is a 0/1 selection and R A P is exactly the
+    fine operator restricted to the kept modes, which is also the order-q modal operator
+    assembled directly with the fine rule."""
+    n = 2
+    fine = fegen.make(n, p, mesh="jitter", lam=10.0, kappa=1, dirichlet=False, rhs="none", basis="modal")
+    H = oracle.Hierarchy.from_problem(fine, basis=1, p_schedule=schedule, coarse_max=1, max_levels=3)
+    q = H.level_info(1)["order"]
+    assert q == oracle.next_order(p, schedule)
+    rp, ci, v, m = H.prolongation(0)
+    P = sp.csr_matrix((v, ci, rp), shape=(fine.n, m))
+    assert np.all(v == 1.0) and np.all(np.diff(rp) <= 1) and P.nnz == m
+    kept = _modal_kept(n, p, q)
+    assert np.array_equal(np.sort(P.nonzero()[0]), np.sort(kept))
+    rp, ci, v, _ = H.level(1)
+    Ac = sp.csr_matrix((v, ci, rp), shape=(m, m)).toarray()
+    sub = fine.scipy().tocsr()[kept][:, kept].toarray()
+    assert np.array_equal(Ac, sub)  # injection: every entry is one fine entry, no rounding
+    direct = fegen.make(n, q, mesh="jitter", lam=10.0, kappa=1, nq=p + 2, dirichlet=False, rhs="none", basis="modal")
+    Ad = direct.scipy().toarray()
+    assert np.max(np.abs(Ac - Ad)) <= 1e-12 * np.max(np.abs(Ad))
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_modal_pcg_matches_dense_solve_and_nodal_energy(p):
+    modal = fegen.make(2, p, mesh="jitter", lam=1.0, basis="modal")
+    nodal = fegen.make(2, p, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(modal, basis=1)
+    x, it, rr, _, st = H.solve(modal.b, rtol=1e-11)
+    assert st == "ok"
+    A = modal.scipy().toarray()
+    assert np.linalg.norm(modal.b - A @ x) <= 1e-10 * np.linalg.norm(modal.b)
+    # the modal matrix is worse conditioned than the nodal one: the error is bounded by
+    # cond(A) times the residual
+    xd = np.linalg.solve(A, modal.b)
+    assert np.linalg.norm(x - xd) <= np.linalg.cond(A) * 1e-10 * np.linalg.norm(xd)
+    xn = np.linalg.solve(nodal.scipy().toarray(), nodal.b)
+    assert abs(x @ modal.b - xn @ nodal.b) <= 1e-10 * abs(xn @ nodal.b)
