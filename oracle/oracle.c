@@ -567,7 +567,9 @@ static void orc_strength(const orc_csr* A, double theta, int64_t** grp, int32_t*
 }
 
 /* Smoothed aggregation prolongation P = T - M A T, T[i, agg(i)] = 1, M = diag(a_ii / sum_j a_ij^2)
-   (SPAI-0).  Pattern: that of A T united with that of T; no dropping. */
+   (SPAI-0).  Pattern: that of A T united with that of T; no dropping.  A row without off-diagonal
+   entries (a Dirichlet identity row: an isolated node, its own aggregate) is not smoothed, M_ii =
+   0: SPAI-0 would give it M_ii = 1/a_ii and so an all-zero column of P. */
 static int orc_sa_prolongation(const orc_csr* A, const int32_t* agg, int64_t n_agg, orc_csr* P) {
   int64_t n = A->n;
   orc_csr T = {n, n_agg, NULL, NULL, NULL};
@@ -592,11 +594,13 @@ static int orc_sa_prolongation(const orc_csr* A, const int32_t* agg, int64_t n_a
   P->v = (double*)malloc(sizeof(double) * (size_t)(P->rp[n] > 0 ? P->rp[n] : 1));
   for (int64_t i = 0; i < n; ++i) {
     double diag = 0.0, ss = 0.0;
+    int coupled = 0;
     for (int64_t t = A->rp[i]; t < A->rp[i + 1]; ++t) {
       ss = ss + A->v[t] * A->v[t];
       if (A->ci[t] == i) diag = A->v[t];
+      else coupled = 1;
     }
-    double mi = diag / ss;
+    double mi = coupled ? diag / ss : 0.0;
     int inserted = 0;
     for (int64_t t = AT.rp[i]; t < AT.rp[i + 1]; ++t) inserted |= AT.ci[t] == agg[i];
     int64_t d = P->rp[i];

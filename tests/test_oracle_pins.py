@@ -664,3 +664,29 @@ def test_modal_pcg_matches_dense_solve_and_nodal_energy(p):
     assert np.linalg.norm(x - xd) <= np.linalg.cond(A) * 1e-10 * np.linalg.norm(xd)
     xn = np.linalg.solve(nodal.scipy().toarray(), nodal.b)
     assert abs(x @ modal.b - xn @ nodal.b) <= 1e-10 * abs(xn @ nodal.b)
+
+
+def test_sa_prolongation_keeps_isolated_rows():
+    """A row with no off-diagonal entry (a Dirichlet identity row, its own aggregate) keeps its
+    tentative column: SPAI-0's m_i = 1 / a_ii would make it exactly zero and the coarse operator
+    singular."""
+    A = sp.csr_matrix(np.array([[1.0, 0, 0, 0], [0, 2.0, -1.0, 0], [0, -1.0, 2.0, -1.0], [0, 0, -1.0, 2.0]]))
+    agg = np.array([0, 1, 1, 1], np.int32)
+    rp, ci, v, _ = oracle.sa_prolongation(A.indptr, A.indices, A.data, agg, 2)
+    P = sp.csr_matrix((v, ci, rp), shape=(4, 2)).toarray()
+    assert P[0, 0] == 1.0 and P[0, 1] == 0.0
+    Ac = P.T @ A.toarray() @ P
+    assert np.all(np.linalg.eigvalsh(Ac) > 0)
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_order_one_input_with_dirichlet_rows(n):
+    """An order-1 system goes straight to aggregation with its Dirichlet identity rows isolated;
+    the hierarchy stays definite and PCG matches the direct solve."""
+    prob = fegen.make(n, 1, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    assert H.level_info(0)["kind"] == oracle.KIND_H
+    x, it, rr, _, st = H.solve(prob.b, rtol=1e-10)
+    assert st == "ok"
+    xd = sla.spsolve(prob.scipy().tocsc(), prob.b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
