@@ -532,8 +532,9 @@ def measure_serving_full(n_requests=512, load=0.8):
 
 def measure_schedules(steps=10, warmup=3):
     """The p schedules compared (the paper compares coarsening by one and by two): halving, by one
-    and by two on the 16^3 p = 6 benchmark operator and on a 16^3 p = 5 one; levels, iterations,
-    solve time (FP32 V-cycle in FP64 FCG and FP64 PCG, CUDA-event medians) and setup time."""
+    and by two on the 16^3 p = 6 benchmark operator, on a 16^3 p = 5 one, and on the benchmark
+    operator in the modal basis (injection P); levels, iterations, solve time (FP32 V-cycle in
+    FP64 FCG and FP64 PCG, CUDA-event medians) and setup time."""
     import statistics
     import torch
     import fegen
@@ -541,15 +542,18 @@ def measure_schedules(steps=10, warmup=3):
     out = {}
     for name, cfg, k in (("helmholtz_16cube_jitter_p6", fegen.WORKLOADS["helmholtz_16cube_jitter_p6"], 3),
                          ("helmholtz_16cube_jitter_p5", dict(n=16, p=5, mesh="jitter", mesh_seed=1, lam=10.0,
-                                                             rhs="manufactured"), 3)):
+                                                             rhs="manufactured"), 3),
+                         ("helmholtz_16cube_jitter_p6_modal", dict(fegen.WORKLOADS["helmholtz_16cube_jitter_p6"],
+                                                                   basis="modal"), 3)):
         cfg = {key: v for key, v in cfg.items() if key != "k"}
+        basis = 1 if cfg.get("basis") == "modal" else 0
         prob = fegen.make(**cfg)
         b = torch.from_numpy(prob.b).cuda()
         res = {}
         for sched, label in ((0, "halving"), (1, "by_one"), (2, "by_two")):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            S = g.Solver.from_problem(prob, device=True, cheb_degree=k, p_schedule=sched)
+            S = g.Solver.from_problem(prob, device=True, cheb_degree=k, p_schedule=sched, basis=basis)
             torch.cuda.synchronize()
             setup_ms = (time.perf_counter() - t0) * 1e3
             row = {"levels": [[S.level_info(l)["n"], S.level_info(l)["order"]] for l in range(S.num_levels)],

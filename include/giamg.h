@@ -105,6 +105,13 @@ typedef struct {
                              its largest proper divisor); 1 by one, q = p - 1; 2 by two,
                              q = p - 2 (at least 1).  When p/q is not whole, coarse nodes are
                              numbered by their nearest fine nodes (ties: the smaller global id) */
+  int basis;              /* element basis of A and elem_dof: 0 (default) nodal, Lagrange on the
+                             GLL points (interpolation between orders, Algorithm 7's nodal form);
+                             1 modal hierarchical, local 1D index 0 and p the vertex modes,
+                             1..p-1 the bubble modes of degree 2..p (the paper's setting: the
+                             coarse space keeps the modes of degree <= q, Algorithm 2's prefix,
+                             and P is the injection, Algorithm 7 with values 1).  Elements must
+                             share one orientation; coords must be NULL */
 } giamg_options;
 
 /* Fill *opt with the defaults listed above. */

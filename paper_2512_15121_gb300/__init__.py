@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
                 ("force_iters", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("hash_kind", ctypes.c_int),
                 ("compress_patterns", ctypes.c_int), ("autotune", ctypes.c_int), ("row_form", ctypes.c_int),
                 ("row_threads", ctypes.c_int), ("prefetch_rows", ctypes.c_int), ("row_chains", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("p_schedule", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("p_schedule", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 _lib = None

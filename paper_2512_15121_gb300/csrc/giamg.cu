@@ -362,6 +362,9 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   GIAMG_CHECK(opt.prefetch_rows >= -1, GIAMG_ERR_ARG, "prefetch_rows must be -1, 0 or positive");
   GIAMG_CHECK(opt.graphs >= 0 && opt.graphs <= 2, GIAMG_ERR_ARG, "graphs must be 0, 1 or 2");
   GIAMG_CHECK(opt.p_schedule >= 0 && opt.p_schedule <= 2, GIAMG_ERR_ARG, "p_schedule must be 0, 1 or 2");
+  GIAMG_CHECK(opt.basis == 0 || opt.basis == 1, GIAMG_ERR_ARG, "basis must be 0 (nodal) or 1 (modal)");
+  GIAMG_CHECK(!(coords && opt.basis == 1), GIAMG_ERR_ARG,
+              "coordinates validate nodal elements only; pass NULL with the modal basis");
   GIAMG_CHECK(opt.row_chains == 0 || opt.row_chains == 2 || opt.row_chains == 4 || opt.row_chains == 8, GIAMG_ERR_ARG,
               "row_chains must be 0, 2, 4 or 8");
   const bool dev = opt.device_ptrs != 0;
@@ -444,7 +447,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       F.p = F.order;
       F.q = next_order(F.order, opt.p_schedule);
       F.n_elem = n_elem;
-      p_level_build(F, *Cl, s);
+      p_level_build(F, *Cl, opt.basis, s);
       clk.mark("p-level map and P", (int)H.lev.size() - 1);
       Cl->order = F.q;
       galerkin(F, Cl->A, false, s);
@@ -1114,6 +1117,7 @@ void giamg_default_options(giamg_options* o) {
   o->prefetch_rows = -1;
   o->graphs = 1;
   o->p_schedule = 0;
+  o->basis = 0;
   o->row_chains = 0;
 }
 

@@ -391,7 +391,8 @@ bool diag_inverse(const DCSR& A, double* dinv, float* dinv32, cudaStream_t s);
 // Lanczos estimate of lambda_max(D^-1/2 A D^-1/2)
 double lanczos_rho(const DCSR& A, int steps, int hash_kind, Hierarchy& H);
 // p-level construction: next map, owners, assembled P
-void p_level_build(Level& F, Level& C, cudaStream_t s);
+// modal: hierarchical basis (prefix of modes, injection P); else nodal GLL (interpolation P)
+void p_level_build(Level& F, Level& C, int modal, cudaStream_t s);
 // h-level construction: MIS-2, aggregates, smoothed prolongation
 int64_t h_level_aggregate(Level& F, double theta, int hash_kind, cudaStream_t s);
 void h_level_prolongation(Level& F, cudaStream_t s);

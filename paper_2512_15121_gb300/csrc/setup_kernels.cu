@@ -457,8 +457,14 @@ __device__ __forceinline__ int anchor_axis(int p, int q, int s, int& ties) {
   ties = (rem != 0 && 2 * rem == q) ? 1 : 0;
   return (rem != 0 && 2 * rem > q) ? f + 1 : f;
 }
-__device__ __forceinline__ int32_t coarse_anchor(const int32_t* __restrict__ le, int p, int q, int i, int j, int k) {
+// Modal (hierarchical) basis: the order-q modes are the order-p modes of degree <= q (Algorithm 2's
+// prefix): coarse 1D mode s is fine mode s for s < q and the vertex mode p for s = q.
+__device__ __forceinline__ int modal_axis(int p, int q, int s) { return s == q ? p : s; }
+
+__device__ __forceinline__ int32_t coarse_anchor(const int32_t* __restrict__ le, int p, int q, int modal, int i, int j,
+                                                 int k) {
   const int n1 = p + 1;
+  if (modal) return le[(n1 * n1) * modal_axis(p, q, i) + n1 * modal_axis(p, q, j) + modal_axis(p, q, k)];
   int ti, tj, tk;
   const int ai = anchor_axis(p, q, i, ti), aj = anchor_axis(p, q, j, tj), ak = anchor_axis(p, q, k, tk);
   int32_t best = le[(n1 * n1) * ai + n1 * aj + ak];
@@ -467,25 +473,26 @@ __device__ __forceinline__ int32_t coarse_anchor(const int32_t* __restrict__ le,
       for (int dk = 0; dk <= tk; ++dk) best = min(best, le[(n1 * n1) * (ai + di) + n1 * (aj + dj) + (ak + dk)]);
   return best;
 }
-__global__ void mark_anchors(int32_t n_elem, int p, int q, const int32_t* __restrict__ l2g, int32_t* __restrict__ flag) {
+__global__ void mark_anchors(int32_t n_elem, int p, int q, int modal, const int32_t* __restrict__ l2g,
+                             int32_t* __restrict__ flag) {
   const int n1 = p + 1, m1 = q + 1;
   const int64_t nlc = (int64_t)m1 * m1 * m1, nlf = (int64_t)n1 * n1 * n1;
   GRID_STRIDE(t, (int64_t)n_elem * nlc) {
     const int64_t e = t / nlc;
     const int b = (int)(t % nlc);
     const int i = b / (m1 * m1), j = (b / m1) % m1, k = b % m1;
-    flag[coarse_anchor(l2g + e * nlf, p, q, i, j, k)] = 1;
+    flag[coarse_anchor(l2g + e * nlf, p, q, modal, i, j, k)] = 1;
   }
 }
-__global__ void coarse_map(int32_t n_elem, int p, int q, const int32_t* __restrict__ l2g, const int64_t* __restrict__ rank,
-                           int32_t* __restrict__ l2g_c) {
+__global__ void coarse_map(int32_t n_elem, int p, int q, int modal, const int32_t* __restrict__ l2g,
+                           const int64_t* __restrict__ rank, int32_t* __restrict__ l2g_c) {
   const int n1 = p + 1, m1 = q + 1;
   const int64_t nlc = (int64_t)m1 * m1 * m1, nlf = (int64_t)n1 * n1 * n1;
   GRID_STRIDE(t, (int64_t)n_elem * nlc) {
     const int64_t e = t / nlc;
     const int b = (int)(t % nlc);
     const int i = b / (m1 * m1), j = (b / m1) % m1, k = b % m1;
-    l2g_c[t] = (int32_t)rank[coarse_anchor(l2g + e * nlf, p, q, i, j, k)];
+    l2g_c[t] = (int32_t)rank[coarse_anchor(l2g + e * nlf, p, q, modal, i, j, k)];
   }
 }
 __global__ void owner_min(int64_t slots, int nlf, const int32_t* __restrict__ l2g, int32_t* __restrict__ owner) {
@@ -666,18 +673,22 @@ __global__ void tentative(int64_t n, const int32_t* __restrict__ agg, int64_t* _
     }
   }
 }
-// P = T - M (A T), M = diag(a_ii / sum_j a_ij^2), on the pattern of A T (which contains T)
+// P = T - M (A T), M = diag(a_ii / sum_j a_ij^2), on the pattern of A T (which contains T).  Rows
+// with no off-diagonal entry (Dirichlet identity rows, isolated nodes forming their own
+// aggregates) keep T: M_ii = 0, since SPAI-0's 1/a_ii would zero their column of P.
 __global__ void sa_smooth(int64_t n, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
                           const double* __restrict__ av, const int32_t* __restrict__ agg,
                           const int64_t* __restrict__ crp, const int32_t* __restrict__ cci, double* __restrict__ cv,
                           int32_t* __restrict__ bad) {
   GRID_STRIDE(i, n) {
     double diag = 0.0, ss = 0.0;
+    bool coupled = false;
     for (int64_t t = arp[i]; t < arp[i + 1]; ++t) {
       ss = __dadd_rn(ss, __dmul_rn(av[t], av[t]));
       if (aci[t] == i) diag = av[t];
+      else coupled = true;
     }
-    const double mi = diag / ss;
+    const double mi = coupled ? diag / ss : 0.0;
     int found = 0;
     for (int64_t t = crp[i]; t < crp[i + 1]; ++t) {
       const bool own = cci[t] == agg[i];
@@ -998,7 +1009,7 @@ static void gll(int p, double* x) {
   if (p % 2 == 0) x[p / 2] = 0.0;
 }
 
-void p_level_build(Level& F, Level& C, cudaStream_t s) {
+void p_level_build(Level& F, Level& C, int modal, cudaStream_t s) {
   const int p = F.p, q = F.q;
   const int n1 = p + 1, m1 = q + 1, nlf = n1 * n1 * n1, nlc = m1 * m1 * m1;
   const int64_t nf = F.A.n;
@@ -1009,7 +1020,7 @@ void p_level_build(Level& F, Level& C, cudaStream_t s) {
   flag.alloc(nf, s);
   flag.zero(s);
   rank.alloc(nf + 1, s);
-  { mark_anchors<<<blocks_for(slots_c, 256, 65535), 256, 0, s>>>(F.n_elem, p, q, F.l2g.get(), flag.get()); note_launch(); }
+  { mark_anchors<<<blocks_for(slots_c, 256, 65535), 256, 0, s>>>(F.n_elem, p, q, modal, F.l2g.get(), flag.get()); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
   scan_i32_to_i64(flag.get(), rank.get(), nf, s);
   int64_t nc = 0;
@@ -1017,7 +1028,7 @@ void p_level_build(Level& F, Level& C, cudaStream_t s) {
   GIAMG_CUDA(cudaStreamSynchronize(s));
   F.n_next = nc;
   F.l2g_c.alloc(slots_c, s);
-  { coarse_map<<<blocks_for(slots_c, 256, 65535), 256, 0, s>>>(F.n_elem, p, q, F.l2g.get(), rank.get(), F.l2g_c.get()); note_launch(); }
+  { coarse_map<<<blocks_for(slots_c, 256, 65535), 256, 0, s>>>(F.n_elem, p, q, modal, F.l2g.get(), rank.get(), F.l2g_c.get()); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
   // the coarse level's element map is the same array
   C.l2g.alloc(slots_c, s);
@@ -1041,8 +1052,11 @@ void p_level_build(Level& F, Level& C, cudaStream_t s) {
     int nz = 0;
     for (int b = 0; b <= q; ++b) {
       double v = 1.0;
-      for (int mm = 0; mm <= q; ++mm)
-        if (mm != b) v = v * ((xp[a] - xq[mm]) / (xq[b] - xq[mm]));
+      if (modal)  // injection (Algorithm 7 with values 1): fine mode a is coarse mode b
+        v = a == (b == q ? p : b) ? 1.0 : 0.0;
+      else
+        for (int mm = 0; mm <= q; ++mm)
+          if (mm != b) v = v * ((xp[a] - xq[mm]) / (xq[b] - xq[mm]));
       tab.t[a * m1 + b] = v;
       t32[a * m1 + b] = (float)v;
       nz += v != 0.0;

@@ -34,6 +34,12 @@ CASES = {
     # non-halving p schedules: coarse nodes labelled by their nearest fine nodes
     "jitter4_p5_by_one": dict(n=4, p=5, mesh="jitter", lam=1.0, perm_seed=5, sym_seed=6, k=3, opts=dict(p_schedule=1)),
     "jitter3_p7_by_two": dict(n=3, p=7, mesh="jitter", lam=10.0, k=2, opts=dict(p_schedule=2)),
+    # an order-1 input: aggregation levels only, Dirichlet identity rows isolated
+    "jitter10_p1": dict(n=10, p=1, mesh="jitter", lam=1.0, k=2),
+    # the modal (hierarchical) basis: prefix of modes, injection P
+    "jitter4_p4_modal": dict(n=4, p=4, mesh="jitter", lam=1.0, basis="modal", k=3, opts=dict(basis=1)),
+    "jitter334_p5_modal_by_one": dict(n=(3, 3, 4), p=5, mesh="jitter", lam=1.0, basis="modal", k=3,
+                                      opts=dict(basis=1, p_schedule=1)),
 }
 
 _cache = {}
