@@ -1,4 +1,5 @@
-"""CPU oracle of GIAMG-preconditioned CG: plain FP64 C (oracle.c) behind ctypes.
+"""CPU oracle of GIAMG-preconditioned CG: plain FP64 C (oracle.c) behind ctypes, and block PCG
+for several right-hand sides in numpy (block_cg.py).
 
 TEST INFRASTRUCTURE ONLY.  Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
 `bench.py` may import this package.  The CUDA library (`paper_2512_15121_gb300`) never imports
@@ -365,3 +366,16 @@ class Hierarchy:
         rc = _lib().orc_solve(self._h, _p(b), _p(x), rtol, max_iter, force_iters, precision, flexible,
                               ctypes.byref(it), ctypes.byref(rr), _p(hist))
         return x, it.value, rr.value, hist[:it.value + 1], STATUS.get(rc, rc)
+
+    def solve_block(self, B, rtol=1e-8, max_iter=1000, force_iters=0, precision=0):
+        """Block PCG (oracle/block_cg.py) on the n x m block B with this hierarchy's V-cycle as M.
+        Returns (X, iters, relres per column, status, kept directions per iteration)."""
+        from .block_cg import block_pcg
+
+        def apply_A(P):
+            return np.stack([self.spmv(0, P[:, j]) for j in range(P.shape[1])], axis=1)
+
+        def apply_M(R):
+            return np.stack([self.vcycle(R[:, j], precision) for j in range(R.shape[1])], axis=1)
+
+        return block_pcg(apply_A, apply_M, B, rtol=rtol, max_iter=max_iter, force_iters=force_iters)

@@ -14,6 +14,9 @@
   V-cycle (Alg. 1) symmetric as an operator
   PCG              dense direct solve; Dirichlet entries converge to zero; fewer iterations
                    than Jacobi-preconditioned CG; thread-count independence
+  block PCG        m = 1 is the scalar PCG; finite termination; the brute-force energy
+                   projection onto the block Krylov space; dependent and zero columns; energy
+                   error never above each column's own PCG; the Gram pseudo-inverse
 """
 import itertools
 
@@ -690,3 +693,119 @@ def test_order_one_input_with_dirichlet_rows(n):
     assert st == "ok"
     xd = sla.spsolve(prob.scipy().tocsc(), prob.b)
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+# ----------------------------------------------------------------------------- block PCG
+# oracle/block_cg.py: O'Leary's block CG with A-conjugate directions and dependent directions
+# dropped.  Pins: m = 1 is the scalar PCG; finite termination after n/m steps; the iterate is
+# the energy-norm projection onto the block Krylov space (brute force); dependent columns;
+# never a larger energy error than the columns' own PCG; the Gram pseudo-inverse.
+from oracle.block_cg import block_pcg, gram_factor, gram_solve  # noqa: E402
+
+
+def _spd(n, cond, rng):
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (Qm * np.geomspace(1.0, cond, n)) @ Qm.T
+
+
+def test_gram_pseudo_inverse_full_rank_and_singular():
+    rng = np.random.default_rng(5)
+    G = _spd(12, 1e4, rng)
+    Y = rng.standard_normal((12, 5))
+    F = gram_factor(G)
+    assert F[1].all()
+    assert np.allclose(gram_solve(F, Y), np.linalg.solve(G, Y), rtol=0, atol=1e-10 * np.abs(np.linalg.solve(G, Y)).max())
+    # rank 4 of 9, with a zero direction: 5 dropped, and G x = y on the range of G
+    V = rng.standard_normal((9, 4))
+    V = np.insert(V, 2, 0.0, axis=0)[:9]
+    G = V @ V.T
+    F = gram_factor(G)
+    assert F[1].sum() == np.linalg.matrix_rank(G) and not F[1][2]
+    y = G @ rng.standard_normal((9, 3))
+    assert np.linalg.norm(G @ gram_solve(F, y) - y) <= 1e-10 * np.linalg.norm(y)
+
+
+def test_block_pcg_one_column_is_the_scalar_pcg():
+    prob = fegen.make(4, 4, mesh="jitter", lam=0.0, rhs="fourier", rhs_seed=1001)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=2)
+    b = prob.b
+    for precision, tol in ((0, 1e-12), (1, 1e-9)):
+        x, it, rr, _, st = H.solve(b, rtol=1e-8, precision=precision)
+        X, itb, rrb, stb, ranks = H.solve_block(b[:, None], rtol=1e-8, precision=precision)
+        assert st == stb == "ok" and itb == it and ranks == [1] * it
+        assert np.linalg.norm(X[:, 0] - x) <= tol * np.linalg.norm(x)
+        assert abs(rrb[0] - rr) <= 1e-6 * rr
+    x = H.solve(b, force_iters=3)[0]
+    X = H.solve_block(b[:, None], force_iters=3)[0]
+    assert np.linalg.norm(X[:, 0] - x) <= 1e-12 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("m", [3, 4, 6])
+def test_block_pcg_finite_termination(m):
+    # the block Krylov space has dimension m k, so n = 24 unknowns are exhausted after 24 / m steps
+    rng = np.random.default_rng(m)
+    n = 24
+    A = _spd(n, 50.0, rng)
+    dinv = 1.0 / np.diag(A)
+    B = rng.standard_normal((n, m))
+    X, it, rr, st, ranks = block_pcg(lambda P: A @ P, lambda R: dinv[:, None] * R, B, force_iters=n // m)
+    assert st == "ok" and it == n // m and ranks == [m] * it
+    assert np.all(rr <= 1e-9)
+    Xd = np.linalg.solve(A, B)
+    assert np.linalg.norm(X - Xd) <= 1e-9 * np.linalg.norm(Xd)
+
+
+def test_block_pcg_is_the_energy_projection_onto_the_block_krylov_space():
+    rng = np.random.default_rng(11)
+    n, m = 40, 3
+    A = _spd(n, 1e3, rng)
+    C = rng.standard_normal((n, n))
+    M = C @ C.T / n + np.eye(n)  # a fixed SPD preconditioner
+    B = rng.standard_normal((n, m))
+    Z0 = M @ B
+    for k in range(1, 5):
+        Xk = block_pcg(lambda P: A @ P, lambda R: M @ R, B, force_iters=k)[0]
+        # span{Z0, (MA) Z0, ..., (MA)^(k-1) Z0}, orthonormalised; X = K (K^T A K)^-1 K^T B
+        blocks, W = [], Z0
+        for _ in range(k):
+            blocks.append(W)
+            W = M @ (A @ W)
+        K, _ = np.linalg.qr(np.hstack(blocks))
+        Xs = K @ np.linalg.solve(K.T @ A @ K, K.T @ B)
+        assert np.linalg.norm(Xk - Xs) <= 1e-9 * np.linalg.norm(Xs), k
+
+
+def test_block_pcg_dependent_and_zero_columns():
+    prob = fegen.make(4, 4, mesh="jitter", lam=0.0)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=2)
+    b0, b1, b2 = (prob.rhs("fourier", s) for s in (7, 8, 9))
+    B = np.stack([b0, b1, b0, np.zeros_like(b0), b0 + 2.0 * b1, b2], axis=1)
+    X, it, rr, st, ranks = H.solve_block(B, rtol=1e-8)
+    assert st == "ok" and np.all(rr <= 1e-8) and max(ranks) == 3
+    X3, it3, _, _, _ = H.solve_block(B[:, [0, 1, 5]], rtol=1e-8)
+    assert it == it3
+    scale = np.linalg.norm(X3)
+    assert np.linalg.norm(X[:, [0, 1, 5]] - X3) <= 1e-10 * scale
+    assert np.linalg.norm(X[:, 2] - X[:, 0]) <= 1e-10 * scale
+    assert np.all(X[:, 3] == 0.0) and rr[3] == 0.0
+    assert np.linalg.norm(X[:, 4] - X[:, 0] - 2.0 * X[:, 1]) <= 1e-10 * scale
+    # all columns zero: nothing to do
+    Xz, itz, rrz, stz, _ = H.solve_block(np.zeros((prob.n, 2)))
+    assert itz == 0 and stz == "ok" and np.all(Xz == 0.0)
+
+
+def test_block_pcg_energy_error_never_above_the_columns_own_pcg():
+    # the block space contains each column's own Krylov space (fixed symmetric V-cycle)
+    prob = fegen.make(4, 4, mesh="jitter", lam=0.0)
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=2)
+    A = prob.scipy().tocsc()
+    B = np.stack([prob.rhs("fourier", 20 + j) for j in range(8)], axis=1)
+    Xd = np.stack([sla.spsolve(A, B[:, j]) for j in range(8)], axis=1)
+
+    def energy(E):
+        return np.sqrt(np.einsum("ij,ij->j", E, A @ E))
+
+    for k in range(1, 7):
+        eb = energy(H.solve_block(B, force_iters=k)[0] - Xd)
+        es = energy(np.stack([H.solve(B[:, j], force_iters=k)[0] for j in range(8)], axis=1) - Xd)
+        assert np.all(eb <= es * (1 + 1e-8) + 1e-12 * energy(Xd)), k
