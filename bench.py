@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the multi-RHS and serving measurements")
     ap.add_argument("--schedules", action="store_true",
                     help="compare the p schedules (halving, by one, by two) on two 16^3 operators and print them")
+    ap.add_argument("--block", action="store_true",
+                    help="compare block CG with independent columns (32 RHS) on the Poisson workload and the modal operator")
     ap.add_argument("--serving-full", action="store_true",
                     help="run only the 512-request serving stream (36 operators up to 12^3, p = 8) and print it")
     ap.add_argument("--summarize-launches", metavar="CSV",
@@ -438,7 +440,8 @@ def run_ours(args):
 
 def measure_batch(g, torch, m=32, reps=5):
     """32 right-hand sides of the 24^3 Poisson workload as one multi-RHS solve (FP32 V-cycle in
-    flexible CG), against one single-RHS solve of the first column."""
+    flexible CG), against one single-RHS solve of the first column, and as one block in block
+    CG."""
     import numpy as np
     import fegen
     name = "poisson_24cube_jitter_p4"
@@ -450,8 +453,10 @@ def measure_batch(g, torch, m=32, reps=5):
     for _ in range(2):
         S.solve_batch(Bd, rtol=1e-8, precision=1)
         S.solve(b0, rtol=1e-8, precision=1)
+    for _ in range(2):
+        S.solve_batch(Bd, rtol=1e-8, precision=1, block=True)
     st = torch.cuda.current_stream()
-    tb, ts = [], []
+    tb, ts, tk = [], [], []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
@@ -464,12 +469,18 @@ def measure_batch(g, torch, m=32, reps=5):
         e1.record(st)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
+        e0.record(st)
+        _, itk, rrk = S.solve_batch(Bd, rtol=1e-8, precision=1, block=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        tk.append(e0.elapsed_time(e1))
     S.close()
-    pb, ps = pct(tb, 0.5), pct(ts, 0.5)
+    pb, ps, pk = pct(tb, 0.5), pct(ts, 0.5), pct(tk, 0.5)
     return {"workload": name, "dofs": prob.n, "nnz": prob.nnz, "m": m, "p50_ms": round(pb, 3),
             "per_solve_ms": round(pb / m, 3), "single_rhs_p50_ms": round(ps, 3),
             "throughput_vs_single": round(ps * m / pb, 2), "iters": [int(it.min()), int(it.max())],
-            "max_relres": float(rr.max()), "dtype": "f32 V-cycle in f64 FCG"}
+            "max_relres": float(rr.max()), "dtype": "f32 V-cycle in f64 FCG",
+            "block_cg": {"p50_ms": round(pk, 3), "iters": int(itk.max()), "max_relres": float(rrk.max())}}
 
 
 def measure_serving(n_requests=128, rate=150.0):
@@ -578,6 +589,47 @@ def measure_schedules(steps=10, warmup=3):
     return out
 
 
+def measure_block(m=32, steps=3, warmup=1):
+    """32 right-hand sides solved as independent CG recurrences (giamg_solve_batch) and as one
+    block in block CG (giamg_solve_block), FP32 and FP64 V-cycle, CUDA-event medians: the 24^3
+    p = 4 Poisson workload and the 16^3 p = 6 operator in the modal basis."""
+    import statistics
+    import numpy as np
+    import torch
+    import fegen
+    import paper_2512_15121_gb300 as g
+    out = {}
+    for name, cfg, k in (("poisson_24cube_jitter_p4", fegen.WORKLOADS["poisson_24cube_jitter_p4"], 2),
+                         ("helmholtz_16cube_jitter_p6_modal", dict(fegen.WORKLOADS["helmholtz_16cube_jitter_p6"],
+                                                                   basis="modal"), 3)):
+        cfg = {key: v for key, v in cfg.items() if key != "k"}
+        cfg["rhs"] = "none"
+        prob = fegen.make(**cfg)
+        B = torch.from_numpy(np.stack([prob.rhs("fourier", 1000 + j) for j in range(m)], axis=1)).cuda()
+        S = g.Solver.from_problem(prob, device=True, cheb_degree=k, basis=1 if cfg.get("basis") == "modal" else 0)
+        res = {}
+        for prec, pkey in ((1, "mixed"), (0, "fp64")):
+            for block, bkey in ((False, "independent"), (True, "block")):
+                for _ in range(warmup):
+                    S.solve_batch(B, rtol=1e-8, precision=prec, block=block)
+                ts = []
+                for _ in range(steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    _, it, rr = S.solve_batch(B, rtol=1e-8, precision=prec, block=block)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                med = statistics.median(ts)
+                res[f"{pkey}_{bkey}"] = {"ms": round(med, 2), "iters": int(it.max()),
+                                         "ms_per_iter": round(med / max(int(it.max()), 1), 3),
+                                         "max_relres": float(rr.max()), "status": S.last_status}
+        S.close()
+        out[name] = {"dofs": prob.n, "m": m, **res}
+        prob.close()
+    return out
+
+
 def cpu_baseline(prob, k, rtol, iters):
     """The oracle as it stands, on the host cores: two CG iterations (FP32 V-cycle, flexible CG)
     on the full workload, scaled to the GPU's iteration count."""
@@ -596,6 +648,9 @@ def main():
     args = parse()
     if args.summarize_launches:
         print(summarize_launches(args.summarize_launches, args.split_at))
+        return
+    if args.block:
+        print(json.dumps({"block": measure_block()}))
         return
     if args.schedules:
         print(json.dumps({"schedules": measure_schedules()}))

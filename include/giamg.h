@@ -156,6 +156,24 @@ GIAMG_API int giamg_solve_batch(giamg_handle h, int m, const double* B, double* 
 GIAMG_API int giamg_solve_batch_ex(giamg_handle h, int precision, int force_iters, int m, const double* B, double* X,
                                    double rtol, int* iters, double* relres);
 
+/* The m right-hand sides as one block in block PCG (O'Leary, "The block conjugate gradient
+ * algorithm and related methods", 1980), preconditioned by the V-cycle of Algorithm 1: one
+ * Krylov space shared by all columns, m x m coefficient matrices per iteration, X0 = 0:
+ *   Q = A P;  G = P^T Q;  alpha = G^+ (P^T R);  X += P alpha;  R -= Q alpha;
+ *   Z = M R;  beta = -G^+ (Q^T Z);  P = Z + P beta   (P0 = Z0 = M B).
+ * beta keeps P A-conjugate to the previous block for a fixed or a varying (FP32) V-cycle.
+ * G^+: G scaled to unit diagonal and factored by Cholesky in index order; a direction with
+ * pivot <= 1e-10 (dependent, duplicate or zero columns) is dropped from alpha and beta.
+ *   precision: 0 FP64 V-cycle, 1 FP32 V-cycle; everything else is FP64.
+ *   B, X: row-major n x m, 1 <= m <= 32 (host or device per device_ptrs; caller-owned).
+ *   iters[m]: the block iteration count (the same for every column); relres[m]: per column.
+ *   force_iters > 0: exactly that many iterations, rtol ignored.
+ * The iteration stops when every column has ||r_j|| <= rtol ||b_j||.  GIAMG_ERR_MAXITER when
+ * max_iter is reached first (X valid); GIAMG_ERR_BREAKDOWN on NaN, or when every direction is
+ * dropped while a column is above rtol. */
+GIAMG_API int giamg_solve_block(giamg_handle h, int precision, int force_iters, int m, const double* B, double* X,
+                                double rtol, int* iters, double* relres);
+
 /* After a solve: relative residual history hist[0..min(len, iters+1)) of the recursive
  * residual, and the true relative residual ||b - A x|| / ||b|| recomputed in FP64. */
 GIAMG_API int giamg_solve_stats(giamg_handle h, double* hist, int len, double* true_relres);

@@ -24,7 +24,7 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 
 # every entry point the header declares (checked by the CPU tests against the .so)
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
-           "giamg_solve_batch", "giamg_solve_batch_ex",
+           "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
            "giamg_level_rho", "giamg_set_cheb_degree", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
@@ -73,6 +73,7 @@ def lib():
         L.giamg_solve_stats.argtypes = [vp, vp, i32, P(dbl)]
         L.giamg_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
         L.giamg_solve_batch_ex.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
+        L.giamg_solve_block.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
         L.giamg_num_levels.argtypes = [vp, P(i32)]
         L.giamg_level_info.argtypes = [vp, i32, P(i32), P(i64), P(i64), P(i32), P(i64), P(i64)]
         L.giamg_export_level.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -232,8 +233,9 @@ class Solver:
         self.last_status = rc
         return x, it, rr
 
-    def solve_batch(self, B, rtol=1e-8, precision=None, force_iters=None, X=None):
-        """B: n x m (row-major, m <= 32).  Returns (X, iters[m], relres[m])."""
+    def solve_batch(self, B, rtol=1e-8, precision=None, force_iters=None, X=None, block=False):
+        """B: n x m (row-major, m <= 32).  Returns (X, iters[m], relres[m]).  block=True: the
+        columns as one block in block CG (giamg_solve_block) instead of independent CGs."""
         m = int(B.shape[1])
         if self.device:
             import torch
@@ -246,11 +248,16 @@ class Solver:
         rr = np.zeros(m, np.float64)
         prec = self.opts.precision if precision is None else precision
         force = self.opts.force_iters if force_iters is None else force_iters
-        rc = lib().giamg_solve_batch_ex(self._h, prec, force, m, _ptr(B), _ptr(X), rtol, _ptr(it), _ptr(rr))
+        fn = lib().giamg_solve_block if block else lib().giamg_solve_batch_ex
+        rc = fn(self._h, prec, force, m, _ptr(B), _ptr(X), rtol, _ptr(it), _ptr(rr))
         if rc not in (GIAMG_OK, GIAMG_ERR_MAXITER):
             _check(rc)
         self.last_status = rc
         return X, it, rr
+
+    def solve_block(self, B, rtol=1e-8, precision=None, force_iters=None, X=None):
+        """Block CG on the columns of B (n x m, m <= 32).  Returns (X, iters[m], relres[m])."""
+        return self.solve_batch(B, rtol=rtol, precision=precision, force_iters=force_iters, X=X, block=True)
 
     def stats(self, hist_len=0):
         hist = np.zeros(max(hist_len, 1))

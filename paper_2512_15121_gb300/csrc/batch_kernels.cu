@@ -246,21 +246,6 @@ __global__ void bat_cheb_first(int64_t n, int m, const V* __restrict__ B, const 
   }
 }
 
-// per-column partial sums over a fixed partition of the rows: block b handles rows
-// [b*chunk, (b+1)*chunk); lane j of each warp accumulates column j (m <= 32)
-__device__ __forceinline__ void column_block_sum(double v, int m, double* sh, double* out) {
-  // v: this thread's partial for column (threadIdx.x & 31); reduce over the block's warps
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  sh[w * 32 + l] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int k = 0; k < nw; ++k) s += sh[k * 32 + threadIdx.x];
-    if (threadIdx.x < m) out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
 // Batched CG scalars, one entry per column.
 struct BatchScalars {
   double rho[32], pq[32], alpha[32], beta[32], rr[32], bb[32];

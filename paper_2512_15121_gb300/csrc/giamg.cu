@@ -28,9 +28,10 @@ void set_error(int code, const std::string& msg) {
 Hierarchy::~Hierarchy() {
   for (SolveGraph& G : graph)
     if (G.exec) cudaGraphExecDestroy(G.exec);
-  for (auto& per_m : bgraph)
-    for (SolveGraph& G : per_m)
-      if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto* set : {&bgraph, &kgraph})
+    for (auto& per_m : *set)
+      for (SolveGraph& G : per_m)
+        if (G.exec) cudaGraphExecDestroy(G.exec);
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (h_gst) cudaFreeHost(h_gst);
   if (h_bgst) cudaFreeHost(h_bgst);
@@ -782,15 +783,20 @@ int solve_impl(Ctx& C, int precision, int force_iters, const double* b_in, doubl
 }
 
 // ------------------------------------------------------------------ multi-right-hand-side solve
+void drop_batch_graphs(Hierarchy& H) {
+  for (auto* set : {&H.bgraph, &H.kgraph})
+    for (auto& per_m : *set)
+      for (SolveGraph& G : per_m)
+        if (G.exec) {
+          GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
+          G = SolveGraph{};
+        }
+}
+
 void alloc_batch(Hierarchy& H, int m) {
   if (H.bm >= m) return;
   cudaStream_t s = H.stream;
-  for (auto& per_m : H.bgraph)  // captured graphs hold the old buffers
-    for (SolveGraph& G : per_m)
-      if (G.exec) {
-        GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
-        G = SolveGraph{};
-      }
+  drop_batch_graphs(H);  // captured graphs hold the old buffers
   for (Level* Lp : H.lev) {
     Level& L = *Lp;
     const size_t nm = (size_t)std::max<int64_t>(L.A.n, 1) * m;
@@ -808,6 +814,8 @@ void alloc_batch(Hierarchy& H, int m) {
   H.bX.alloc(nm, s); H.bB.alloc(nm, s);
   H.bpartial.alloc((size_t)2 * batch_reduction_blocks() * 32, s);
   H.bsc.alloc(batch_scalars_bytes(), s);
+  H.kpartial.alloc((size_t)block_gram_blocks() * 2 * 1024, s);
+  H.kst.alloc(1, s);
   if (!H.h_bsc) GIAMG_CUDA(cudaMallocHost(&H.h_bsc, batch_scalars_bytes()));
   H.bm = m;
 }
@@ -902,12 +910,38 @@ void bat_step(Ctx& C, int precision, int m, double* X) {
                     H.bsc.get(), s);
 }
 
+// The halves of a block CG iteration (O'Leary 1980, A-conjugate directions): after the
+// V-cycle, beta = -G^+ Q^T Z and P = Z + P beta; the step Q = A P, G = P^T Q, C = P^T R,
+// alpha = G^+ C, X += P alpha, R -= Q alpha.
+// With the FP32 V-cycle (precision 1) the Gram products and P beta take FP32 arithmetic.
+void blk_precondition(Ctx& C, int precision, int m, int first) {
+  Hierarchy& H = *C.H;
+  const double* Z = apply_bvcycle(C, precision, m, H.bR.get());
+  if (!first) {
+    blk_gram(H.n, m, H.bQ.get(), Z, nullptr, precision, H.kpartial.get(), H.kst.get(), H.stream);
+    blk_coef(m, 1, precision ? kBlockDropTol32 : kBlockDropTol, H.kst.get(), H.stream);
+  }
+  blk_update_p(H.n, m, Z, H.bP.get(), H.kst.get(), first, precision, H.stream);
+}
+void blk_step(Ctx& C, int precision, int m, double* X) {
+  Hierarchy& H = *C.H;
+  Level& L0 = *H.lev[0];
+  cudaStream_t s = H.stream;
+  bat_rows_launch64(L0.A, m, 0, L0.A.v.get(), H.bP.get(), nullptr, H.bQ.get(), nullptr, nullptr, 0.0, 0.0, s);
+  blk_gram(H.n, m, H.bP.get(), H.bQ.get(), H.bR.get(), precision, H.kpartial.get(), H.kst.get(), s);
+  blk_coef(m, 0, precision ? kBlockDropTol32 : kBlockDropTol, H.kst.get(), s);
+  blk_update_xr(H.n, m, H.bP.get(), H.bQ.get(), X, H.bR.get(), H.kst.get(), H.bpartial.get(), H.bsc.get(), s);
+}
+
 // Capture the multi-right-hand-side solve for (precision, m) as one CUDA graph, shaped like the
 // single-vector one: init; start; IF go: precondition (first); WHILE cont: step; check;
-// IF cont: precondition.  It reads B from H.bB and writes X to H.bX.
-void capture_batch(Ctx& C, int precision, int m) {
+// IF cont: precondition.  It reads B from H.bB and writes X to H.bX.  block: block CG instead
+// of independent columns.
+void capture_batch(Ctx& C, int precision, int m, bool block) {
   Hierarchy& H = *C.H;
-  SolveGraph& G = H.bgraph[precision][m];
+  SolveGraph& G = (block ? H.kgraph : H.bgraph)[precision][m];
+  auto precondition = block ? blk_precondition : bat_precondition;
+  auto step = block ? blk_step : bat_step;
   if (!H.capture_stream) GIAMG_CUDA(cudaStreamCreateWithFlags(&H.capture_stream, cudaStreamNonBlocking));
   if (!H.bgst.get()) {
     H.bgst.alloc(1, H.stream);
@@ -947,18 +981,18 @@ void capture_batch(Ctx& C, int precision, int m) {
   GIAMG_CUDA(cudaStreamEndCapture(cs, &g));
   const long long c1 = g_launches.load();
   GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_first, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  bat_precondition(C, precision, m, 1);
+  precondition(C, precision, m, 1);
   GIAMG_CUDA(cudaStreamEndCapture(cs, &body_first));
   const long long c2 = g_launches.load();
   GIAMG_CUDA(cudaGraphConditionalHandleCreate(&h_more, body_loop, 0, cudaGraphCondAssignDefault));
   GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_loop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  bat_step(C, precision, m, H.bX.get());
+  step(C, precision, m, H.bX.get());
   bat_graph_check_launch(H.bsc.get(), m, H.bgst.get(), h_loop, h_more, cs);
   cudaGraph_t body_more = add_conditional(cs, h_more, cudaGraphCondTypeIf);
   GIAMG_CUDA(cudaStreamEndCapture(cs, &body_loop));
   const long long c3 = g_launches.load();
   GIAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body_more, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  bat_precondition(C, precision, m, 0);
+  precondition(C, precision, m, 0);
   GIAMG_CUDA(cudaStreamEndCapture(cs, &body_more));
   const long long c4 = g_launches.load();
   GIAMG_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
@@ -970,7 +1004,7 @@ void capture_batch(Ctx& C, int precision, int m) {
 }
 
 int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double* B_in, double* X_out, double rtol,
-                     int* iters, double* relres) {
+                     int* iters, double* relres, bool block) {
   Hierarchy& H = *C.H;
   cudaStream_t s = H.stream;
   const int64_t n = H.n;
@@ -992,10 +1026,10 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
   std::vector<int> its(m, 0);
   int it = 0;
   bool breakdown = false;
-  SolveGraph& BG = H.bgraph[precision][m];
+  SolveGraph& BG = (block ? H.kgraph : H.bgraph)[precision][m];
   if (H.opt.graphs && !H.prof.on && (BG.exec || ++BG.uses >= (H.opt.graphs == 2 ? 1 : 2))) {
-    if (!BG.exec) capture_batch(C, precision, m);
-    const SolveGraph& G = H.bgraph[precision][m];
+    if (!BG.exec) capture_batch(C, precision, m, block);
+    const SolveGraph& G = BG;
     GIAMG_CUDA(cudaMemcpyAsync(H.bB.get(), B_in, sizeof(double) * n * m, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     BatchGraphState& gs = *H.h_bgst;
     gs.limit = limit;
@@ -1007,7 +1041,7 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
     GIAMG_CUDA(cudaStreamSynchronize(s));
     it = gs.it;
     breakdown = gs.breakdown != 0;
-    for (int j = 0; j < m; ++j) its[j] = gs.its[j];
+    for (int j = 0; j < m; ++j) its[j] = block ? it : gs.its[j];
     const bool ran = it > 0;
     g_launches.fetch_add(G.n_init + (ran ? G.n_first + it * G.n_loop + (it - 1) * G.n_more : 0));
   } else {
@@ -1023,21 +1057,23 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
     GIAMG_CUDA(cudaStreamSynchronize(s));
     int active = 0;
     for (int j = 0; j < m; ++j) active += hs->active[j];
-    if (active > 0 && limit > 0) bat_precondition(C, precision, m, 1);
+    auto precondition = block ? blk_precondition : bat_precondition;
+    auto step = block ? blk_step : bat_step;
+    if (active > 0 && limit > 0) precondition(C, precision, m, 1);
     while (active > 0 && it < limit) {
-      bat_step(C, precision, m, Xd);
+      step(C, precision, m, Xd);
       const std::vector<int> was(hs->active, hs->active + m);
       GIAMG_CUDA(cudaMemcpyAsync(hs, sc, sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
       GIAMG_CUDA(cudaStreamSynchronize(s));
       ++it;
       active = 0;
       for (int j = 0; j < m; ++j) {
-        if (was[j]) its[j] = it;
+        if (was[j] || block) its[j] = it;
         if (hs->status[j] != 0) breakdown = true;
         active += hs->active[j];
       }
       if (breakdown || active == 0 || it == limit) break;
-      bat_precondition(C, precision, m, 0);
+      precondition(C, precision, m, 0);
     }
     if (!dev) GIAMG_CUDA(cudaMemcpyAsync(X_out, Xd, sizeof(double) * n * m, cudaMemcpyDeviceToHost, s));
     GIAMG_CUDA(cudaStreamSynchronize(s));
@@ -1049,7 +1085,7 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
     if (relres) relres[j] = rr;
     if (!force && !(rr <= rtol)) unconverged = true;
   }
-  if (breakdown) throw Error{GIAMG_ERR_BREAKDOWN, "CG breakdown in at least one column"};
+  if (breakdown) throw Error{GIAMG_ERR_BREAKDOWN, block ? "block CG breakdown" : "CG breakdown in at least one column"};
   if (unconverged) throw Error{GIAMG_ERR_MAXITER, "max_iter reached before rtol in at least one column"};
   return GIAMG_OK;
 }
@@ -1148,13 +1184,18 @@ int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double*
 int giamg_solve_batch(giamg_handle h, int m, const double* B, double* X, double rtol, int* iters, double* relres) {
   return guarded([&] {
     Ctx& C = *ctx_of(h);
-    return solve_batch_impl(C, C.H->opt.precision, C.H->opt.force_iters, m, B, X, rtol, iters, relres);
+    return solve_batch_impl(C, C.H->opt.precision, C.H->opt.force_iters, m, B, X, rtol, iters, relres, false);
   });
 }
 
 int giamg_solve_batch_ex(giamg_handle h, int precision, int force_iters, int m, const double* B, double* X, double rtol,
                          int* iters, double* relres) {
-  return guarded([&] { return solve_batch_impl(*ctx_of(h), precision, force_iters, m, B, X, rtol, iters, relres); });
+  return guarded([&] { return solve_batch_impl(*ctx_of(h), precision, force_iters, m, B, X, rtol, iters, relres, false); });
+}
+
+int giamg_solve_block(giamg_handle h, int precision, int force_iters, int m, const double* B, double* X, double rtol,
+                      int* iters, double* relres) {
+  return guarded([&] { return solve_batch_impl(*ctx_of(h), precision, force_iters, m, B, X, rtol, iters, relres, true); });
 }
 
 int giamg_solve_stats(giamg_handle h, double* hist, int len, double* true_relres) {
@@ -1271,12 +1312,7 @@ int giamg_set_cheb_degree(giamg_handle h, int degree) {
         GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
         G = SolveGraph{};
       }
-    for (auto& per_m : H.bgraph)
-      for (SolveGraph& G : per_m)
-        if (G.exec) {
-          GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
-          G = SolveGraph{};
-        }
+    drop_batch_graphs(H);
     return GIAMG_OK;
   });
 }

@@ -184,6 +184,17 @@ struct GraphState {
   int status;
 };
 
+// Block CG (O'Leary) on m <= 32 columns: the m x m matrices of one iteration, row-major 32 x 32
+// with entry [a * 32 + c] = direction a, column c.
+struct BlockState {
+  double gram[2][1024];  // last reduced block products: G = P^T Q and C = P^T R, or E = Q^T Z in [0]
+  double L[1024];        // Cholesky factor of diag(G)^-1/2 G diag(G)^-1/2 on the kept directions
+  double alpha[1024];    // G^+ C
+  double beta[1024];     // -G^+ E
+  double s[32];          // diag(G)^-1/2, 0 for a dropped direction
+  int keep[32];
+  int rank, pad;
+};
 // Device-side state of the multi-right-hand-side solve captured as a CUDA graph.
 struct BatchGraphState {
   int it, limit, breakdown, pad;
@@ -247,6 +258,9 @@ struct Hierarchy {
   DBuf<GraphState> gst;
   GraphState* h_gst = nullptr;  // pinned host copy
   SolveGraph bgraph[2][33];       // multi-right-hand-side solve graphs by precision and m
+  SolveGraph kgraph[2][33];       // block CG solve graphs by precision and m
+  DBuf<double> kpartial;          // block CG: per-block partial Gram products
+  DBuf<BlockState> kst;           // block CG: the m x m matrices of the current iteration
   DBuf<BatchGraphState> bgst;
   BatchGraphState* h_bgst = nullptr;
   ~Hierarchy();
@@ -362,6 +376,39 @@ struct BatchScalarsHost {
   int force;
   int pad;
 };
+
+// per-column partial sums over a fixed partition of the rows: block b handles rows
+// [b*chunk, (b+1)*chunk); lane j of each warp accumulates column j (m <= 32)
+__device__ __forceinline__ void column_block_sum(double v, int m, double* sh, double* out) {
+  // v: this thread's partial for column (threadIdx.x & 31); reduce over the block's warps
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  sh[w * 32 + l] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sh[k * 32 + threadIdx.x];
+    if (threadIdx.x < m) out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// pivot of the unit-diagonal Gram matrix below which a direction is dropped: FP64 products,
+// and FP32 products (whose entries carry ~1e-7 relative rounding)
+constexpr double kBlockDropTol = 1e-10;
+constexpr double kBlockDropTol32 = 1e-5;
+int block_gram_blocks();
+// O = Lf^T R1 (and Lf^T R2), reduced into st->gram[0] (and [1]); Lf, R1, R2 are n x m row-major;
+// fp32: products in FP32 arithmetic, FP64 accumulation across chunks
+void blk_gram(int64_t n, int m, const double* Lf, const double* R1, const double* R2, int fp32, double* partial,
+              BlockState* st, cudaStream_t s);
+// factor G = st->gram[0] and alpha = G^+ st->gram[1] (mode 0); beta = -G^+ st->gram[0] (mode 1)
+void blk_coef(int m, int mode, double tau, BlockState* st, cudaStream_t s);
+// X += P alpha; R -= Q alpha; per-column ||r||^2, convergence and breakdown into the batch scalars
+void blk_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, const BlockState* st,
+                   double* partial, void* sc, cudaStream_t s);
+// P = Z + P beta (first: P = Z); fp32: P beta in FP32 arithmetic
+void blk_update_p(int64_t n, int m, const double* Z, double* P, const BlockState* st, int first, int fp32,
+                  cudaStream_t s);
 
 // ------------------------------------------------------------------ setup kernels
 uint32_t host_hash(int kind, int64_t i);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgiamg.so")
-SOURCES = ["giamg.cu", "solve_kernels.cu", "setup_kernels.cu", "noalloc.cu", "pattern.cu", "batch_kernels.cu", "graph_kernels.cu"]
+SOURCES = ["giamg.cu", "solve_kernels.cu", "setup_kernels.cu", "noalloc.cu", "pattern.cu", "batch_kernels.cu", "graph_kernels.cu", "block_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -15,6 +15,11 @@ to a minute on the host cores, so the checks are the ones of the small cases:
   FP32 V-cycle in FP64 flexible CG: true relative residual (oracle product)     <= 1.5e-8
   32-column batch (Poisson): three columns against the oracle's single solves   x within 1e-10
                              every column's true residual (oracle product)      <= 1.5e-8
+  32-column block CG (Poisson), both V-cycle precisions: every column's true
+                             residual (oracle product)                          <= 1.5e-8
+                             (the oracle's block PCG couples all 32 columns through 32 V-cycles
+                             per iteration, too slow at this size; it is compared element by
+                             element on the smaller cases of test_gpu_block.py)
 """
 import numpy as np
 import pytest
@@ -123,3 +128,17 @@ def test_batch_32_columns(full):
     for j in range(32):
         r = B[:, j] - full.orc.spmv(0, Xm[:, j])
         assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(B[:, j]), j
+
+
+def test_block_32_columns(full):
+    if full.name != "poisson_24cube_jitter_p4":
+        pytest.skip("the 32-RHS batch is the Poisson workload's")
+    prob = full.prob
+    B = np.stack([prob.rhs("fourier", 1000 + j) for j in range(32)], axis=1)
+    for precision in (1, 0):
+        X, it, rr = full.gpu.solve_block(dev(B), rtol=1e-8, precision=precision)
+        assert full.gpu.last_status == g.GIAMG_OK and np.all(it == it[0]) and np.all(rr <= 1e-8)
+        X = X.cpu().numpy()
+        for j in range(32):
+            r = B[:, j] - full.orc.spmv(0, X[:, j])
+            assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(B[:, j]), (precision, j)
