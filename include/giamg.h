@@ -87,8 +87,10 @@ typedef struct {
                              (FP32 rows: pattern form; FP64 rows: CSR with 16 threads per row) */
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
                              groups, 4 hybrid (groups of at least 16 rows by the group kernel, the
-                             other rows by the row-pattern kernel); each falls back to CSR where
-                             the form is not available */
+                             other rows by the row-pattern kernel), 5 vector hybrid (FP32 rows:
+                             the big groups' values from a group-major copy with rows padded to
+                             16 bytes, read with 16-byte loads; FP64 rows as 4); each falls back
+                             to CSR where the form is not available */
   int row_threads;        /* force threads per row (4, 8, 16, 32); 0 automatic */
   int prefetch_rows;      /* row-pattern kernels: every block prefetches into L2 the values of the
                              block this many rows ahead; 0 off, -1 (default) automatic */
@@ -197,8 +199,8 @@ GIAMG_API int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_
 GIAMG_API int giamg_level_templates(giamg_handle h, int level, int64_t* n_templates, int64_t* n_offsets);
 /* Row-kernel variant used on A_l for precision 0 (FP64) or 1 (FP32): threads per row and the
  * form (*pattern: 0 CSR, 1 row patterns, 2 row groups with identical column sets, 3 hybrid of
- * big row groups and row patterns), chosen by the
- * setup-time tuner when autotune is set. */
+ * big row groups and row patterns, 4 vector hybrid), chosen by the setup-time tuner when
+ * autotune is set. */
 GIAMG_API int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern);
 /* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */
 GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);

@@ -356,7 +356,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   GIAMG_CHECK(opt.max_levels >= 1 && opt.max_levels <= 64, GIAMG_ERR_ARG, "max_levels must be in [1, 64]");
   GIAMG_CHECK(opt.lanczos_steps >= 1, GIAMG_ERR_ARG, "lanczos_steps must be >= 1");
   GIAMG_CHECK(opt.precision == 0 || opt.precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
-  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 4, GIAMG_ERR_ARG, "row_form must be in 0..4");
+  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 5, GIAMG_ERR_ARG, "row_form must be in 0..5");
   GIAMG_CHECK(opt.row_threads == 0 || opt.row_threads == 4 || opt.row_threads == 8 || opt.row_threads == 16 ||
                   opt.row_threads == 32,
               GIAMG_ERR_ARG, "row_threads must be 0, 4, 8, 16 or 32");
@@ -511,6 +511,10 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       }
       if (opt.autotune) tune_rows(L.A, s);
       else choose_rows(L.A, opt.row_form, opt.row_threads);
+      if (L.A.var32.vector) {
+        L.A.var32.vector = hybrid_vector_build(L.A, s);
+        clk.mark("group-major FP32 copy", (int)l);
+      }
       set_prefetch(L.A, opt.prefetch_rows, opt.row_chains);
       alloc_work(L, s);
       if (L.kind != GIAMG_LEVEL_COARSEST) {
@@ -1291,7 +1295,8 @@ int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_pe
     const RowVariant& v = precision == 0 ? L.A.var64 : L.A.var32;
     const double avg = L.A.n ? (double)L.A.nnz / L.A.n : 0.0;
     if (threads_per_row) *threads_per_row = v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
-    if (pattern) *pattern = v.hybrid ? 3 : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
+    if (pattern)
+      *pattern = v.hybrid ? (v.vector && L.A.grp.hvon ? 4 : 3) : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
     return GIAMG_OK;
   });
 }

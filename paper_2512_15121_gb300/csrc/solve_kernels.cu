@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -286,6 +287,118 @@ HYB_SELECT(float, kCheb, hyb_cheb_f32)
 HYB_SELECT(double, kAddSpmv, hyb_add_f64)
 HYB_SELECT(float, kAddSpmv, hyb_add_f32)
 
+// ------------------------------------------------------------------ vector hybrid form (FP32)
+// The hybrid form with the big groups read from a group-major copy of the FP32 values (hv): a
+// group is one contiguous block and every row starts on 16 bytes (rows padded with zeros to a
+// multiple of 4 values), so the warp of a row loads it with float4 loads, 4 per lane at once,
+// from a sequential stream: one step covers a row of 344 padded values (86 float4 of 128
+// slots), two a row of 640.  Against hyb_body's 4-byte loads from rows scattered over the value
+// array this doubles the bytes a warp has in flight with the same 32 registers.  The other rows
+// run the row-pattern kernel in the same launch, as in hyb_body's kernel.
+template <typename V>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int kU = 4;
+  static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void fma4(const T& v, const T& x, float* a) {
+    a[0] = fmaf(v.x, x.x, a[0]);
+    a[1] = fmaf(v.y, x.y, a[1]);
+    a[2] = fmaf(v.z, x.z, a[2]);
+    a[3] = fmaf(v.w, x.w, a[3]);
+  }
+};
+template <typename V, int MODE>
+__device__ __forceinline__ void hyv_body(const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,
+                                         const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr,
+                                         const int32_t* __restrict__ grow, const int64_t* __restrict__ hoff,
+                                         const V* __restrict__ hv, const V* __restrict__ x,
+                                         const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,
+                                         const V* __restrict__ dinv, V c1, V c2) {
+  using VT = typename Vec16<V>::T;
+  constexpr int EV = 16 / sizeof(V), U = Vec16<V>::kU;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xs = reinterpret_cast<V*>(smem_raw);
+  const int64_t j = blockIdx.x;
+  const int64_t g = big[j];
+  const int64_t c0 = gptr[g];
+  const int c = (int)(gptr[g + 1] - c0);
+  const int cp = (c + 3) & ~3, nq = cp / EV;
+  const int64_t t0 = rptr[g];
+  const int rows = (int)(rptr[g + 1] - t0);
+  const V* src = hv + hoff[j];
+  for (int k = threadIdx.x; k < cp; k += blockDim.x) xs[k] = k < c ? x[__ldg(gcol + c0 + k)] : V(0);
+  __syncthreads();
+  const VT* xq = reinterpret_cast<const VT*>(xs);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = warp; t < rows; t += nw) {
+    const VT* vr = reinterpret_cast<const VT*>(src + (int64_t)t * cp);
+    V a[4] = {V(0), V(0), V(0), V(0)};
+    for (int q0 = 0; q0 < nq; q0 += 32 * U) {
+      VT v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + lane + 32 * u;
+        v[u] = q < nq ? __ldcs(vr + q) : Vec16<V>::zero();
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + lane + 32 * u;
+        Vec16<V>::fma4(v[u], xq[q < nq ? q : 0], a);  // a padded slot multiplies zeros
+      }
+    }
+    V acc = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane != 0) continue;
+    const int64_t row = grow[t0 + t];
+    if (MODE == kSpmv) {
+      y[row] = acc;
+    } else if (MODE == kAddSpmv) {
+      y[row] += acc;
+    } else if (MODE == kResidual) {
+      y[row] = b[row] - acc;
+    } else {
+      const V rr = b[row] - acc;
+      const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * rr;
+      d[row] = dn;
+      y[row] = x[row] + dn;
+    }
+  }
+}
+
+#define HYV_KERNEL(NAME, V, MODE)                                                                               \
+  __global__ void __launch_bounds__(kThreads)                                                                 \
+      NAME(int64_t n_big, const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,                  \
+           const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow, \
+           const int64_t* __restrict__ hoff, const V* __restrict__ hv,                                       \
+           int64_t n_rest, const int32_t* __restrict__ rest, const int32_t* __restrict__ obase,               \
+           const int32_t* __restrict__ toff, const int64_t* __restrict__ rp, const V* __restrict__ val,       \
+           const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,            \
+           const V* __restrict__ dinv, V c1, V c2) {                                                          \
+    if ((int64_t)blockIdx.x < n_big)                                                                          \
+      hyv_body<V, MODE>(big, gptr, gcol, rptr, grow, hoff, hv, x, b, y, d, dinv, c1, c2);                    \
+    else                                                                                                      \
+      pat_body<32, 2, V, MODE, true>(n_rest, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, 0, 0, rest, n_big); \
+  }
+HYV_KERNEL(hyv_spmv_f32, float, kSpmv)
+HYV_KERNEL(hyv_resid_f32, float, kResidual)
+HYV_KERNEL(hyv_cheb_f32, float, kCheb)
+HYV_KERNEL(hyv_add_f32, float, kAddSpmv)
+
+template <typename V, int MODE>
+struct HyvKernel;
+#define HYV_SELECT(V, MODE, H)                          \
+  template <>                                           \
+  struct HyvKernel<V, MODE> {                           \
+    static constexpr decltype(&H) get() { return &H; }  \
+  };
+HYV_SELECT(float, kSpmv, hyv_spmv_f32)
+HYV_SELECT(float, kResidual, hyv_resid_f32)
+HYV_SELECT(float, kCheb, hyv_cheb_f32)
+HYV_SELECT(float, kAddSpmv, hyv_add_f32)
+
 // Row-group kernels: one CTA per group of rows with identical column sets; the group's x values
 // are gathered once into shared memory, then every warp streams one row's values from HBM
 // against them (consecutive lanes read consecutive shared words: no bank conflicts).
@@ -399,6 +512,25 @@ void launch_hyb(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   note_launch();
 }
 
+template <typename V, int MODE>
+void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  auto k = HyvKernel<V, MODE>::get();
+  const size_t sm = (size_t)A.grp.cpmax * sizeof(V);
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
+  const V* hv = A.grp.hv.get();
+  const int64_t rest_blocks = (A.grp.n_rest * 32 + kThreads - 1) / kThreads;
+  k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
+      A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
+      A.grp.hoff.get(), hv, A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(), A.rp.get(), val, x,
+      b, y, d, dinv, c1, c2);
+  note_launch();
+}
+
 template <int TPR, int U, typename V, int MODE>
 void launch_pat(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
                 int64_t pf, cudaStream_t s) {
@@ -431,7 +563,12 @@ void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* v
                     const V* dinv, V c1, V c2, cudaStream_t s) {
   const int tpr = var.tpr ? var.tpr : default_tpr(avg);
   const bool pat = var.tpr ? var.pat : A.pat.on;
-  if (var.hybrid && A.grp.hyb && A.pat.on) {
+  bool vector = false;
+  if constexpr (std::is_same<V, float>::value)
+    vector = var.hybrid && var.vector && A.grp.hyb && A.pat.on && A.grp.hvon && val == A.v32.get();
+  if (vector) {
+    if constexpr (std::is_same<V, float>::value) launch_hyv<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
+  } else if (var.hybrid && A.grp.hyb && A.pat.on) {
     launch_hyb<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
   } else if (var.group && A.grp.on) {
     launch_grp<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
@@ -902,11 +1039,13 @@ void choose_rows(DCSR& A, int form, int threads) {
       // threads per long row
       v.pat = prec == 1 && A.pat.on;
       v.hybrid = prec == 1 && A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
+      v.vector = v.hybrid;
       v.tpr = prec == 1 ? (v.hybrid ? 32 : default_tpr(avg)) : (avg >= 48 ? 16 : default_tpr(avg));
     } else {
-      v.pat = (form == 2 || form == 4) && A.pat.on;
+      v.pat = (form == 2 || form >= 4) && A.pat.on;
       v.group = form == 3 && A.grp.on;
-      v.hybrid = form == 4 && A.grp.hyb && A.pat.on;
+      v.hybrid = (form >= 4) && A.grp.hyb && A.pat.on;
+      v.vector = form == 5 && v.hybrid && prec == 1;
       v.tpr = v.group || v.hybrid ? 32 : default_tpr(avg);
     }
     if (threads && !v.group && !v.hybrid) v.tpr = threads;
