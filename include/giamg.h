@@ -82,9 +82,12 @@ typedef struct {
                              (stored as a template id instead of column indices) and groups of rows
                              with identical column sets (x gathered once per group); detection is
                              exact, plain CSR otherwise; 0: plain CSR everywhere */
-  int autotune;           /* 1: time the row-kernel variants on every large level at setup and keep
-                             the fastest; 0 (default): the variants measured best inside the solve
-                             (FP32 rows: pattern form; FP64 rows: CSR with 16 threads per row) */
+  int autotune;           /* 1: time the row-kernel variants (CSR, row patterns, row groups,
+                             hybrid, vector hybrid) on every large level at setup and keep the
+                             fastest product; 0 (default): the variants measured best inside the
+                             solve (FP32 rows: vector hybrid where there are at least 4096 groups
+                             of 16 or more rows averaging 192 or more columns, else row patterns;
+                             FP64 rows: CSR with 16 threads per row) */
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
                              groups, 4 hybrid (groups of at least 16 rows by the group kernel, the
                              other rows by the row-pattern kernel), 5 vector hybrid (FP32 rows:

@@ -459,7 +459,7 @@ __global__ void hv_gather(const int32_t* __restrict__ big, const int64_t* __rest
 
 bool hybrid_vector_build(DCSR& A, cudaStream_t s) {
   Groups& R = A.grp;
-  R.hvon = false;
+  if (R.hvon) return true;  // built already (by the setup-time tuner)
   if (!R.hyb || R.n_big == 0 || !A.v32.get()) return false;
   const int64_t G = R.n_groups, nb = R.n_big;
   std::vector<int64_t> gp(G + 1), rp_h(G + 1);

@@ -1095,10 +1095,22 @@ void tune_rows(DCSR& A, cudaStream_t s) {
     v.group = true;
     cands.push_back(v);
   }
+  // the hybrid forms, the vector one (FP32 only) on a group-major copy built for the timing
+  const bool vec = A.grp.hyb && A.pat.on && hybrid_vector_build(A, s);
+  if (A.grp.hyb && A.pat.on) {
+    RowVariant v;
+    v.tpr = 32;
+    v.pat = true;
+    v.hybrid = true;
+    cands.push_back(v);
+    v.vector = true;
+    if (vec) cands.push_back(v);
+  }
   for (int prec = 0; prec < 2; ++prec) {
     float best = 1e30f;
     RowVariant pick;
     for (const RowVariant& v : cands) {
+      if (prec == 0 && v.vector) continue;
       float t = 1e30f;
       for (int rep = 0; rep < 6; ++rep) {
         GIAMG_CUDA(cudaEventRecord(e0, s));
@@ -1114,7 +1126,8 @@ void tune_rows(DCSR& A, cudaStream_t s) {
       }
       if (log)
         fprintf(stderr, "tune n=%lld nnz=%lld %s form=%s tpr=%d unroll=%d: %.4f ms\n", (long long)A.n,
-                (long long)A.nnz, prec ? "fp32" : "fp64", v.group ? "groups" : v.pat ? "pattern" : "csr", v.tpr,
+                (long long)A.nnz, prec ? "fp32" : "fp64",
+                v.vector ? "vector" : v.hybrid ? "hybrid" : v.group ? "groups" : v.pat ? "pattern" : "csr", v.tpr,
                 v.unroll, t);
       if (t < best) {
         best = t;
@@ -1122,6 +1135,11 @@ void tune_rows(DCSR& A, cudaStream_t s) {
       }
     }
     (prec == 0 ? A.var64 : A.var32) = pick;
+  }
+  if (vec && !A.var32.vector) {  // the copy is kept only for the form that reads it
+    A.grp.hv.release();
+    A.grp.hoff.release();
+    A.grp.hvon = false;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -340,6 +340,37 @@ def test_row_kernel_forms_match_oracle(form, threads):
         gpu.close()
 
 
+def test_autotuned_forms_match_oracle():
+    """autotune = 1 times every row-kernel form on the large levels at setup (the hybrid and vector
+    hybrid forms included) and keeps the fastest product; whatever it picks matches the oracle."""
+    if "p" not in _forms_oracle:
+        prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
+        _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
+    prob, orc = _forms_oracle["p"]
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, autotune=1)
+    try:
+        for prec in (0, 1):
+            assert gpu.kernel(0, prec)[1] in ("csr", "pattern", "groups", "hybrid", "vector")
+        rng = np.random.default_rng(5)
+        for l in range(orc.num_levels):
+            rp, ci, v, _ = orc.level(l)
+            x = rng.normal(size=len(rp) - 1)
+            y, yo = host(gpu.spmv(l, dev(x))), orc.spmv(l, x)
+            assert np.max(np.abs(y - yo)) <= 1e-12 * np.max(np.abs(yo)), l
+            y32 = gpu.spmv32(l, dev(x)).cpu().numpy().astype(np.float64)
+            ref, bound = fp32_product_bound(rp, ci, v, x)
+            assert np.all(np.abs(y32 - ref) <= bound), l
+        xo, ito, _, _, _ = orc.solve(prob.b, rtol=1e-8)
+        x, it, _ = gpu.solve(dev(prob.b), rtol=1e-8, force_iters=ito)
+        assert np.linalg.norm(host(x) - xo) <= 1e-10 * np.linalg.norm(xo)
+        xm, itm, rrm = gpu.solve(dev(prob.b), rtol=1e-8, precision=1)
+        assert rrm <= 1e-8
+        r = prob.b - orc.spmv(0, host(xm))
+        assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(prob.b)
+    finally:
+        gpu.close()
+
+
 def fp32_product_bound(rp, ci, v, x):
     """y = fl32(A) fl32(x) evaluated in FP64 from the FP32-rounded operands (the definition of the
     FP32 product up to the FP32 accumulation), and the bound n_row * 2^-23 * |fl32(A)||fl32(x)|
