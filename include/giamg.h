@@ -85,15 +85,16 @@ typedef struct {
   int autotune;           /* 1: time the row-kernel variants (CSR, row patterns, row groups,
                              hybrid, vector hybrid) on every large level at setup and keep the
                              fastest product; 0 (default): the variants measured best inside the
-                             solve (FP32 rows: vector hybrid where there are at least 4096 groups
-                             of 16 or more rows averaging 192 or more columns, else row patterns;
-                             FP64 rows: CSR with 16 threads per row) */
+                             solve (vector hybrid where there are at least 4096 groups of 16 or
+                             more rows averaging 192 or more columns; else FP32 rows on row
+                             patterns and FP64 rows on CSR with 16 threads per row) */
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
                              groups, 4 hybrid (groups of at least 16 rows by the group kernel, the
-                             other rows by the row-pattern kernel), 5 vector hybrid (FP32 rows:
-                             the big groups' values from a group-major copy with rows padded to
-                             16 bytes, read with 16-byte loads; FP64 rows as 4); each falls back
-                             to CSR where the form is not available */
+                             other rows by the row-pattern kernel), 5 vector hybrid (the big
+                             groups' values from a group-major copy with rows padded to 16 bytes,
+                             read with 16-byte loads: FP32 one warp per row, FP64 4 lanes per row
+                             and 8 rows of a group per warp); each falls back to CSR where the
+                             form is not available */
   int row_threads;        /* force threads per row (4, 8, 16, 32); 0 automatic */
   int prefetch_rows;      /* row-pattern kernels: every block prefetches into L2 the values of the
                              block this many rows ahead; 0 off, -1 (default) automatic */

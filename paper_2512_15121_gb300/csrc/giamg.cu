@@ -512,8 +512,12 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       if (opt.autotune) tune_rows(L.A, s);
       else choose_rows(L.A, opt.row_form, opt.row_threads);
       if (L.A.var32.vector) {
-        L.A.var32.vector = hybrid_vector_build(L.A, s);
+        L.A.var32.vector = hybrid_vector_build(L.A, 1, s);
         clk.mark("group-major FP32 copy", (int)l);
+      }
+      if (L.A.var64.vector) {
+        L.A.var64.vector = hybrid_vector_build(L.A, 0, s);
+        clk.mark("group-major FP64 copy", (int)l);
       }
       set_prefetch(L.A, opt.prefetch_rows, opt.row_chains);
       alloc_work(L, s);
@@ -1294,9 +1298,11 @@ int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_pe
     GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
     const RowVariant& v = precision == 0 ? L.A.var64 : L.A.var32;
     const double avg = L.A.n ? (double)L.A.nnz / L.A.n : 0.0;
-    if (threads_per_row) *threads_per_row = v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
+    const bool vec = v.hybrid && v.vector && (precision == 1 ? L.A.grp.hvon : L.A.grp.hv64on);
+    if (threads_per_row)  // the FP64 vector hybrid takes 4 lanes per row of a big group
+      *threads_per_row = vec && precision == 0 ? 4 : v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
     if (pattern)
-      *pattern = v.hybrid ? (v.vector && L.A.grp.hvon ? 4 : 3) : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
+      *pattern = v.hybrid ? (vec ? 4 : 3) : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
     return GIAMG_OK;
   });
 }

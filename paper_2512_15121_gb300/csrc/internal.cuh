@@ -99,13 +99,14 @@ struct Groups {
   int64_t n_big = 0, n_rest = 0;
   double big_cols = 0.0;  // average column count of the rows in big groups
   DBuf<int32_t> big, rest;
-  // vector hybrid form (FP32): the big groups' values copied group by group (in the order of
-  // `big`), each row padded with zeros to a multiple of 4 values, so every row starts on 16
-  // bytes and a group is one contiguous block
-  bool hvon = false;
+  // vector hybrid forms: the big groups' values copied group by group (in the order of `big`),
+  // each row padded with zeros to a multiple of 4 values, so every row starts on 16 bytes and a
+  // group is one contiguous block; hv from the FP32 values, hv64 from the FP64 values
+  bool hvon = false, hv64on = false;
   int cpmax = 0;                // widest padded row of a big group
-  DBuf<int64_t> hoff;           // start of big group j's block in hv (values), n_big + 1 entries
+  DBuf<int64_t> hoff;           // start of big group j's block (values), n_big + 1 entries
   DBuf<float> hv;
+  DBuf<double> hv64;
 };
 constexpr int kHybridRows = 16;
 
@@ -118,7 +119,7 @@ struct RowVariant {
   bool group = false;  // row-group form (one CTA per group, x gathered once into shared memory)
   bool hybrid = false;  // big row groups by the group kernel, the other rows by the pattern kernel
   int64_t prefetch = 0;  // pattern form: L2 prefetch distance in rows (0: none)
-  bool vector = false;   // hybrid form, FP32: big groups read with 16-byte loads from the group-major copy
+  bool vector = false;   // hybrid form: big groups read with 16-byte loads from the group-major copy
 };
 
 struct DCSR {
@@ -433,9 +434,10 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 void csr_to32(DCSR& A, cudaStream_t s);
 // time the row-kernel variants on A (both precisions) and keep the fastest in A.var64 / A.var32
 void tune_rows(DCSR& A, cudaStream_t s);
-// the group-major FP32 copy of the big groups' values for the vector hybrid form (needs the
-// hybrid lists and A.v32); false if the form does not apply
-bool hybrid_vector_build(DCSR& A, cudaStream_t s);
+// the group-major copy of the big groups' values for the vector hybrid form from the FP32
+// (precision 1, A.v32) or FP64 (precision 0, A.v) values; needs the hybrid lists; false if the
+// form does not apply
+bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s);
 // set A.var64 / A.var32 from forced options or the defaults measured best inside the solve
 void choose_rows(DCSR& A, int form, int threads);
 // prefetch_rows -1: automatic, 0: off, > 0: distance in rows; chains 0: keep, else 2, 4 or 8

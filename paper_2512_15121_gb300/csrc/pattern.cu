@@ -439,53 +439,67 @@ bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
 namespace {
 // One CTA per big group: the group's rows (in group order), each padded with zeros to a
 // multiple of 4 values.
+template <typename V>
 __global__ void hv_gather(const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,
                           const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow,
-                          const int64_t* __restrict__ rp, const float* __restrict__ v32,
-                          const int64_t* __restrict__ hoff, float* __restrict__ hv) {
+                          const int64_t* __restrict__ rp, const V* __restrict__ val,
+                          const int64_t* __restrict__ hoff, V* __restrict__ hv) {
   const int64_t j = blockIdx.x;
   const int64_t g = big[j];
   const int c = (int)(gptr[g + 1] - gptr[g]);
   const int cp = (c + 3) & ~3;
   const int64_t t0 = rptr[g], rows = rptr[g + 1] - t0;
-  float* __restrict__ out = hv + hoff[j];
+  V* __restrict__ out = hv + hoff[j];
   for (int64_t e = threadIdx.x; e < rows * cp; e += blockDim.x) {
     const int64_t t = e / cp;
     const int k = (int)(e - t * cp);
-    out[e] = k < c ? v32[rp[grow[t0 + t]] + k] : 0.f;
+    out[e] = k < c ? val[rp[grow[t0 + t]] + k] : V(0);
   }
 }
 }  // namespace
 
-bool hybrid_vector_build(DCSR& A, cudaStream_t s) {
+bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s) {
   Groups& R = A.grp;
-  if (R.hvon) return true;  // built already (by the setup-time tuner)
-  if (!R.hyb || R.n_big == 0 || !A.v32.get()) return false;
+  if (precision == 1 ? R.hvon : R.hv64on) return true;  // built already (by the setup-time tuner)
+  if (!R.hyb || R.n_big == 0 || (precision == 1 ? !A.v32.get() : !A.v.get())) return false;
   const int64_t G = R.n_groups, nb = R.n_big;
-  std::vector<int64_t> gp(G + 1), rp_h(G + 1);
-  std::vector<int32_t> big(nb);
-  GIAMG_CUDA(cudaMemcpyAsync(gp.data(), R.gptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaMemcpyAsync(big.data(), R.big.get(), sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaStreamSynchronize(s));
-  std::vector<int64_t> hoff(nb + 1, 0);
-  int cpmax = 0;
-  for (int64_t j = 0; j < nb; ++j) {
-    const int64_t g = big[j];
-    const int cp = (int)((gp[g + 1] - gp[g] + 3) & ~(int64_t)3);
-    cpmax = std::max(cpmax, cp);
-    hoff[j + 1] = hoff[j] + (rp_h[g + 1] - rp_h[g]) * cp;
+  if (!R.hoff.get()) {  // the layout, shared by both precisions
+    std::vector<int64_t> gp(G + 1), rp_h(G + 1);
+    std::vector<int32_t> big(nb);
+    GIAMG_CUDA(cudaMemcpyAsync(gp.data(), R.gptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(big.data(), R.big.get(), sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> hoff(nb + 1, 0);
+    int cpmax = 0;
+    for (int64_t j = 0; j < nb; ++j) {
+      const int64_t g = big[j];
+      const int cp = (int)((gp[g + 1] - gp[g] + 3) & ~(int64_t)3);
+      cpmax = std::max(cpmax, cp);
+      hoff[j + 1] = hoff[j] + (rp_h[g + 1] - rp_h[g]) * cp;
+    }
+    if ((size_t)cpmax * 8 > 96 * 1024) return false;  // x of a group in shared memory (FP64)
+    R.hoff.alloc(nb + 1, s);
+    GIAMG_CUDA(cudaMemcpyAsync(R.hoff.get(), hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    R.cpmax = cpmax;
   }
-  if ((size_t)cpmax * 4 > 96 * 1024) return false;  // x of a group in shared memory
-  R.hoff.alloc(nb + 1, s);
-  GIAMG_CUDA(cudaMemcpyAsync(R.hoff.get(), hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
-  R.hv.alloc((size_t)std::max<int64_t>(hoff[nb], 4), s);
-  { hv_gather<<<(unsigned)nb, 256, 0, s>>>(R.big.get(), R.gptr.get(), R.rptr.get(), R.grow.get(), A.rp.get(), A.v32.get(),
-                                           R.hoff.get(), R.hv.get()); note_launch(); }
+  int64_t total = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&total, R.hoff.get() + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (precision == 1) {
+    R.hv.alloc((size_t)std::max<int64_t>(total, 4), s);
+    { hv_gather<float><<<(unsigned)nb, 256, 0, s>>>(R.big.get(), R.gptr.get(), R.rptr.get(), R.grow.get(), A.rp.get(),
+                                                    A.v32.get(), R.hoff.get(), R.hv.get()); note_launch(); }
+    R.hvon = true;
+  } else {
+    R.hv64.alloc((size_t)std::max<int64_t>(total, 4), s);
+    { hv_gather<double><<<(unsigned)nb, 256, 0, s>>>(R.big.get(), R.gptr.get(), R.rptr.get(), R.grow.get(),
+                                                     A.rp.get(), A.v.get(), R.hoff.get(), R.hv64.get()); note_launch(); }
+    R.hv64on = true;
+  }
   GIAMG_CUDA(cudaGetLastError());
   GIAMG_CUDA(cudaStreamSynchronize(s));
-  R.cpmax = cpmax;
-  R.hvon = true;
   return true;
 }
 

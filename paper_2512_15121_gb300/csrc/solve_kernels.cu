@@ -399,6 +399,109 @@ HYV_SELECT(float, kResidual, hyv_resid_f32)
 HYV_SELECT(float, kCheb, hyv_cheb_f32)
 HYV_SELECT(float, kAddSpmv, hyv_add_f32)
 
+// ------------------------------------------------------------------ vector hybrid form (FP64)
+// FP64 rows are bound by the FP64 pipe, which also executes the adds of a shuffle reduction as
+// full-warp instructions: with 16 or 32 lanes per row they cost 4 or 5 FP64 instructions per row
+// on top of about 11-22 FMAs, and two rows of different lengths in one warp leave lanes idle.
+// Here the big groups (from the group-major FP64 copy hv64) take 4 lanes per row and 8 rows of
+// one group per warp: every row of a group has the same length, so no lane waits on another
+// row; the reduction is 2 shuffle levels; each lane loads the row's values with 16-byte loads,
+// U at once; and the 8 rows read the same x words from shared memory (broadcasts).
+template <int MODE>
+__device__ __forceinline__ void hy4_body(const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,
+                                         const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr,
+                                         const int32_t* __restrict__ grow, const int64_t* __restrict__ hoff,
+                                         const double* __restrict__ hv, const double* __restrict__ x,
+                                         const double* __restrict__ b, double* __restrict__ y,
+                                         double* __restrict__ d, const double* __restrict__ dinv, double c1,
+                                         double c2) {
+  constexpr int U = 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* xs = reinterpret_cast<double*>(smem_raw);
+  const int64_t j = blockIdx.x;
+  const int64_t g = big[j];
+  const int64_t c0 = gptr[g];
+  const int c = (int)(gptr[g + 1] - c0);
+  const int cp = (c + 3) & ~3, nq = cp >> 1;  // double2 per padded row
+  const int64_t t0 = rptr[g];
+  const int rows = (int)(rptr[g + 1] - t0);
+  const double* src = hv + hoff[j];
+  for (int k = threadIdx.x; k < cp; k += blockDim.x) xs[k] = k < c ? x[__ldg(gcol + c0 + k)] : 0.0;
+  __syncthreads();
+  const double2* xq = reinterpret_cast<const double2*>(xs);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int sub = lane & 3, rw = lane >> 2;
+  for (int tb = warp * 8; tb < rows; tb += nw * 8) {
+    const int t = tb + rw;
+    const bool valid = t < rows;
+    const double2* vr = reinterpret_cast<const double2*>(src + (int64_t)(valid ? t : tb) * cp);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q0 = sub; q0 < nq; q0 += 4 * U) {
+      double2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + 4 * u;
+        v[u] = q < nq ? __ldcs(vr + q) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + 4 * u;
+        const double2 xv = xq[q < nq ? q : 0];
+        a[2 * (u & 1)] = fma(v[u].x, xv.x, a[2 * (u & 1)]);
+        a[2 * (u & 1) + 1] = fma(v[u].y, xv.y, a[2 * (u & 1) + 1]);
+      }
+    }
+    double acc = (a[0] + a[1]) + (a[2] + a[3]);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (!valid || sub != 0) continue;
+    const int64_t row = grow[t0 + t];
+    if (MODE == kSpmv) {
+      y[row] = acc;
+    } else if (MODE == kAddSpmv) {
+      y[row] += acc;
+    } else if (MODE == kResidual) {
+      y[row] = b[row] - acc;
+    } else {
+      const double rr = b[row] - acc;
+      const double dn = (c1 == 0.0 ? 0.0 : c1 * d[row]) + c2 * dinv[row] * rr;
+      d[row] = dn;
+      y[row] = x[row] + dn;
+    }
+  }
+}
+
+#define HY4_KERNEL(NAME, MODE)                                                                                  \
+  __global__ void __launch_bounds__(kThreads)                                                                 \
+      NAME(int64_t n_big, const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,                  \
+           const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow, \
+           const int64_t* __restrict__ hoff, const double* __restrict__ hv, int64_t n_rest,                  \
+           const int32_t* __restrict__ rest, const int32_t* __restrict__ obase, const int32_t* __restrict__ toff, \
+           const int64_t* __restrict__ rp, const double* __restrict__ val, const double* __restrict__ x,      \
+           const double* __restrict__ b, double* __restrict__ y, double* __restrict__ d,                      \
+           const double* __restrict__ dinv, double c1, double c2) {                                           \
+    if ((int64_t)blockIdx.x < n_big)                                                                          \
+      hy4_body<MODE>(big, gptr, gcol, rptr, grow, hoff, hv, x, b, y, d, dinv, c1, c2);                       \
+    else                                                                                                      \
+      pat_body<16, 2, double, MODE, true>(n_rest, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, 0, 0, rest, n_big); \
+  }
+HY4_KERNEL(hy4_spmv_f64, kSpmv)
+HY4_KERNEL(hy4_resid_f64, kResidual)
+HY4_KERNEL(hy4_cheb_f64, kCheb)
+HY4_KERNEL(hy4_add_f64, kAddSpmv)
+
+template <int MODE>
+struct Hy4Kernel;
+#define HY4_SELECT(MODE, H)                             \
+  template <>                                           \
+  struct Hy4Kernel<MODE> {                              \
+    static constexpr decltype(&H) get() { return &H; }  \
+  };
+HY4_SELECT(kSpmv, hy4_spmv_f64)
+HY4_SELECT(kResidual, hy4_resid_f64)
+HY4_SELECT(kCheb, hy4_cheb_f64)
+HY4_SELECT(kAddSpmv, hy4_add_f64)
+
 // Row-group kernels: one CTA per group of rows with identical column sets; the group's x values
 // are gathered once into shared memory, then every warp streams one row's values from HBM
 // against them (consecutive lanes read consecutive shared words: no bank conflicts).
@@ -531,6 +634,24 @@ void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   note_launch();
 }
 
+template <int MODE>
+void launch_hy4(const DCSR& A, const double* val, const double* x, const double* b, double* y, double* d,
+                const double* dinv, double c1, double c2, cudaStream_t s) {
+  auto k = Hy4Kernel<MODE>::get();
+  const size_t sm = (size_t)A.grp.cpmax * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
+  const int64_t rest_blocks = (A.grp.n_rest * 16 + kThreads - 1) / kThreads;
+  k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
+      A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
+      A.grp.hoff.get(), A.grp.hv64.get(), A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(),
+      A.rp.get(), val, x, b, y, d, dinv, c1, c2);
+  note_launch();
+}
+
 template <int TPR, int U, typename V, int MODE>
 void launch_pat(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
                 int64_t pf, cudaStream_t s) {
@@ -563,11 +684,12 @@ void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* v
                     const V* dinv, V c1, V c2, cudaStream_t s) {
   const int tpr = var.tpr ? var.tpr : default_tpr(avg);
   const bool pat = var.tpr ? var.pat : A.pat.on;
-  bool vector = false;
-  if constexpr (std::is_same<V, float>::value)
-    vector = var.hybrid && var.vector && A.grp.hyb && A.pat.on && A.grp.hvon && val == A.v32.get();
+  bool vector = var.hybrid && var.vector && A.grp.hyb && A.pat.on;
+  if constexpr (std::is_same<V, float>::value) vector = vector && A.grp.hvon && val == A.v32.get();
+  else vector = vector && A.grp.hv64on && val == A.v.get();
   if (vector) {
     if constexpr (std::is_same<V, float>::value) launch_hyv<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
+    else launch_hy4<MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
   } else if (var.hybrid && A.grp.hyb && A.pat.on) {
     launch_hyb<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
   } else if (var.group && A.grp.on) {
@@ -1031,21 +1153,22 @@ void choose_rows(DCSR& A, int form, int threads) {
   for (int prec = 0; prec < 2; ++prec) {
     RowVariant v;
     if (form == 0) {
-      // defaults: FP32 rows on the hybrid form (big row groups with x in shared memory, the
-      // other rows on the pattern form) where there are enough big groups to fill the GPU for
-      // many waves and their rows are long (measured faster from 12^3 elements at p = 6 and on
-      // the 12^3, p = 8 operator; slower at 8^3 and at p = 4), else the pattern form (halved
-      // index traffic); FP64 rows, which are bound by the 1/64-rate FP64 pipe, on CSR with 16
-      // threads per long row
-      v.pat = prec == 1 && A.pat.on;
-      v.hybrid = prec == 1 && A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
-      v.vector = v.hybrid;
-      v.tpr = prec == 1 ? (v.hybrid ? 32 : default_tpr(avg)) : (avg >= 48 ? 16 : default_tpr(avg));
+      // defaults: the vector hybrid form (big row groups from a group-major copy with x in
+      // shared memory, the other rows on the pattern form) where there are enough big groups to
+      // fill the GPU for many waves and their rows are long (measured faster from 12^3 elements
+      // at p = 6 and on the 12^3, p = 8 operator; slower at 8^3 and at p = 4), in both
+      // precisions; else FP32 rows on the pattern form (halved index traffic) and FP64 rows,
+      // which are bound by the 1/64-rate FP64 pipe, on CSR with 16 threads per long row
+      const bool big = A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
+      v.pat = (prec == 1 || big) && A.pat.on;
+      v.hybrid = big;
+      v.vector = big;
+      v.tpr = big ? 32 : prec == 1 ? default_tpr(avg) : (avg >= 48 ? 16 : default_tpr(avg));
     } else {
       v.pat = (form == 2 || form >= 4) && A.pat.on;
       v.group = form == 3 && A.grp.on;
       v.hybrid = (form >= 4) && A.grp.hyb && A.pat.on;
-      v.vector = form == 5 && v.hybrid && prec == 1;
+      v.vector = form == 5 && v.hybrid;
       v.tpr = v.group || v.hybrid ? 32 : default_tpr(avg);
     }
     if (threads && !v.group && !v.hybrid) v.tpr = threads;
@@ -1095,8 +1218,8 @@ void tune_rows(DCSR& A, cudaStream_t s) {
     v.group = true;
     cands.push_back(v);
   }
-  // the hybrid forms, the vector one (FP32 only) on a group-major copy built for the timing
-  const bool vec = A.grp.hyb && A.pat.on && hybrid_vector_build(A, s);
+  // the hybrid forms, the vector ones on group-major copies built for the timing
+  const bool vec = A.grp.hyb && A.pat.on && hybrid_vector_build(A, 1, s) && hybrid_vector_build(A, 0, s);
   if (A.grp.hyb && A.pat.on) {
     RowVariant v;
     v.tpr = 32;
@@ -1110,7 +1233,6 @@ void tune_rows(DCSR& A, cudaStream_t s) {
     float best = 1e30f;
     RowVariant pick;
     for (const RowVariant& v : cands) {
-      if (prec == 0 && v.vector) continue;
       float t = 1e30f;
       for (int rep = 0; rep < 6; ++rep) {
         GIAMG_CUDA(cudaEventRecord(e0, s));
@@ -1136,10 +1258,14 @@ void tune_rows(DCSR& A, cudaStream_t s) {
     }
     (prec == 0 ? A.var64 : A.var32) = pick;
   }
-  if (vec && !A.var32.vector) {  // the copy is kept only for the form that reads it
+  // a copy is kept only for the form that reads it
+  if (vec && !A.var32.vector) {
     A.grp.hv.release();
-    A.grp.hoff.release();
     A.grp.hvon = false;
+  }
+  if (vec && !A.var64.vector) {
+    A.grp.hv64.release();
+    A.grp.hv64on = false;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -315,7 +315,7 @@ def test_row_kernel_forms_match_oracle(form, threads):
     prob, orc = _forms_oracle["p"]
     gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, row_form=form, row_threads=threads)
     try:
-        names = ["csr", "pattern", "groups", "hybrid", "hybrid"][form - 1], \
+        names = ["csr", "pattern", "groups", "hybrid", "vector"][form - 1], \
             ["csr", "pattern", "groups", "hybrid", "vector"][form - 1]
         for prec in (0, 1):
             assert gpu.kernel(0, prec)[1] == names[prec]
