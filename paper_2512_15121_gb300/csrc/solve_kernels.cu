@@ -309,6 +309,17 @@ struct Vec16<float> {
     a[3] = fmaf(v.w, x.w, a[3]);
   }
 };
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int kU = 4;
+  static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
+  // alternate accumulator pairs between consecutive vectors: four FMA chains per lane
+  static __device__ __forceinline__ void fma4(const T& v, const T& x, double* a, int u) {
+    a[2 * (u & 1)] = fma(v.x, x.x, a[2 * (u & 1)]);
+    a[2 * (u & 1) + 1] = fma(v.y, x.y, a[2 * (u & 1) + 1]);
+  }
+};
 template <typename V, int MODE>
 __device__ __forceinline__ void hyv_body(const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,
                                          const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr,
@@ -407,51 +418,49 @@ HYV_SELECT(float, kAddSpmv, hyv_add_f32)
 // one group per warp: every row of a group has the same length, so no lane waits on another
 // row; the reduction is 2 shuffle levels; each lane loads the row's values with 16-byte loads,
 // U at once; and the 8 rows read the same x words from shared memory (broadcasts).
-template <int MODE>
+template <typename V, int MODE>
 __device__ __forceinline__ void hy4_body(const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,
                                          const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr,
                                          const int32_t* __restrict__ grow, const int64_t* __restrict__ hoff,
-                                         const double* __restrict__ hv, const double* __restrict__ x,
-                                         const double* __restrict__ b, double* __restrict__ y,
-                                         double* __restrict__ d, const double* __restrict__ dinv, double c1,
-                                         double c2) {
-  constexpr int U = 4;
+                                         const V* __restrict__ hv, const V* __restrict__ x,
+                                         const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,
+                                         const V* __restrict__ dinv, V c1, V c2) {
+  using VT = typename Vec16<V>::T;
+  constexpr int EV = 16 / sizeof(V), U = 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* xs = reinterpret_cast<double*>(smem_raw);
+  V* xs = reinterpret_cast<V*>(smem_raw);
   const int64_t j = blockIdx.x;
   const int64_t g = big[j];
   const int64_t c0 = gptr[g];
   const int c = (int)(gptr[g + 1] - c0);
-  const int cp = (c + 3) & ~3, nq = cp >> 1;  // double2 per padded row
+  const int cp = (c + 3) & ~3, nq = cp / EV;  // 16-byte vectors per padded row
   const int64_t t0 = rptr[g];
   const int rows = (int)(rptr[g + 1] - t0);
-  const double* src = hv + hoff[j];
-  for (int k = threadIdx.x; k < cp; k += blockDim.x) xs[k] = k < c ? x[__ldg(gcol + c0 + k)] : 0.0;
+  const V* src = hv + hoff[j];
+  for (int k = threadIdx.x; k < cp; k += blockDim.x) xs[k] = k < c ? x[__ldg(gcol + c0 + k)] : V(0);
   __syncthreads();
-  const double2* xq = reinterpret_cast<const double2*>(xs);
+  const VT* xq = reinterpret_cast<const VT*>(xs);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int sub = lane & 3, rw = lane >> 2;
   for (int tb = warp * 8; tb < rows; tb += nw * 8) {
     const int t = tb + rw;
     const bool valid = t < rows;
-    const double2* vr = reinterpret_cast<const double2*>(src + (int64_t)(valid ? t : tb) * cp);
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    const VT* vr = reinterpret_cast<const VT*>(src + (int64_t)(valid ? t : tb) * cp);
+    V a[4] = {V(0), V(0), V(0), V(0)};
     for (int q0 = sub; q0 < nq; q0 += 4 * U) {
-      double2 v[U];
+      VT v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int q = q0 + 4 * u;
-        v[u] = q < nq ? __ldcs(vr + q) : make_double2(0.0, 0.0);
+        v[u] = q < nq ? __ldcs(vr + q) : Vec16<V>::zero();
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int q = q0 + 4 * u;
-        const double2 xv = xq[q < nq ? q : 0];
-        a[2 * (u & 1)] = fma(v[u].x, xv.x, a[2 * (u & 1)]);
-        a[2 * (u & 1) + 1] = fma(v[u].y, xv.y, a[2 * (u & 1) + 1]);
+        Vec16<V>::fma4(v[u], xq[q < nq ? q : 0], a, u);  // a padded slot multiplies zeros
       }
     }
-    double acc = (a[0] + a[1]) + (a[2] + a[3]);
+    V acc = (a[0] + a[1]) + (a[2] + a[3]);
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
     if (!valid || sub != 0) continue;
@@ -463,44 +472,44 @@ __device__ __forceinline__ void hy4_body(const int32_t* __restrict__ big, const 
     } else if (MODE == kResidual) {
       y[row] = b[row] - acc;
     } else {
-      const double rr = b[row] - acc;
-      const double dn = (c1 == 0.0 ? 0.0 : c1 * d[row]) + c2 * dinv[row] * rr;
+      const V rr = b[row] - acc;
+      const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * rr;
       d[row] = dn;
       y[row] = x[row] + dn;
     }
   }
 }
 
-#define HY4_KERNEL(NAME, MODE)                                                                                  \
+#define HY4_KERNEL(NAME, V, MODE, REST)                                                                        \
   __global__ void __launch_bounds__(kThreads)                                                                 \
       NAME(int64_t n_big, const int32_t* __restrict__ big, const int64_t* __restrict__ gptr,                  \
            const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow, \
-           const int64_t* __restrict__ hoff, const double* __restrict__ hv, int64_t n_rest,                  \
+           const int64_t* __restrict__ hoff, const V* __restrict__ hv, int64_t n_rest,                        \
            const int32_t* __restrict__ rest, const int32_t* __restrict__ obase, const int32_t* __restrict__ toff, \
-           const int64_t* __restrict__ rp, const double* __restrict__ val, const double* __restrict__ x,      \
-           const double* __restrict__ b, double* __restrict__ y, double* __restrict__ d,                      \
-           const double* __restrict__ dinv, double c1, double c2) {                                           \
+           const int64_t* __restrict__ rp, const V* __restrict__ val, const V* __restrict__ x,                \
+           const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1,    \
+           V c2) {                                                                                            \
     if ((int64_t)blockIdx.x < n_big)                                                                          \
-      hy4_body<MODE>(big, gptr, gcol, rptr, grow, hoff, hv, x, b, y, d, dinv, c1, c2);                       \
+      hy4_body<V, MODE>(big, gptr, gcol, rptr, grow, hoff, hv, x, b, y, d, dinv, c1, c2);                    \
     else                                                                                                      \
-      pat_body<16, 2, double, MODE, true>(n_rest, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, 0, 0, rest, n_big); \
+      pat_body<REST, 2, V, MODE, true>(n_rest, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, 0, 0, rest, n_big); \
   }
-HY4_KERNEL(hy4_spmv_f64, kSpmv)
-HY4_KERNEL(hy4_resid_f64, kResidual)
-HY4_KERNEL(hy4_cheb_f64, kCheb)
-HY4_KERNEL(hy4_add_f64, kAddSpmv)
+HY4_KERNEL(hy4_spmv_f64, double, kSpmv, 16)
+HY4_KERNEL(hy4_resid_f64, double, kResidual, 16)
+HY4_KERNEL(hy4_cheb_f64, double, kCheb, 16)
+HY4_KERNEL(hy4_add_f64, double, kAddSpmv, 16)
 
-template <int MODE>
+template <typename V, int MODE>
 struct Hy4Kernel;
-#define HY4_SELECT(MODE, H)                             \
+#define HY4_SELECT(V, MODE, H)                          \
   template <>                                           \
-  struct Hy4Kernel<MODE> {                              \
+  struct Hy4Kernel<V, MODE> {                           \
     static constexpr decltype(&H) get() { return &H; }  \
   };
-HY4_SELECT(kSpmv, hy4_spmv_f64)
-HY4_SELECT(kResidual, hy4_resid_f64)
-HY4_SELECT(kCheb, hy4_cheb_f64)
-HY4_SELECT(kAddSpmv, hy4_add_f64)
+HY4_SELECT(double, kSpmv, hy4_spmv_f64)
+HY4_SELECT(double, kResidual, hy4_resid_f64)
+HY4_SELECT(double, kCheb, hy4_cheb_f64)
+HY4_SELECT(double, kAddSpmv, hy4_add_f64)
 
 // Row-group kernels: one CTA per group of rows with identical column sets; the group's x values
 // are gathered once into shared memory, then every warp streams one row's values from HBM
@@ -634,21 +643,22 @@ void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   note_launch();
 }
 
-template <int MODE>
-void launch_hy4(const DCSR& A, const double* val, const double* x, const double* b, double* y, double* d,
-                const double* dinv, double c1, double c2, cudaStream_t s) {
-  auto k = Hy4Kernel<MODE>::get();
-  const size_t sm = (size_t)A.grp.cpmax * sizeof(double);
+template <typename V, int MODE>  // V = double
+void launch_hy4(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  auto k = Hy4Kernel<V, MODE>::get();
+  const size_t sm = (size_t)A.grp.cpmax * sizeof(V);
   static bool attr = false;
   if (!attr) {
     GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     attr = true;
   }
+  const V* hv = A.grp.hv64.get();
   const int64_t rest_blocks = (A.grp.n_rest * 16 + kThreads - 1) / kThreads;
   k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
       A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
-      A.grp.hoff.get(), A.grp.hv64.get(), A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(),
-      A.rp.get(), val, x, b, y, d, dinv, c1, c2);
+      A.grp.hoff.get(), hv, A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(), A.rp.get(), val, x,
+      b, y, d, dinv, c1, c2);
   note_launch();
 }
 
@@ -689,7 +699,7 @@ void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* v
   else vector = vector && A.grp.hv64on && val == A.v.get();
   if (vector) {
     if constexpr (std::is_same<V, float>::value) launch_hyv<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
-    else launch_hy4<MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
+    else launch_hy4<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
   } else if (var.hybrid && A.grp.hyb && A.pat.on) {
     launch_hyb<V, MODE>(A, val, x, b, y, d, dinv, c1, c2, s);
   } else if (var.group && A.grp.on) {
