@@ -307,28 +307,42 @@ __global__ void __launch_bounds__(kRedThreads) bat_dot(int64_t n, int m, const d
   column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
 }
 
-// column sums of the block partials in block order
-__device__ double column_total(const double* partial, int blocks, int j) {
+// Column sums of the block partials, by all kFinishThreads threads of the block: warp w sums the
+// partials of blocks w, w + 32, ... in order, then lane j of warp 0 adds the 32 warp sums in warp
+// order (a fixed order for a fixed grid: bitwise reproducible).  The result is valid in warp 0.
+constexpr int kFinishThreads = 1024;
+__device__ double column_total(const double* partial, int blocks, double (*sh)[33]) {
+  const int j = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double s = 0.0;
-  for (int b = 0; b < blocks; ++b) s += partial[(int64_t)b * 32 + j];
-  return s;
+  for (int b = w; b < blocks; b += nw) s += partial[(int64_t)b * 32 + j];
+  sh[w][j] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0)
+    for (int k = 0; k < nw; ++k) t += sh[k][j];
+  __syncthreads();
+  return t;
 }
 
-__global__ void bat_finish_bb(BatchScalars* sc, const double* partial, int blocks, int m) {
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_bb(BatchScalars* sc, const double* partial, int blocks,
+                                                                 int m) {
+  __shared__ double sh[32][33];
   const int j = threadIdx.x;
+  const double v = column_total(partial, blocks, sh);
   if (j >= m) return;
-  const double v = column_total(partial, blocks, j);
   sc->bb[j] = v;
   sc->rr[j] = v;
   sc->status[j] = 0;
   sc->active[j] = v > 0.0 ? 1 : 0;
 }
 
-__global__ void bat_finish_rz(BatchScalars* sc, const double* partial, int blocks, int m, int first, int flexible) {
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_rz(BatchScalars* sc, const double* partial, int blocks,
+                                                                 int m, int first, int flexible) {
+  __shared__ double sh[32][33];
   const int j = threadIdx.x;
+  const double rz = column_total(partial, blocks, sh);
+  const double zd = column_total(partial + (int64_t)blocks * 32, blocks, sh);
   if (j >= m) return;
-  const double rz = column_total(partial, blocks, j);
-  const double zd = column_total(partial + (int64_t)blocks * 32, blocks, j);
   if (!sc->active[j]) {
     sc->beta[j] = 0.0;
     return;
@@ -338,10 +352,12 @@ __global__ void bat_finish_rz(BatchScalars* sc, const double* partial, int block
   sc->rho[j] = rz;
 }
 
-__global__ void bat_finish_pq(BatchScalars* sc, const double* partial, int blocks, int m) {
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_pq(BatchScalars* sc, const double* partial, int blocks,
+                                                                 int m) {
+  __shared__ double sh[32][33];
   const int j = threadIdx.x;
+  const double pq = column_total(partial, blocks, sh);
   if (j >= m) return;
-  const double pq = column_total(partial, blocks, j);
   sc->pq[j] = pq;
   if (!sc->active[j]) {
     sc->alpha[j] = 0.0;
@@ -352,10 +368,12 @@ __global__ void bat_finish_pq(BatchScalars* sc, const double* partial, int block
 }
 
 // after the update: record ||r_j||^2 and retire columns that reached the tolerance
-__global__ void bat_finish_rr(BatchScalars* sc, const double* partial, int blocks, int m) {
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_rr(BatchScalars* sc, const double* partial, int blocks,
+                                                                 int m) {
+  __shared__ double sh[32][33];
   const int j = threadIdx.x;
+  const double rr = column_total(partial, blocks, sh);
   if (j >= m) return;
-  const double rr = column_total(partial, blocks, j);
   if (!sc->active[j]) return;
   sc->rr[j] = rr;
   if (!(rr == rr) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
@@ -528,13 +546,13 @@ int batch_reduction_blocks() { return kBatBlocks; }
 
 void bat_pcg_init(int64_t n, int m, const double* B, double* X, double* R, double* partial, void* sc, cudaStream_t s) {
   { bat_init<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, B, X, R, partial); note_launch(); }
-  { bat_finish_bb<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
+  { bat_finish_bb<<<1, kFinishThreads, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
 void bat_pcg_rz(int64_t n, int m, const double* R, const double* Z, const double* Rold, int flexible, int first,
                 double* partial, void* sc, cudaStream_t s) {
   { bat_dot_rz<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, R, Z, Rold, flexible, partial); note_launch(); }
-  { bat_finish_rz<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m, first, flexible); note_launch(); }
+  { bat_finish_rz<<<1, kFinishThreads, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m, first, flexible); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
 void bat_pcg_update_p(int64_t n, int m, const double* Z, double* P, const void* sc, int first, cudaStream_t s) {
@@ -543,13 +561,13 @@ void bat_pcg_update_p(int64_t n, int m, const double* Z, double* P, const void* 
 }
 void bat_pcg_pq(int64_t n, int m, const double* P, const double* Q, double* partial, void* sc, cudaStream_t s) {
   { bat_dot<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, P, Q, partial); note_launch(); }
-  { bat_finish_pq<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
+  { bat_finish_pq<<<1, kFinishThreads, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
 void bat_pcg_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, double* Rold,
                        int flexible, double* partial, void* sc, cudaStream_t s) {
   { bat_update_xr<<<kBatBlocks, kRedThreads, 0, s>>>(n, m, P, Q, X, R, Rold, flexible, (const BatchScalars*)sc, partial); note_launch(); }
-  { bat_finish_rr<<<1, 32, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
+  { bat_finish_rr<<<1, kFinishThreads, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
 void bat_graph_start_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle first,

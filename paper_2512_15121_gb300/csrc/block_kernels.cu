@@ -255,12 +255,18 @@ __global__ void __launch_bounds__(kRedThreads) update_xr_kernel(int64_t n, int m
 // ||r_j||^2 in block order; a column stays active until it meets the tolerance (or, with a
 // forced count, while it is non-zero); NaN, or no direction left while a column is active, is a
 // breakdown.
-__global__ void finish_rr_kernel(BatchScalarsHost* sc, const BlockState* st, const double* partial, int blocks,
-                                 int m) {
-  const int j = threadIdx.x;
-  if (j >= m) return;
+__global__ void __launch_bounds__(1024) finish_rr_kernel(BatchScalarsHost* sc, const BlockState* st,
+                                                         const double* partial, int blocks, int m) {
+  // warp w sums blocks w, w + 32, ... in order; lane j of warp 0 adds the warp sums in order
+  __shared__ double sh[32][33];
+  const int j = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double part = 0.0;
+  for (int b = w; b < blocks; b += 32) part += partial[(int64_t)b * 32 + j];
+  sh[w][j] = part;
+  __syncthreads();
+  if (w != 0 || j >= m) return;
   double rr = 0.0;
-  for (int b = 0; b < blocks; ++b) rr += partial[(int64_t)b * 32 + j];
+  for (int k = 0; k < 32; ++k) rr += sh[k][j];
   sc->rr[j] = rr;
   const bool open = sc->bb[j] > 0.0 && (sc->force || !(rr <= sc->tol2 * sc->bb[j]));
   sc->active[j] = open ? 1 : 0;
@@ -326,7 +332,7 @@ void blk_coef(int m, int mode, double tau, BlockState* st, cudaStream_t s) {
 void blk_update_xr(int64_t n, int m, const double* P, const double* Q, double* X, double* R, const BlockState* st,
                    double* partial, void* sc, cudaStream_t s) {
   { update_xr_kernel<<<kRowBlocks, kRedThreads, 0, s>>>(n, m, P, Q, X, R, st, partial); note_launch(); }
-  { finish_rr_kernel<<<1, 32, 0, s>>>((BatchScalarsHost*)sc, st, partial, kRowBlocks, m); note_launch(); }
+  { finish_rr_kernel<<<1, 1024, 0, s>>>((BatchScalarsHost*)sc, st, partial, kRowBlocks, m); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
 
