@@ -151,6 +151,21 @@ GIAMG_API int giamg_solve(giamg_handle h, const double* b, double* x, double rto
 GIAMG_API int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double* b, double* x,
                    double rtol, int* iters, double* relres);
 
+/* giamg_solve enqueued on the handle's stream without any host synchronisation (the solve of
+ * Algorithm 1's PCG loop as one CUDA graph with its stopping rule on the device).  Needs
+ * device_ptrs = 1 and graphs != 0; force_iters and max_iter from the options (force_iters <=
+ * max_iter).
+ *   b, x: device arrays of n values (caller-owned; b may be reused once the stream passes the call).
+ *   iters, relres, status: device pointers (each may be NULL) written when the stream reaches the
+ *     end of the solve: the iteration count, ||r||/||b|| (0 for b = 0), and GIAMG_OK,
+ *     GIAMG_ERR_MAXITER or GIAMG_ERR_BREAKDOWN with the rules of giamg_solve.
+ * The caller synchronises the stream before reading them.  The first call for a precision
+ * captures the graph, which synchronises the stream once.  The return value reports argument
+ * and launch errors only.  giamg_solve_stats keeps the true residual of an asynchronous solve
+ * but not its history. */
+GIAMG_API int giamg_solve_async(giamg_handle h, int precision, const double* b, double* x, double rtol, int* iters,
+                                double* relres, int* status);
+
 /* m independent solves A X_j = B_j sharing every matrix pass (multi-right-hand-side PCG: one
  * CG recurrence per column, each with its own alpha, beta and stopping test; the products and
  * the V-cycle work on all columns at once, so the matrix is read once per m solves).

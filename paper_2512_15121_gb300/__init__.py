@@ -24,7 +24,7 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 
 # every entry point the header declares (checked by the CPU tests against the .so)
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
-           "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block",
+           "giamg_solve_async", "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
            "giamg_level_rho", "giamg_set_cheb_degree", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
@@ -74,6 +74,7 @@ def lib():
         L.giamg_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
         L.giamg_solve_batch_ex.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
         L.giamg_solve_block.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
+        L.giamg_solve_async.argtypes = [vp, i32, vp, vp, dbl, vp, vp, vp]
         L.giamg_num_levels.argtypes = [vp, P(i32)]
         L.giamg_level_info.argtypes = [vp, i32, P(i32), P(i64), P(i64), P(i32), P(i64), P(i64)]
         L.giamg_export_level.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -232,6 +233,21 @@ class Solver:
             _check(rc)
         self.last_status = rc
         return x, it, rr
+
+    def solve_async(self, b, rtol=1e-8, precision=None, x=None):
+        """Enqueue a solve on the handle's stream (device mode, graphs on).  Returns device tensors
+        (x, iters, relres, status), valid once the stream has passed the solve."""
+        import torch
+        if not self.device:
+            raise GiamgError(GIAMG_ERR_ARG, "solve_async needs device=True")
+        b = b.to("cuda", torch.float64).contiguous()
+        x = torch.empty_like(b) if x is None else x
+        it = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rr = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        prec = self.opts.precision if precision is None else precision
+        _check(lib().giamg_solve_async(self._h, prec, _ptr(b), _ptr(x), rtol, _ptr(it), _ptr(rr), _ptr(st)))
+        return x, it, rr, st
 
     def solve_batch(self, B, rtol=1e-8, precision=None, force_iters=None, X=None, block=False):
         """B: n x m (row-major, m <= 32).  Returns (X, iters[m], relres[m]).  block=True: the

@@ -1098,6 +1098,38 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
   return GIAMG_OK;
 }
 
+// The solve enqueued on the handle's stream with no host synchronisation: the captured graph
+// (captured here on first use, which synchronises once), parameters passed as kernel arguments,
+// results written to device memory by a kernel after the graph.  b, x and the results are
+// device pointers (device_ptrs mode).
+int solve_async_impl(Ctx& C, int precision, const double* b, double* x, double rtol, int* iters, double* relres,
+                     int* status) {
+  Hierarchy& H = *C.H;
+  cudaStream_t s = H.stream;
+  const int64_t n = H.n;
+  GIAMG_CHECK(b && x, GIAMG_ERR_ARG, "b and x are required");
+  GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+  GIAMG_CHECK(rtol >= 0.0, GIAMG_ERR_ARG, "rtol must be non-negative");
+  GIAMG_CHECK(H.opt.device_ptrs != 0, GIAMG_ERR_ARG, "an asynchronous solve needs device pointers (device_ptrs = 1)");
+  GIAMG_CHECK(H.opt.graphs != 0, GIAMG_ERR_ARG, "an asynchronous solve runs the captured graph (graphs != 0)");
+  GIAMG_CHECK(!H.prof.on, GIAMG_ERR_ARG, "an asynchronous solve cannot run with profiling enabled");
+  const int force = H.opt.force_iters;
+  const int limit = force > 0 ? force : H.opt.max_iter;
+  GIAMG_CHECK(limit <= H.opt.max_iter, GIAMG_ERR_ARG, "force_iters beyond max_iter needs the synchronous solve");
+  SolveGraph& SG = H.graph[precision];
+  if (!SG.exec) capture_solve(C, precision);
+  GIAMG_CUDA(cudaMemcpyAsync(H.gb.get(), b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  pcg_graph_params(H.gst.get(), rtol, limit, force > 0 ? 1 : 0, s);
+  GIAMG_CUDA(cudaGraphLaunch(SG.exec, s));
+  pcg_graph_results(H.gst.get(), H.ghist.get(), iters, relres, status, s);
+  GIAMG_CUDA(cudaMemcpyAsync(x, H.gx.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  vec_copy(n, H.gb.get(), H.tmp.get(), s);  // b and x for the true residual of giamg_solve_stats
+  vec_copy(n, H.gx.get(), H.xw.get(), s);
+  H.hist.clear();  // the history of an asynchronous solve stays on the device
+  g_launches.fetch_add(SG.n_init);  // the iterations' kernels are not known on the host
+  return GIAMG_OK;
+}
+
 Ctx* ctx_of(giamg_handle h) {
   GIAMG_CHECK(h != nullptr, GIAMG_ERR_ARG, "NULL handle");
   return reinterpret_cast<Ctx*>(h);
@@ -1187,6 +1219,11 @@ int giamg_solve(giamg_handle h, const double* b, double* x, double rtol, int* it
 int giamg_solve_ex(giamg_handle h, int precision, int force_iters, const double* b, double* x, double rtol, int* iters,
                    double* relres) {
   return guarded([&] { return solve_impl(*ctx_of(h), precision, force_iters, b, x, rtol, iters, relres); });
+}
+
+int giamg_solve_async(giamg_handle h, int precision, const double* b, double* x, double rtol, int* iters,
+                      double* relres, int* status) {
+  return guarded([&] { return solve_async_impl(*ctx_of(h), precision, b, x, rtol, iters, relres, status); });
 }
 
 int giamg_solve_batch(giamg_handle h, int m, const double* B, double* X, double rtol, int* iters, double* relres) {

@@ -45,7 +45,40 @@ __global__ void graph_check_kernel(const Scalars* __restrict__ sc, GraphState* _
   cudaGraphSetConditional(more, cont);
 }
 
+// an asynchronous solve's parameters, from kernel arguments (a host buffer could be overwritten
+// by the next call before the copy ran)
+__global__ void graph_params_kernel(GraphState* __restrict__ st, double rtol, int limit, int force) {
+  st->rtol = rtol;
+  st->limit = limit;
+  st->force = force;
+  st->it = 0;
+  st->status = 0;
+}
+
+// an asynchronous solve's results, with the synchronous call's rules: b = 0 gives relres 0 and
+// no iteration; the limit reached above rtol (iteration count not forced) is GIAMG_ERR_MAXITER
+__global__ void graph_results_kernel(const GraphState* __restrict__ st, const double* __restrict__ hist,
+                                     int* iters, double* relres, int* status) {
+  const bool zero = hist[0] == 0.0;
+  int code = st->status;
+  if (code == GIAMG_OK && !zero && !st->force && !(st->relres <= st->rtol)) code = GIAMG_ERR_MAXITER;
+  if (iters) *iters = st->it;
+  if (relres) *relres = zero ? 0.0 : st->relres;
+  if (status) *status = code;
+}
+
 }  // namespace
+
+void pcg_graph_params(GraphState* st, double rtol, int limit, int force, cudaStream_t s) {
+  { graph_params_kernel<<<1, 1, 0, s>>>(st, rtol, limit, force); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+void pcg_graph_results(const GraphState* st, const double* hist, int* iters, double* relres, int* status,
+                       cudaStream_t s) {
+  { graph_results_kernel<<<1, 1, 0, s>>>(st, hist, iters, relres, status); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
 
 void pcg_graph_start(const Scalars* sc, GraphState* st, double* hist, cudaGraphConditionalHandle first,
                      cudaGraphConditionalHandle loop, cudaStream_t s) {

@@ -343,6 +343,10 @@ void pcg_update_xr(int64_t n, const double* p, const double* q, double* x, doubl
                    const Scalars* sc, double* partial, cudaStream_t s);
 void pcg_finish_rr(Scalars* sc, const double* partial, cudaStream_t s);
 // control of the graph-captured loop (graph_kernels.cu)
+// asynchronous solve: parameters into the graph state; results (device pointers, each may be NULL)
+void pcg_graph_params(GraphState* st, double rtol, int limit, int force, cudaStream_t s);
+void pcg_graph_results(const GraphState* st, const double* hist, int* iters, double* relres, int* status,
+                       cudaStream_t s);
 void pcg_graph_start(const Scalars* sc, GraphState* st, double* hist, cudaGraphConditionalHandle first,
                      cudaGraphConditionalHandle loop, cudaStream_t s);
 void pcg_graph_check(const Scalars* sc, GraphState* st, double* hist, cudaGraphConditionalHandle loop,

@@ -538,3 +538,49 @@ def test_tune_cheb_degree():
         assert timings[2].iterations <= timings[0].iterations
     finally:
         s.close()
+
+
+def test_async_solve_equals_the_synchronous_graph_solve():
+    """giamg_solve_async enqueues the captured solve with no host round trip; its results, read
+    after a stream synchronisation, are those of giamg_solve bit for bit."""
+    prob, orc, _, k = setup_case("cube4_p4")
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=2)
+    lim = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=2, max_iter=2)
+    try:
+        b = dev(prob.b)
+        b2 = dev(prob.rhs("fourier", 77))
+        for precision in (0, 1):
+            x, it, rr = gpu.solve(b, rtol=1e-8, precision=precision)
+            x2, it2, rr2 = gpu.solve(b2, rtol=1e-8, precision=precision)
+            # two solves queued back to back, then one synchronisation
+            ya, ita, rra, sta = gpu.solve_async(b, rtol=1e-8, precision=precision)
+            yb, itb, rrb, stb = gpu.solve_async(b2, rtol=1e-8, precision=precision)
+            torch.cuda.synchronize()
+            assert torch.equal(ya, x) and int(ita) == it and float(rra) == rr and int(sta) == g.GIAMG_OK
+            assert torch.equal(yb, x2) and int(itb) == it2 and float(rrb) == rr2 and int(stb) == g.GIAMG_OK
+        _, tr = gpu.stats(0)
+        assert tr <= 1.5e-8
+        # b = 0: no iteration
+        z, itz, rrz, stz = gpu.solve_async(dev(np.zeros(prob.n)), rtol=1e-8)
+        torch.cuda.synchronize()
+        assert int(itz) == 0 and float(rrz) == 0.0 and int(stz) == g.GIAMG_OK and torch.count_nonzero(z) == 0
+        # the iteration limit: MAXITER on the device, as giamg_solve reports it
+        xl, itl, rrl = lim.solve(b, rtol=1e-14)
+        za, ita, rra, sta = lim.solve_async(b, rtol=1e-14)
+        torch.cuda.synchronize()
+        assert lim.last_status == g.GIAMG_ERR_MAXITER == int(sta) and int(ita) == itl == 2
+        assert torch.equal(za, xl) and float(rra) == rrl
+    finally:
+        gpu.close()
+        lim.close()
+    # host arrays or the host loop: refused
+    host_mode = g.Solver.from_problem(prob, device=False, cheb_degree=k)
+    loop = g.Solver.from_problem(prob, device=True, cheb_degree=k, graphs=0)
+    try:
+        with pytest.raises(g.GiamgError):
+            host_mode.solve_async(torch.zeros(prob.n, dtype=torch.float64, device="cuda"))
+        with pytest.raises(g.GiamgError):
+            loop.solve_async(dev(prob.b))
+    finally:
+        host_mode.close()
+        loop.close()
