@@ -689,6 +689,20 @@ void launch_csr(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
 // default threads per row from the average row length (before or without tuning)
 inline int default_tpr(double avg) { return avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4; }
 
+// threads per row for the automatic choice: about `per_lane` values per lane (fewer lanes per row
+// mean fewer shuffle-reduction levels per row, which cost FP64 rows pipe time); a level whose
+// rows then give fewer than 2^18 threads (under one wave of the GPU's 311,296) is latency-bound
+// and keeps at least the lanes of the length rule default_tpr.  Measured in the solve: the 24^3
+// p = 4 finest level (191 values per row) is fastest with 8 lanes per row in FP32 (16% faster
+// solve than 32) and 4 in FP64; the 12^3 p = 8 p = 4-level (205) with 16; levels of a few
+// thousand rows with the length rule.
+inline int auto_tpr(int64_t n, double avg, double per_lane) {
+  int t = 4;
+  while (t < 32 && avg / t > per_lane) t *= 2;
+  if ((double)n * t < (double)(1 << 18)) t = std::max(t, default_tpr(avg));
+  return t;
+}
+
 template <typename V, int MODE>
 void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* val, const V* x, const V* b, V* y, V* d,
                     const V* dinv, V c1, V c2, cudaStream_t s) {
@@ -1168,12 +1182,12 @@ void choose_rows(DCSR& A, int form, int threads) {
       // fill the GPU for many waves and their rows are long (measured faster from 12^3 elements
       // at p = 6 and on the 12^3, p = 8 operator; slower at 8^3 and at p = 4), in both
       // precisions; else FP32 rows on the pattern form (halved index traffic) and FP64 rows,
-      // which are bound by the 1/64-rate FP64 pipe, on CSR with 16 threads per long row
+      // which are bound by the 1/64-rate FP64 pipe, on CSR, threads per row by auto_tpr
       const bool big = A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
       v.pat = (prec == 1 || big) && A.pat.on;
       v.hybrid = big;
       v.vector = big;
-      v.tpr = big ? 32 : prec == 1 ? default_tpr(avg) : (avg >= 48 ? 16 : default_tpr(avg));
+      v.tpr = big ? 32 : auto_tpr(A.n, avg, prec == 1 ? 24.0 : 48.0);
     } else {
       v.pat = (form == 2 || form >= 4) && A.pat.on;
       v.group = form == 3 && A.grp.on;
