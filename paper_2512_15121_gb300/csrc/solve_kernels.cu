@@ -312,7 +312,6 @@ struct Vec16<float> {
 template <>
 struct Vec16<double> {
   using T = double2;
-  static constexpr int kU = 4;
   static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
   // alternate accumulator pairs between consecutive vectors: four FMA chains per lane
   static __device__ __forceinline__ void fma4(const T& v, const T& x, double* a, int u) {
