@@ -52,6 +52,10 @@ def test_argument_errors_without_a_gpu(lib):
                            ctypes.byref(h)) == g.GIAMG_ERR_ARG
     assert lib.giamg_solve(None, None, None, 1e-8, None, None) == g.GIAMG_ERR_ARG
     assert b"handle" in lib.giamg_last_error()
+    for rc in (lib.giamg_solve_async(None, 0, None, None, 1e-8, None, None, None),
+               lib.giamg_solve_block(None, 0, 0, 4, None, None, 1e-8, None, None),
+               lib.giamg_solve_batch_ex(None, 0, 0, 4, None, None, 1e-8, None, None)):
+        assert rc == g.GIAMG_ERR_ARG and b"handle" in lib.giamg_last_error()
     assert lib.giamg_free(None) == g.GIAMG_OK
     assert lib.giamg_launch_count(None) == g.GIAMG_ERR_ARG
     c = ctypes.c_int64(-1)
