@@ -77,6 +77,68 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// FP32, m > 16 columns: one warp per work item of two rows of one row group (or one row), lane j
+// owning column j.  The two rows have the same columns (the group's column list), so each
+// gathered X row (128 bytes) serves both; values are those of each row's CSR entries.  The
+// products are summed in bat_rows' order (even and odd entries in two chains).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+    bat_pairs(int64_t n_items, const int32_t* __restrict__ ia, const int32_t* __restrict__ ib,
+              const int32_t* __restrict__ ig, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gcol,
+              const int64_t* __restrict__ rp, int m, const float* __restrict__ val, const float* __restrict__ X,
+              const float* __restrict__ B, float* __restrict__ Y, float* __restrict__ D,
+              const float* __restrict__ dinv, float c1, float c2) {
+  const int64_t item = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const int j = threadIdx.x & 31;
+  if (item >= n_items || j >= m) return;
+  const int64_t ra = ia[item], rb = ib[item], g = ig[item];
+  const int64_t c0 = gptr[g];
+  const int len = (int)(gptr[g + 1] - c0);
+  const int32_t* __restrict__ cols = gcol + c0;
+  const float* __restrict__ va = val + rp[ra];
+  const float* __restrict__ vb = val + rp[rb >= 0 ? rb : ra];
+  const float* __restrict__ xc = X + j;
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  int k = 0;
+  if (rb >= 0) {
+    for (; k + 1 < len; k += 2) {
+      const float x0 = xc[(int64_t)__ldg(cols + k) * m], x1 = xc[(int64_t)__ldg(cols + k + 1) * m];
+      a0 = fmaf(__ldg(va + k), x0, a0);
+      a1 = fmaf(__ldg(va + k + 1), x1, a1);
+      b0 = fmaf(__ldg(vb + k), x0, b0);
+      b1 = fmaf(__ldg(vb + k + 1), x1, b1);
+    }
+    if (k < len) {
+      const float x0 = xc[(int64_t)__ldg(cols + k) * m];
+      a0 = fmaf(__ldg(va + k), x0, a0);
+      b0 = fmaf(__ldg(vb + k), x0, b0);
+    }
+  } else {
+    for (; k + 1 < len; k += 2) {
+      a0 = fmaf(__ldg(va + k), xc[(int64_t)__ldg(cols + k) * m], a0);
+      a1 = fmaf(__ldg(va + k + 1), xc[(int64_t)__ldg(cols + k + 1) * m], a1);
+    }
+    if (k < len) a0 = fmaf(__ldg(va + k), xc[(int64_t)__ldg(cols + k) * m], a0);
+  }
+  auto finish = [&](int64_t row, float acc) {
+    const int64_t o = row * m + j;
+    if (MODE == kSpmm) {
+      Y[o] = acc;
+    } else if (MODE == kAdd) {
+      Y[o] += acc;
+    } else if (MODE == kResid) {
+      Y[o] = B[o] - acc;
+    } else {
+      const float r = B[o] - acc;
+      const float dn = (c1 == 0.f ? 0.f : c1 * D[o]) + c2 * dinv[row] * r;
+      D[o] = dn;
+      Y[o] = X[o] + dn;
+    }
+  };
+  finish(ra, a0 + a1);
+  if (rb >= 0) finish(rb, b0 + b1);
+}
+
 template <int G, typename V, int MODE, bool PAT>
 void launch_g(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y, V* D, const V* dinv, V c1, V c2,
               cudaStream_t s) {
@@ -91,6 +153,16 @@ void launch_bat(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y
   if (A.n == 0) return;
   const bool own = val == (sizeof(V) == 8 ? (const V*)A.v.get() : (const V*)A.v32.get());
   const bool pat = own && A.pat.on;
+  if constexpr (sizeof(V) == 4) {
+    if (pat && A.grp.pon && m > 16) {
+      bat_pairs<MODE><<<grid_for(A.grp.n_items * 32, kThreads), kThreads, 0, s>>>(
+          A.grp.n_items, A.grp.item_a.get(), A.grp.item_b.get(), A.grp.item_g.get(), A.grp.gptr.get(),
+          A.grp.gcol.get(), A.rp.get(), m, val, X, B, Y, D, dinv, c1, c2);
+      note_launch();
+      GIAMG_CUDA(cudaGetLastError());
+      return;
+    }
+  }
   const int G = m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
 #define BAT_CASE(GG)                                                              \
   case GG:                                                                        \

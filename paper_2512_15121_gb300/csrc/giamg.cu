@@ -507,6 +507,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
         pattern_build(L.A, s, 1 << 16, 1 << 24);
         clk.mark("row patterns", (int)l);
         groups_build(L.A, s, 1 << 22);
+        batch_pairs_build(L.A, s);
         clk.mark("row groups, hybrid", (int)l);
       }
       if (opt.autotune) tune_rows(L.A, s);

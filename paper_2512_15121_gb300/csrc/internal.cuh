@@ -107,6 +107,11 @@ struct Groups {
   DBuf<int64_t> hoff;           // start of big group j's block (values), n_big + 1 entries
   DBuf<float> hv;
   DBuf<double> hv64;
+  // multi-right-hand-side FP32 products: work items of two rows of one group (or one row), so a
+  // warp applies each gathered row of X to both; a group's rows are paired in list order
+  bool pon = false;
+  int64_t n_items = 0;
+  DBuf<int32_t> item_a, item_b, item_g;  // rows (item_b = -1 for a single row) and their group
 };
 constexpr int kHybridRows = 16;
 
@@ -442,6 +447,8 @@ void tune_rows(DCSR& A, cudaStream_t s);
 // (precision 1, A.v32) or FP64 (precision 0, A.v) values; needs the hybrid lists; false if the
 // form does not apply
 bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s);
+// the row-pair work items of the multi-right-hand-side FP32 products (needs the row groups)
+bool batch_pairs_build(DCSR& A, cudaStream_t s);
 // set A.var64 / A.var32 from forced options or the defaults measured best inside the solve
 void choose_rows(DCSR& A, int form, int threads);
 // prefetch_rows -1: automatic, 0: off, > 0: distance in rows; chains 0: keep, else 2, 4 or 8

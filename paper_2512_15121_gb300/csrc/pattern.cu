@@ -458,6 +458,38 @@ __global__ void hv_gather(const int32_t* __restrict__ big, const int64_t* __rest
 }
 }  // namespace
 
+bool batch_pairs_build(DCSR& A, cudaStream_t s) {
+  Groups& R = A.grp;
+  R.pon = false;
+  if (!R.on) return false;
+  const int64_t G = R.n_groups, n = A.n;
+  std::vector<int64_t> rp_h(G + 1);
+  std::vector<int32_t> rows(n);
+  GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaMemcpyAsync(rows.data(), R.grow.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> ia, ib, ig;
+  ia.reserve(n / 2 + G);
+  for (int64_t g = 0; g < G; ++g) {
+    for (int64_t t = rp_h[g]; t < rp_h[g + 1]; t += 2) {
+      ia.push_back(rows[t]);
+      ib.push_back(t + 1 < rp_h[g + 1] ? rows[t + 1] : -1);
+      ig.push_back((int32_t)g);
+    }
+  }
+  const size_t ni = ia.size();
+  R.item_a.alloc(ni, s);
+  R.item_b.alloc(ni, s);
+  R.item_g.alloc(ni, s);
+  GIAMG_CUDA(cudaMemcpyAsync(R.item_a.get(), ia.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+  GIAMG_CUDA(cudaMemcpyAsync(R.item_b.get(), ib.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+  GIAMG_CUDA(cudaMemcpyAsync(R.item_g.get(), ig.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  R.n_items = (int64_t)ni;
+  R.pon = true;
+  return true;
+}
+
 bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s) {
   Groups& R = A.grp;
   if (precision == 1 ? R.hvon : R.hv64on) return true;  // built already (by the setup-time tuner)
