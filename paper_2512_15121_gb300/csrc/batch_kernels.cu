@@ -4,7 +4,9 @@
 //
 //   SpMM row kernels: G = next power of two >= m lanes per row, lane j holds column j; each
 //     nonzero (value, column) is loaded once per row and applied to the m gathered values
-//     X[col * m + j] (one coalesced segment), so the matrix is read once per m solves.
+//     X[col * m + j] (one coalesced segment), so the matrix is read once per m solves.  FP32
+//     with m > 16 (the V-cycle of a wide batch): two rows of one row group per warp, so each
+//     gathered X row serves both (bat_pairs).
 //   p-transfers: the element contractions of the single-vector path with a column index.
 //   coarsest solve: X = A^-1 B with the dense inverse.
 //   CG updates and dot products per column, reduced in a fixed order (reproducible bits).
