@@ -6,14 +6,17 @@
                    Table 1's 4 levels and 27/343 coarsest level
   SpGEMM           scipy's product (values) and the boolean product (pattern)
   MIS-2 (Sec. 2.5) brute-force greedy MIS of the squared graph; validity; hand-worked path
-  aggregates       cover, one root each, connected; hand-worked path
+  aggregates       cover, one root each, connected; hand-worked paths (one where the second
+                   phase decides between two aggregates)
   SPAI-0           minimiser of ||e_i - m a_i|| row by row
   Lanczos          dense eigenvalues (numpy) within 1%
   Chebyshev        closed-form damping T_k((theta - mu)/delta) / T_k(theta/delta)
   Cholesky         numpy's factor and solve
-  V-cycle (Alg. 1) symmetric as an operator
+  V-cycle (Alg. 1) symmetric as an operator; the FP32 V-cycle applies the FP64 operator to
+                   FP32 rounding
   PCG              dense direct solve; Dirichlet entries converge to zero; fewer iterations
-                   than Jacobi-preconditioned CG; thread-count independence
+                   than Jacobi-preconditioned CG; thread-count independence; flexible CG
+                   follows the standard recurrence to rounding with a fixed V-cycle
   block PCG        m = 1 is the scalar PCG; finite termination; the brute-force energy
                    projection onto the block Krylov space; dependent and zero columns; energy
                    error never above each column's own PCG; the Gram pseudo-inverse
@@ -259,6 +262,20 @@ def test_mis2_hand_worked_path():
     assert agg.tolist() == [int(v) for v in g["aggregates"]] and na == 3
 
 
+
+def test_aggregates_hand_worked_second_phase():
+    """Two paths whose middle nodes lie at distance 2 from two roots: the second phase of the
+    aggregation (Sec. 2.5, smallest phase-1 aggregate id) decides where they go."""
+    g = read_golden("aggregates_phase2.txt")
+    n = int(g["n"][0])
+    edges = [tuple(map(int, e.split("-"))) for e in g["edges"]]
+    rp, ci, _ = _graph_from_edges(n, edges)
+    ins, rounds = oracle.mis2(rp, ci, hash_kind=1)
+    assert sorted(np.flatnonzero(ins).tolist()) == [int(v) for v in g["roots"]]
+    assert rounds == int(g["rounds"][0])
+    agg, na = oracle.aggregate(rp, ci, ins)
+    assert agg.tolist() == [int(v) for v in g["aggregates"]] and na == len(g["roots"])
+
 @pytest.mark.parametrize("seed", range(40))
 @pytest.mark.parametrize("hash_kind", [0, 1])
 def test_mis2_equals_greedy_on_squared_graph(seed, hash_kind):
@@ -402,6 +419,19 @@ def test_vcycle_is_symmetric(n, p, mesh, k):
     assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
 
 
+@pytest.mark.parametrize("n,p,mesh", [(4, 4, "jitter"), (8, 2, "uniform"), (3, 6, "jitter")])
+def test_fp32_vcycle_is_the_fp64_operator_to_fp32_rounding(n, p, mesh):
+    """The FP32 V-cycle (FP32 values, smoother and transfers; coarsest solve in FP64) is the same
+    linear operator as the FP64 one, so the two agree to FP32 rounding (unit roundoff 6e-8,
+    a few hundred roundings deep): a wrong coefficient in the FP32 smoother or transfer moves
+    the result by O(1)."""
+    prob = fegen.make(n, p, mesh=mesh, lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    rng = np.random.default_rng(5)
+    for r in (prob.b, rng.standard_normal(prob.n)):
+        z64, z32 = H.vcycle(r, 0), H.vcycle(r, 1)
+        assert np.linalg.norm(z32 - z64) <= 1e-5 * np.linalg.norm(z64)
+
 @pytest.mark.parametrize("n,p,mesh,lam", [(2, 2, "uniform", 1.0), (2, 4, "jitter", 10.0), (3, 3, "graded", 1000.0),
                                           (8, 2, "jitter", 0.0)])
 def test_pcg_matches_dense_direct_solve(n, p, mesh, lam):
@@ -445,6 +475,10 @@ def test_force_iters_and_flexible_cg():
     # flexible CG with the same symmetric V-cycle follows PCG to rounding
     xfl, itfl, rrfl, histfl, _ = H.solve(prob.b, rtol=1e-8, flexible=1)
     assert abs(itfl - it) <= 1
+    # with a fixed SPD preconditioner <z_{k+1}, r_k> = 0, so the flexible beta equals the
+    # standard one in exact arithmetic: the residual histories agree to rounding
+    m = min(len(hist), len(histfl))
+    assert np.allclose(histfl[:m], hist[:m], rtol=1e-8, atol=0.0)
     # FP32 V-cycle inside FP64 flexible CG reaches the same tolerance
     x32, it32, rr32, _, st32 = H.solve(prob.b, rtol=1e-8, precision=1)
     assert st32 == "ok" and rr32 <= 1e-8
