@@ -73,6 +73,8 @@ def _lib():
             L.fegen_l2_error.restype = ctypes.c_double
             L.fegen_free.argtypes = [vp]
             L.fegen_num_threads.restype = ctypes.c_int
+            L.fegen_gauss_rule.argtypes = [ctypes.c_int, vp, vp]
+            L.fegen_gauss_rule.restype = ctypes.c_int
             _lib_handle = L
     return _lib_handle
 
@@ -222,3 +224,11 @@ def workload(name: str, **over) -> Problem:
 
 def num_threads() -> int:
     return _lib().fegen_num_threads()
+
+
+def gauss_rule(n: int):
+    """The n-point Gauss-Legendre rule the assembly integrates with: (nodes, weights) on [-1, 1]."""
+    x, w = np.empty(n), np.empty(n)
+    if _lib().fegen_gauss_rule(n, _ptr(x), _ptr(w)) != 0:
+        raise ValueError(f"no Gauss-Legendre rule with {n} points")
+    return x, w

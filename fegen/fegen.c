@@ -772,3 +772,10 @@ int fegen_num_threads(void) {
   return 1;
 #endif
 }
+
+/* The n-point Gauss-Legendre rule of the assembly (nodes ascending), exposed for its tests. */
+int fegen_gauss_rule(int n, double* x, double* w) {
+  if (n < 1 || n > 64 || !x || !w) return -1;
+  fg_gauss(n, x, w);
+  return 0;
+}

@@ -48,5 +48,7 @@ double fegen_l2_error(const fegen_ctx* c, const double* uh);
 double fegen_u_manufactured(const double x[3]);
 void fegen_free(fegen_ctx* c);
 int fegen_num_threads(void);
+/* n-point Gauss-Legendre rule on [-1, 1] (1 <= n <= 64), nodes ascending; 0 or -1 on bad n */
+int fegen_gauss_rule(int n, double* x, double* w);
 
 #endif

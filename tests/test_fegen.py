@@ -3,13 +3,32 @@
 The generator stands in for the paper's FE library (Sec. 2).  These checks tie its output to
 mathematics that fixes it independently of the code: the nonzero count of the tensor-product
 pattern, exact symmetry, zero row sums of the pure Laplacian, the mass matrix integrating to
-the cube's volume, and O(h^{p+1}) convergence to the manufactured solution of Sec. 3.1.
+the cube's volume, O(h^{p+1}) convergence to the manufactured solution of Sec. 3.1, and the
+Gauss-Legendre rule's exactness degree and remainder.
 """
+import math
+
 import numpy as np
 import pytest
 import scipy.sparse.linalg as sla
 
 import fegen
+
+
+@pytest.mark.parametrize("n", range(1, 13))
+def test_gauss_legendre_rule(n):
+    """The n-point rule of the assembly: numpy's Gauss-Legendre nodes and weights, exact on the
+    monomials of degree <= 2n - 1, and on x^(2n) off by exactly the Gauss remainder
+    2^(2n+1) (n!)^4 / ((2n+1) ((2n)!)^2), which no rule of other points or degree has."""
+    x, w = fegen.gauss_rule(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.max(np.abs(x - xr)) <= 1e-14 and np.max(np.abs(w - wr)) <= 1e-14
+    for k in range(2 * n):
+        exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+        assert abs(np.dot(w, x ** k) - exact) <= 1e-14
+    k = 2 * n
+    rem = 2.0 ** (2 * n + 1) * math.factorial(n) ** 4 / ((2 * n + 1) * math.factorial(2 * n) ** 2)
+    assert abs((2.0 / (k + 1) - np.dot(w, x ** k)) - rem) <= 1e-6 * rem
 
 
 def _nnz_formula(n, p):

@@ -3,6 +3,7 @@
   GLL nodes        Fig. 1's printed positions, closed forms, numpy's Legendre roots
   P (Alg. 2-4, 7)  partition of unity, exact reproduction of degree-q fields, coincident nodes
   RAP (Sec. 2)     equals the order-q operator assembled directly with the fine rule;
+                   on affine meshes also with the coarse level's own (q+2)-point rule;
                    Table 1's 4 levels and 27/343 coarsest level
   SpGEMM           scipy's product (values) and the boolean product (pattern)
   MIS-2 (Sec. 2.5) brute-force greedy MIS of the squared graph; validity; hand-worked path
@@ -142,6 +143,22 @@ def test_rap_equals_direct_assembly_with_the_fine_rule(mesh, p, kappa, lam):
     Ad = direct.scipy().toarray()
     assert np.max(np.abs(Ac - Ad)) <= 1e-12 * np.max(np.abs(Ad))
 
+
+
+@pytest.mark.parametrize("mesh,p,lam", [("uniform", 4, 1.0), ("uniform", 6, 10.0), ("graded", 8, 1000.0),
+                                        ("uniform", 3, 1.0)])
+def test_rap_equals_own_rule_assembly_on_affine_meshes(mesh, p, lam):
+    """On elements whose map is affine (uniform or z-graded boxes) with constant kappa, the order-q
+    stiffness and mass integrands are polynomials of degree <= 2q per direction, which the coarse
+    level's own (q+2)-point rule integrates exactly: R A P equals that assembly too."""
+    fine = fegen.make(2, p, mesh=mesh, lam=lam, dirichlet=False, rhs="none")
+    H = oracle.Hierarchy.from_problem(fine, coarse_max=1)
+    q = H.level_info(1)["order"]
+    own = fegen.make(2, q, mesh=mesh, lam=lam, dirichlet=False, rhs="none")
+    rp, ci, v, _ = H.level(1)
+    Ac = sp.csr_matrix((v, ci, rp), shape=(own.n, own.n)).toarray()
+    Ad = own.scipy().toarray()
+    assert np.max(np.abs(Ac - Ad)) <= 1e-12 * np.max(np.abs(Ad))
 
 def test_rap_interior_block_with_dirichlet():
     fine = fegen.make(3, 4, mesh="jitter", lam=1.0)
