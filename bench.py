@@ -632,16 +632,27 @@ def measure_block(m=32, steps=3, warmup=1):
 
 def cpu_baseline(prob, k, rtol, iters):
     """The oracle as it stands, on the host cores: two CG iterations (FP32 V-cycle, flexible CG)
-    on the full workload, scaled to the GPU's iteration count."""
+    on the full workload, scaled to the GPU's iteration count; then the same two iterations on
+    one thread ("plain"), which the fixed-block reductions make bitwise equal."""
     import oracle
     H = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
-    H.solve(prob.b, force_iters=2, precision=1)
+    x_all = H.solve(prob.b, force_iters=2, precision=1)[0]
     per_iter = (time.perf_counter() - t0) * 1e3 / 2
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        x_one = H.solve(prob.b, force_iters=2, precision=1)[0]
+        per_iter_one = (time.perf_counter() - t0) * 1e3 / 2
+    finally:
+        oracle.set_num_threads(cores)
     H.close()
-    return {"value": round(per_iter * iters, 1), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": round(per_iter * iters, 1), "unit": "ms", "cores": cores, "kind": "oracle",
             "sample": f"2 oracle CG iterations (FP32 V-cycle in FP64 flexible CG) on the full workload, "
-                      f"scaled to {iters} iterations"}
+                      f"scaled to {iters} iterations",
+            "plain": {"value": round(per_iter_one * iters, 1), "cores": 1,
+                      "bitwise_equal_to_all_cores": x_all.tobytes() == x_one.tobytes()}}
 
 
 def main():

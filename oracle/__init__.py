@@ -101,6 +101,7 @@ def _lib():
             L.orc_solve.argtypes = [vp, vp, vp, dbl, i32, i32, i32, i32, ctypes.POINTER(i32),
                                     ctypes.POINTER(dbl), vp]
             L.orc_num_threads.restype = i32
+            L.orc_set_num_threads.argtypes = [i32]
             _L = L
     return _L
 
@@ -243,6 +244,11 @@ def chol_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def num_threads() -> int:
     return _lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the OpenMP row loops; results are bitwise the same for any count."""
+    _lib().orc_set_num_threads(int(n))
 
 
 # ------------------------------------------------------------------ hierarchy

@@ -1185,3 +1185,12 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* thread count of the OpenMP row loops (the results do not depend on it); no effect without OpenMP */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

@@ -109,4 +109,5 @@ int orc_solve(orc_hier* h, const double* b, double* x, double rtol, int max_iter
               int precision, int flexible, int* iters, double* relres, double* hist);
 
 int orc_num_threads(void);
+void orc_set_num_threads(int n);
 #endif

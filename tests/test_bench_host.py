@@ -17,6 +17,18 @@ def test_percentiles():
     assert abs(bench.pct(v, 0.99) - 4.96) < 1e-12
 
 
+
+def test_cpu_baseline_all_cores_and_one_thread():
+    import fegen
+    import oracle
+    prob = fegen.make(4, 4, mesh="jitter", lam=1.0)
+    before = oracle.num_threads()
+    cpu = bench.cpu_baseline(prob, 3, 1e-8, 5)
+    assert cpu["kind"] == "oracle" and cpu["unit"] == "ms" and cpu["value"] > 0
+    assert cpu["cores"] == before and oracle.num_threads() == before
+    assert cpu["plain"]["cores"] == 1 and cpu["plain"]["value"] > 0
+    assert cpu["plain"]["bitwise_equal_to_all_cores"] is True
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
