@@ -75,6 +75,7 @@ def _lib():
             L.fegen_num_threads.restype = ctypes.c_int
             L.fegen_gauss_rule.argtypes = [ctypes.c_int, vp, vp]
             L.fegen_gauss_rule.restype = ctypes.c_int
+            L.fegen_fourier_coef.argtypes = [ctypes.c_uint64, vp]
             _lib_handle = L
     return _lib_handle
 
@@ -232,3 +233,11 @@ def gauss_rule(n: int):
     if _lib().fegen_gauss_rule(n, _ptr(x), _ptr(w)) != 0:
         raise ValueError(f"no Gauss-Legendre rule with {n} points")
     return x, w
+
+
+def fourier_coef(seed: int) -> np.ndarray:
+    """The coefficients c[k1-1, k2-1, k3-1] of rhs("fourier", seed) (the generator's own
+    counter-based normal draws, not numpy's)."""
+    c = np.empty(64)
+    _lib().fegen_fourier_coef(seed, _ptr(c))
+    return c.reshape(4, 4, 4)

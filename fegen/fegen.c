@@ -779,3 +779,9 @@ int fegen_gauss_rule(int n, double* x, double* w) {
   fg_gauss(n, x, w);
   return 0;
 }
+
+/* The 64 coefficients c_k (k = (k1 - 1) 16 + (k2 - 1) 4 + (k3 - 1)) of the Fourier right-hand
+   side drawn from `seed`, as fegen_rhs uses them; exposed for its tests. */
+void fegen_fourier_coef(uint64_t seed, double* coef) {
+  for (int k = 0; k < 64; ++k) coef[k] = fg_normal(seed, (uint64_t)k);
+}

@@ -50,5 +50,7 @@ void fegen_free(fegen_ctx* c);
 int fegen_num_threads(void);
 /* n-point Gauss-Legendre rule on [-1, 1] (1 <= n <= 64), nodes ascending; 0 or -1 on bad n */
 int fegen_gauss_rule(int n, double* x, double* w);
+/* the 64 coefficients of the Fourier right-hand side of `seed`, index (k1-1)*16 + (k2-1)*4 + (k3-1) */
+void fegen_fourier_coef(uint64_t seed, double* coef);
 
 #endif

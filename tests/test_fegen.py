@@ -3,8 +3,9 @@
 The generator stands in for the paper's FE library (Sec. 2).  These checks tie its output to
 mathematics that fixes it independently of the code: the nonzero count of the tensor-product
 pattern, exact symmetry, zero row sums of the pure Laplacian, the mass matrix integrating to
-the cube's volume, O(h^{p+1}) convergence to the manufactured solution of Sec. 3.1, and the
-Gauss-Legendre rule's exactness degree and remainder.
+the cube's volume, O(h^{p+1}) convergence to the manufactured solution of Sec. 3.1, the
+Gauss-Legendre rule's exactness degree and remainder, the patch test on distorted elements, and
+closed-form moments of the Fourier load.
 """
 import math
 
@@ -135,6 +136,46 @@ def test_graded_mesh_aspect_ratio():
     assert abs(h.sum() - 1.0) < 1e-12
     assert abs(h[1] / h[0] - 1.37618) < 1e-4
 
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
+def test_patch_test_on_jittered_elements(p):
+    """Irons' patch test on trilinear (non-affine) elements: a linear field lies in the mapped
+    space, and |J| J^-T is a polynomial of degree <= 2 per direction, so the p + 2 Gauss points
+    integrate grad(u).grad(phi_i) exactly; integrating by parts, K u vanishes at every node away
+    from the domain's boundary.  A wrong metric (J^-T J^-1 for J^-1 J^-T) or a missing
+    off-diagonal metric term fails here, though not on the box-shaped elements of a uniform mesh."""
+    import numpy as np
+    P = fegen.make(3, p, mesh="jitter", lam=0.0, dirichlet=False, rhs="none")
+    K = P.scipy()
+    X = P.coords
+    inner = np.flatnonzero(np.all((X > 1e-12) & (X < 1.0 - 1e-12), axis=1))
+    assert len(inner) == (3 * p - 1) ** 3
+    scale = abs(K).max()
+    for u in (X[:, 0], X[:, 1], X[:, 2], 0.3 * X[:, 0] - 1.1 * X[:, 1] + 0.7 * X[:, 2] + 2.0):
+        r = K @ u
+        assert np.max(np.abs(r[inner])) <= 1e-13 * scale * np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("mesh", ["uniform", "jitter"])
+def test_fourier_load_moments(mesh):
+    """rhs("fourier") loads f = sum c_k sin(k1 pi x) sin(k2 pi y) sin(k3 pi z), k in 1..4, by
+    quadrature.  Without Dirichlet rows the basis sums to 1 and reproduces x, so sum_i b_i is the
+    integral of f and sum_i b_i x_i that of x f: per direction int_0^1 sin(k pi x) dx =
+    (1 - (-1)^k) / (k pi) and int_0^1 x sin(k pi x) dx = (-1)^(k+1) / (k pi).  Fourteen Gauss
+    points per direction make the quadrature error negligible."""
+    import numpy as np
+    P = fegen.make(3, 4, mesh=mesh, lam=1.0, dirichlet=False, nq=14, rhs="none")
+    b = P.rhs("fourier", 7)
+    c = fegen.fourier_coef(7)
+    k = np.arange(1, 5)
+    i0 = (1.0 - (-1.0) ** k) / (k * np.pi)
+    i1 = (-1.0) ** (k + 1) / (k * np.pi)
+    tol = 1e-12 * np.abs(c).sum()
+    assert abs(b.sum() - np.einsum("abc,a,b,c->", c, i0, i0, i0)) <= tol
+    assert abs(b @ P.coords[:, 0] - np.einsum("abc,a,b,c->", c, i1, i0, i0)) <= tol
+    assert abs(b @ P.coords[:, 1] - np.einsum("abc,a,b,c->", c, i0, i1, i0)) <= tol
+    assert abs(b @ P.coords[:, 2] - np.einsum("abc,a,b,c->", c, i0, i0, i1)) <= tol
 
 def test_nodal_fourier_rhs():
     """rhs_nodal: the Fourier field at the nodes, zero on Dirichlet rows, seeded; against a direct
