@@ -7,9 +7,10 @@ transposed index, a missing factor), rebuilds the copy and runs the pins named f
 has to fail.  The unmodified copies have to pass the same pins, so a failure is the mistake's
 and not the harness's.  The sources under `oracle/` and `fegen/` are never written.
 
-Mistakes that leave the result unchanged are not planted: a different order of the coarse
-numbering (a relabelling, which the pins treat as the same operator) and keeping the last
-instead of the first duplicate of a prolongation entry (the elements sharing a node give the
+Changes that leave the result unchanged are not planted: a different order of the coarse
+numbering, or the larger instead of the smaller global id between two half-way candidates of a
+non-whole ratio (both relabellings, which the pins treat as the same operator), and keeping the
+last instead of the first duplicate of a prolongation entry (the elements sharing a node give the
 same interpolation value).
 """
 import os
@@ -37,6 +38,24 @@ MUTATIONS = {
     "p1d_denominator_index": (
         "oracle/oracle.c", "(xq[b] - xq[m])", "(xp[b] - xq[m])", 1,
         "test_p1d_interpolates_degree_q_polynomials"),
+    # p schedule: the smallest instead of the largest proper divisor of an odd p
+    "schedule_largest_divisor": (
+        "oracle/oracle.c", "for (int d = p / 2; d >= 1; --d)", "for (int d = 1; d <= p / 2; ++d)", 1,
+        "test_p_schedule"),
+    # the schedule by two stepping by one
+    "schedule_by_two": (
+        "oracle/oracle.c", "if (schedule == 2) return p > 2 ? p - 2 : 1;",
+        "if (schedule == 2) return p > 2 ? p - 1 : 1;", 1,
+        "test_p_schedules_by_one_and_two"),
+    # modal basis: the bubbles of the coarse order mapped one mode too high
+    "modal_index": (
+        "oracle/oracle.c", "static int orc_modal_index(int p, int q, int b) { return b == q ? p : b; }",
+        "static int orc_modal_index(int p, int q, int b) { return b == q ? p : b + 1; }", 1,
+        "test_modal_injection_rap_is_the_principal_submatrix"),
+    # h-coarsening continues only while the coarse level has fewer than 5% of the rows (0.9 read)
+    "coarsening_stop_ratio": (
+        "oracle/oracle.c", "(double)n_agg > 0.9 * (double)f->A.n", "(double)n_agg > 0.05 * (double)f->A.n", 1,
+        "test_order_one_input_with_dirichlet_rows"),
     # coarse labels for non-whole ratios: rounding up where the nearest fine node is below
     "anchor_rounding": (
         "oracle/oracle.c", "if (2 * rem < q) return f;", "if (2 * rem < q) return f + 1;", 1,
