@@ -74,3 +74,51 @@ def test_oracle_is_not_imported_by_the_product():
                 with open(os.path.join(dirpath, fn)) as f:
                     text = f.read()
                 assert "import oracle" not in text and "orc_" not in text, fn
+
+
+def test_setup_input_checks_without_a_gpu(lib):
+    """Host-mode setup rejects malformed inputs before its first CUDA call: options out of range,
+    non-uniform or unsupported element orders, a missing element map, and a row pointer that
+    cannot hold a diagonal per row (return code and message)."""
+    import numpy as np
+    n = 27
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    v = np.ones(n)
+    dofs = np.zeros((2, 27), np.int32)
+    ptr = lambda a: None if a is None else a.ctypes.data
+
+    def setup(opt=None, n_elem=2, order=(2, 2), elem_dof=dofs, row_ptr=rp, coords=None):
+        h = ctypes.c_void_p()
+        o = opt if opt is not None else g.default_options()
+        ords = np.array(order, np.int32)
+        rc = lib.giamg_setup(n, ptr(row_ptr), ptr(ci), ptr(v), n_elem, ptr(elem_dof), ptr(ords), ptr(coords),
+                             ctypes.byref(o), None, ctypes.byref(h))
+        assert h.value is None
+        return rc, lib.giamg_last_error().decode()
+
+    cases = [
+        (dict(order=(2, 3)), g.GIAMG_ERR_ORDER, "not uniform"),
+        (dict(order=(13, 13)), g.GIAMG_ERR_ORDER, "outside 1..12"),
+        (dict(order=(0, 0)), g.GIAMG_ERR_ORDER, "outside 1..12"),
+        (dict(elem_dof=None), g.GIAMG_ERR_MAP, "elem_dof is required"),
+        (dict(n_elem=-1, order=()), g.GIAMG_ERR_ARG, "n_elem must be positive"),
+        (dict(row_ptr=np.zeros(n + 1, np.int64)), g.GIAMG_ERR_ARG, "row_ptr[n]"),
+        (dict(opt=g.default_options(precision=2)), g.GIAMG_ERR_ARG, "precision"),
+        (dict(opt=g.default_options(row_form=6)), g.GIAMG_ERR_ARG, "row_form"),
+        (dict(opt=g.default_options(row_threads=3)), g.GIAMG_ERR_ARG, "row_threads"),
+        (dict(opt=g.default_options(row_chains=3)), g.GIAMG_ERR_ARG, "row_chains"),
+        (dict(opt=g.default_options(graphs=3)), g.GIAMG_ERR_ARG, "graphs"),
+        (dict(opt=g.default_options(p_schedule=3)), g.GIAMG_ERR_ARG, "p_schedule"),
+        (dict(opt=g.default_options(basis=2)), g.GIAMG_ERR_ARG, "basis"),
+        (dict(opt=g.default_options(cheb_degree=65)), g.GIAMG_ERR_ARG, "cheb_degree"),
+        (dict(opt=g.default_options(cheb_lo=0.0)), g.GIAMG_ERR_ARG, "cheb_lo"),
+        (dict(opt=g.default_options(cheb_lo=1.2, cheb_hi=1.1)), g.GIAMG_ERR_ARG, "cheb_lo"),
+        (dict(opt=g.default_options(max_levels=0)), g.GIAMG_ERR_ARG, "max_levels"),
+        (dict(opt=g.default_options(lanczos_steps=0)), g.GIAMG_ERR_ARG, "lanczos_steps"),
+        (dict(opt=g.default_options(prefetch_rows=-2)), g.GIAMG_ERR_ARG, "prefetch_rows"),
+        (dict(opt=g.default_options(basis=1), coords=np.zeros((n, 3))), g.GIAMG_ERR_ARG, "modal"),
+    ]
+    for kw, code, text in cases:
+        rc, msg = setup(**kw)
+        assert rc == code and text in msg, (kw, rc, msg)
