@@ -166,7 +166,9 @@ def summarize_launches(path, split=None):
     for r in csv.DictReader(io.StringIO("".join(lines))):
         if r.get("Metric Name") != "gpu__time_duration.sum":
             continue
-        name = re.sub(r"\(.*", "", r["Kernel Name"]).replace("(anonymous namespace)::", "")
+        raw = r["Kernel Name"].replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
+        raw = re.sub(r"^void\s+", "", raw.replace("unnamed>::", ""))
+        name = re.sub(r"\(.*", "", raw)
         m = re.search(r"csr_rows<(\d+), (\w+), (\d)>", r["Kernel Name"])
         if m:
             name = f"csr_rows<{m.group(1)},{m.group(2)},{['spmv','residual','cheb','add'][int(m.group(3))]}>"

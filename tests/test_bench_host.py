@@ -61,3 +61,39 @@ def test_two_rank_max_over_ranks_with_gloo():
     for p, (o, e) in zip(procs, outs):
         assert p.returncode == 0, e
     assert all("max 11.0" in o for o, _ in outs)
+
+
+NCU_CSV = '''==PROF== Connected to process 1
+"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"
+"0","1","python","h","unnamed>::hyv_cheb_f32(int, const float *)","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","usecond","300.00"
+"1","1","python","h","void unnamed>::csr_rows<16, double, 0>(long, const long *)","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","msecond","0.10"
+"2","1","python","h","void (anonymous namespace)::hyv_cheb_f32(int, const float *)","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","nsecond","100000"
+'''
+
+
+def test_summarize_launches(tmp_path):
+    """Launches and device time per kernel, whatever unit ncu prints and however it writes the
+    anonymous namespace, and their shares."""
+    path = tmp_path / "launches.csv"
+    path.write_text(NCU_CSV)
+    text = bench.summarize_launches(str(path), split="csr_rows")
+    first = text.split("\n\n")[0]
+    rows = {line.split()[-1]: line.split() for line in first.splitlines() if "%" in line}
+    assert rows["hyv_cheb_f32"][:3] == ["2", "0.400", "80.00%"]
+    assert rows["csr_rows<16,double,spmv>"][:3] == ["1", "0.100", "20.00%"]
+    assert "segment 1 (from launch 1)" in text
+
+
+def test_traffic_is_null_once_the_kernel_source_changes(monkeypatch):
+    """roofline.traffic comes from the committed capture only while the kernel source is the one
+    that was captured."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        import json
+        rec = json.load(f)
+    workload = next(iter(rec))
+    mode = next(iter(rec[workload]))
+    want = rec[workload][mode]["dram_bytes_per_launch"]
+    assert rec[workload][mode]["solve_kernels_sha"] == bench.kernel_source_hash()
+    assert bench.ncu_traffic(workload, mode) == want
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic(workload, mode) is None
