@@ -20,15 +20,26 @@ class DegreeTiming:
     ms: float  # median solve time
 
 
+def _cuda_event_timer(fn):
+    """Run fn() between two CUDA events on the current stream; (fn's result, milliseconds)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return res, e0.elapsed_time(e1)
+
+
 def tune_cheb_degree(solver, b, degrees=(1, 2, 3, 4, 5), precision: int = 1, rtol: float = 1e-8,
-                     reps: int = 5, warmup: int = 2):
+                     reps: int = 5, warmup: int = 2, timer=None):
     """Time solves of A x = b for each smoother degree, set the fastest one that reaches rtol on
     the solver and return (best degree, [DegreeTiming, ...]).  b: a device vector of the solver's
-    pointer mode.  Times are CUDA-event medians on the current stream."""
+    pointer mode.  Times are CUDA-event medians on the current stream (`timer` replaces the
+    CUDA-event timer: a function of a callable returning (its result, milliseconds))."""
     import statistics
 
-    import torch
-
+    timer = timer or _cuda_event_timer
     out = []
     for k in degrees:
         solver.set_cheb_degree(k)
@@ -36,12 +47,8 @@ def tune_cheb_degree(solver, b, degrees=(1, 2, 3, 4, 5), precision: int = 1, rto
             solver.solve(b, rtol=rtol, precision=precision)
         ts = []
         for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            _, it, rr = solver.solve(b, rtol=rtol, precision=precision)
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
+            (_, it, rr), ms = timer(lambda: solver.solve(b, rtol=rtol, precision=precision))
+            ts.append(ms)
         out.append(DegreeTiming(k, int(it), float(rr), statistics.median(ts)))
     ok = [t for t in out if t.relres <= rtol]
     best = min(ok or out, key=lambda t: t.ms)
