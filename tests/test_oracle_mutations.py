@@ -94,6 +94,16 @@ MUTATIONS = {
     "lanczos_three_term": (
         "oracle/oracle.c", "w[i] = dsq[i] * w[i] - bprev * vp[i];", "w[i] = dsq[i] * w[i];", 1,
         "test_lanczos_estimate_within_one_percent"),
+    # Lanczos: alpha_j v_j not subtracted
+    "lanczos_alpha_term": (
+        "oracle/oracle.c", "for (int64_t i = 0; i < n; ++i) w[i] = w[i] - a * v[i];",
+        "for (int64_t i = 0; i < n; ++i) w[i] = w[i];", 1,
+        "test_lanczos_ritz_bounds_finite_termination_and_start_vector"),
+    # Lanczos start vector: the hash scaled by 1/512 instead of 1/1024
+    "lanczos_start_vector": (
+        "oracle/oracle.c", "v[i] = 1.0 + (double)(orc_hash(hash_kind, i) % 1024u) / 1024.0;",
+        "v[i] = 1.0 + (double)(orc_hash(hash_kind, i) % 1024u) / 512.0;", 1,
+        "test_lanczos_ritz_bounds_finite_termination_and_start_vector"),
     # Sturm count: beta not squared
     "sturm_beta_square": (
         "oracle/oracle.c", "beta[i - 1] * beta[i - 1] / d", "beta[i - 1] / d", 1,

@@ -10,7 +10,8 @@
   aggregates       cover, one root each, connected; hand-worked paths (one where the second
                    phase decides between two aggregates)
   SPAI-0           minimiser of ||e_i - m a_i|| row by row
-  Lanczos          dense eigenvalues (numpy) within 1%
+  Lanczos          dense eigenvalues (numpy) within 1%; Ritz bounds, monotone growth, finite
+                   termination, one step = the start vector's Rayleigh quotient
   Chebyshev        closed-form damping T_k((theta - mu)/delta) / T_k(theta/delta)
   Cholesky         numpy's factor and solve
   V-cycle (Alg. 1) symmetric as an operator; the FP32 V-cycle applies the FP64 operator to
@@ -382,6 +383,37 @@ def test_lanczos_estimate_within_one_percent():
         lam = np.linalg.eigvalsh(d[:, None] * A * d[None, :]).max()
         assert abs(H.rho_hat(l) - lam) <= 0.01 * lam
 
+
+
+def test_lanczos_ritz_bounds_finite_termination_and_start_vector():
+    """Lanczos on B = D^-1/2 A D^-1/2: the largest Ritz value never exceeds lambda_max(B) and
+    grows with the number of steps; with as many steps as rows the Krylov space is the whole
+    space and it equals lambda_max(B); after one step it is the Rayleigh quotient of the start
+    vector v_i = 1 + (h(i) mod 1024) / 1024."""
+    rng = np.random.default_rng(3)
+    for n in (5, 12, 20):
+        M = rng.normal(size=(n, n))
+        A = M @ M.T + n * np.eye(n)
+        S = sp.csr_matrix(A)
+        d = 1.0 / np.sqrt(np.diag(A))
+        lam = np.linalg.eigvalsh(d[:, None] * A * d[None, :]).max()
+        assert abs(oracle.lanczos_rho(S.indptr, S.indices, S.data, steps=20) - lam) <= 1e-12 * lam
+    n = 300
+    A = sp.diags([-np.ones(n - 1), 2.5 + rng.random(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    Ad = A.toarray()
+    d = 1.0 / np.sqrt(np.diag(Ad))
+    B = d[:, None] * Ad * d[None, :]
+    lam = np.linalg.eigvalsh(B).max()
+    prev = 0.0
+    for steps in (1, 2, 5, 10, 20, 40):
+        r = oracle.lanczos_rho(A.indptr, A.indices, A.data, steps=steps)
+        assert prev - 1e-14 <= r <= lam * (1 + 1e-12)
+        prev = r
+    for kind in (0, 1):
+        v = 1.0 + np.array([oracle.hash32(i, kind) % 1024 for i in range(n)]) / 1024.0
+        v /= np.linalg.norm(v)
+        r1 = oracle.lanczos_rho(A.indptr, A.indices, A.data, steps=1, hash_kind=kind)
+        assert abs(r1 - v @ B @ v) <= 1e-13 * abs(r1)
 
 def test_tridiagonal_eigenvalue_by_bisection():
     rng = np.random.default_rng(1)
