@@ -122,3 +122,13 @@ def test_setup_input_checks_without_a_gpu(lib):
     for kw, code, text in cases:
         rc, msg = setup(**kw)
         assert rc == code and text in msg, (kw, rc, msg)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libgiamg.so every entry into the package raises: there is no fallback path."""
+    monkeypatch.setattr(g, "_lib", None)
+    monkeypatch.setattr(g, "LIB_PATH", str(tmp_path / "libgiamg.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        g.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        g.default_options()
