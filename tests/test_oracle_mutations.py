@@ -70,6 +70,10 @@ MUTATIONS = {
     "prolongation_tensor_index": (
         "oracle/oracle.c", "tab[a2 * m1 + b2] * tab[a3 * m1 + b3]", "tab[a2 * m1 + b3] * tab[a3 * m1 + b2]", 2,
         "test_prolongation_reproduces_degree_q_fields"),
+    # the hash: a finaliser shift off by one
+    "hash_shift": (
+        "oracle/oracle.c", "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;", 1,
+        "test_hash_is_the_splitmix64_finaliser"),
     # MIS-2: the hash order reversed
     "mis2_hash_order": (
         "oracle/oracle.c", "if (ha != hb) return ha > hb;", "if (ha != hb) return ha < hb;", 1,

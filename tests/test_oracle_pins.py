@@ -7,6 +7,7 @@
                    Table 1's 4 levels and 27/343 coarsest level
   SpGEMM           scipy's product (values) and the boolean product (pattern)
   MIS-2 (Sec. 2.5) brute-force greedy MIS of the squared graph; validity; hand-worked path
+  hash             SplitMix64's published outputs from state 0
   aggregates       cover, one root each, connected; hand-worked paths (one where the second
                    phase decides between two aggregates)
   SPAI-0           minimiser of ||e_i - m a_i|| row by row
@@ -269,6 +270,15 @@ def _greedy_mis2(n, adj, prio):
             chosen.append(i)
     return set(chosen), D
 
+
+
+def test_hash_is_the_splitmix64_finaliser():
+    """h(i) = upper 32 bits of SplitMix64's output i + 1 from state 0 (published reference
+    values, `tests/golden/splitmix64_seed0.txt`); the identity option returns i."""
+    g = read_golden("splitmix64_seed0.txt")
+    for i, hexval in enumerate(g["outputs"]):
+        assert oracle.hash32(i, 0) == int(hexval, 16) >> 32
+    assert [oracle.hash32(i, 1) for i in (0, 1, 7, 123456)] == [0, 1, 7, 123456]
 
 def test_mis2_hand_worked_path():
     g = read_golden("mis2_path7.txt")
