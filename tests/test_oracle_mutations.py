@@ -155,6 +155,11 @@ MUTATIONS = {
     "flexible_beta_sign": (
         "oracle/oracle.c", "double beta = orc_dot(n, z, rold) / rho;", "double beta = -orc_dot(n, z, rold) / rho;", 1,
         "test_force_iters_and_flexible_cg"),
+    # the iteration limit not reported
+    "maxiter_status": (
+        "oracle/oracle.c", "if (status == ORC_OK && force_iters <= 0 && rr > rtol) status = ORC_ERR_MAXITER;",
+        "if (status == ORC_OK && force_iters <= 0 && rr > 1.0) status = ORC_ERR_MAXITER;", 1,
+        "test_iteration_limit_and_zero_right_hand_side"),
     # relative residual not divided by ||b||
     "relres_unnormalised": (
         "oracle/oracle.c", "rr = sqrt(orc_dot(n, r, r)) / bnorm;", "rr = sqrt(orc_dot(n, r, r));", 1,

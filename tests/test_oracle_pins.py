@@ -563,6 +563,22 @@ def test_iterations_nearly_independent_of_order():
     assert max(jac) >= 3 * min(jac), jac
     assert all(a < b for a, b in zip(ours, jac))
 
+
+def test_iteration_limit_and_zero_right_hand_side():
+    """Stopping rules (Sec. 3.1: x0 = 0, relative residual): a limit below the needed count stops
+    there with status maxiter and the recursive residual of that iterate, which for an exact
+    recurrence is the true one; b = 0 returns x = 0 after no iteration with relres 0."""
+    prob = fegen.make(3, 4, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob)
+    _, it, _, hist, st = H.solve(prob.b, rtol=1e-8)
+    assert st == "ok" and it > 3 and hist[0] == 1.0 and np.all(np.diff(hist) < 0)
+    x2, it2, rr2, hist2, st2 = H.solve(prob.b, rtol=1e-8, max_iter=2)
+    assert (it2, st2) == (2, "maxiter") and rr2 == hist2[-1] == hist[2]
+    true = np.linalg.norm(prob.b - prob.scipy() @ x2) / np.linalg.norm(prob.b)
+    assert abs(true - rr2) <= 1e-10 * rr2
+    x0, it0, rr0, _, st0 = H.solve(np.zeros(prob.n), rtol=1e-8)
+    assert (it0, rr0, st0) == (0, 0.0, "ok") and not np.any(x0)
+
 def test_force_iters_and_flexible_cg():
     prob = fegen.make(4, 4, mesh="jitter", lam=1.0)
     H = oracle.Hierarchy.from_problem(prob)
