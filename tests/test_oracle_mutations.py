@@ -121,6 +121,11 @@ MUTATIONS = {
         "oracle/oracle.c", "double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;",
         "double c1 = rho_new * rho, c2 = rho_new / delta;", 1,
         "test_chebyshev_damping_closed_form"),
+    # Chebyshev started from zero: the first step taken twice
+    "chebyshev_zero_start": (
+        "oracle/oracle.c", "    x[i] = x_is_zero ? d[i] : x[i] + d[i];\n  }\n  for (int s = 1; s < k; ++s) {\n    orc_spmv(&L->A, x, r);",
+        "    x[i] = x_is_zero ? 2.0 * d[i] : x[i] + d[i];\n  }\n  for (int s = 1; s < k; ++s) {\n    orc_spmv(&L->A, x, r);", 1,
+        "test_chebyshev_zero_start_equals_explicit_zero"),
     # Chebyshev (FP32): rho_{s-1} dropped from the direction coefficient
     "chebyshev_fp32_coefficient": (
         "oracle/oracle.c", "float c1 = (float)(rho_new * rho)", "float c1 = (float)(rho_new)", 1,

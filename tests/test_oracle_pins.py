@@ -452,6 +452,20 @@ def test_chebyshev_damping_closed_form():
             assert np.allclose(x, damp * v, atol=1e-11 * np.abs(v).max())
 
 
+
+def test_chebyshev_zero_start_equals_explicit_zero():
+    """Presmoothing starts from x = 0 and skips the first product (its residual is b); the general
+    branch started from an explicit zero vector computes r = b - A 0 and must give the same x."""
+    prob = fegen.make(3, 4, mesh="jitter", lam=1.0)
+    rng = np.random.default_rng(4)
+    for k in (1, 2, 3):
+        H = oracle.Hierarchy.from_problem(prob, cheb_degree=k)
+        for l in range(H.num_levels - 1):
+            b = rng.standard_normal(H.level_info(l)["n"])
+            x_fast = H.cheb(l, b)
+            x_full = H.cheb(l, b, np.zeros_like(b))
+            assert np.max(np.abs(x_fast - x_full)) <= 1e-14 * np.max(np.abs(x_full))
+
 # ----------------------------------------------------------------------------- coarsest
 def test_cholesky_matches_numpy():
     rng = np.random.default_rng(5)
