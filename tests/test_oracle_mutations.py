@@ -135,6 +135,11 @@ MUTATIONS = {
         "oracle/oracle.c", "orc_cheb(h, L, b, x, 1);                       /* presmooth */",
         "for (int64_t i = 0; i < n; ++i) x[i] = 0.0;", 1,
         "test_vcycle_is_symmetric"),
+    # the prolongation entry point overwrites instead of correcting
+    "prolong_overwrites": (
+        "oracle/oracle.c", "for (int64_t i = 0; i < L->A.n; ++i) xf[i] = xf[i] + t[i];",
+        "for (int64_t i = 0; i < L->A.n; ++i) xf[i] = t[i];", 1,
+        "test_single_steps_are_their_definitions"),
     # Algorithm 1: the coarse correction subtracted
     "coarse_correction_sign": (
         "oracle/oracle.c", "x[i] = x[i] + L->r[i]; /* correct */", "x[i] = x[i] - L->r[i]; /* correct */", 1,

@@ -466,6 +466,31 @@ def test_chebyshev_zero_start_equals_explicit_zero():
             x_full = H.cheb(l, b, np.zeros_like(b))
             assert np.max(np.abs(x_fast - x_full)) <= 1e-14 * np.max(np.abs(x_full))
 
+
+def test_single_steps_are_their_definitions():
+    """The per-step entry points the GPU parity tests compare against: level product y = A_l x,
+    restriction r_c = P_l^T r_f, prolongation x_f + P_l e_c, coarsest solve A_L^-1 r (with the
+    levels' exported A_l and P_l, themselves pinned above)."""
+    prob = fegen.make(4, 4, mesh="jitter", lam=1.0)
+    H = oracle.Hierarchy.from_problem(prob, coarse_max=100)
+    rng = np.random.default_rng(6)
+    assert H.level_info(H.num_levels - 2)["kind"] == oracle.KIND_H
+    for l in range(H.num_levels):
+        info = H.level_info(l)
+        rp, ci, v, _ = H.level(l)
+        A = sp.csr_matrix((v, ci, rp), shape=(info["n"], info["n"]))
+        x = rng.standard_normal(info["n"])
+        assert np.allclose(H.spmv(l, x), A @ x, rtol=0, atol=1e-13 * np.abs(A).sum(axis=1).max() * np.abs(x).max())
+        if info["kind"] == oracle.KIND_COARSEST:
+            z = H.coarse_solve(x)
+            assert np.linalg.norm(z - np.linalg.solve(A.toarray(), x)) <= 1e-10 * np.linalg.norm(z)
+            continue
+        prp, pci, pv, m = H.prolongation(l)
+        P = sp.csr_matrix((pv, pci, prp), shape=(info["n"], m))
+        e = rng.standard_normal(m)
+        assert np.allclose(H.restrict(l, x), P.T @ x, rtol=1e-13, atol=1e-13 * np.abs(x).max())
+        assert np.allclose(H.prolong(l, e, x), x + P @ e, rtol=1e-13, atol=1e-13 * np.abs(e).max())
+
 # ----------------------------------------------------------------------------- coarsest
 def test_cholesky_matches_numpy():
     rng = np.random.default_rng(5)
