@@ -97,3 +97,22 @@ def test_traffic_is_null_once_the_kernel_source_changes(monkeypatch):
     assert bench.ncu_traffic(workload, mode) == want
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.ncu_traffic(workload, mode) is None
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the CPU oracle on the host cores) prints one JSON line with
+    the contract's keys, on the small workload."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "helmholtz_4cube_p4", "--steps", "3", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and (d["steps"], d["warmup"]) == (3, 3)
+    assert d["unit"] == "ms" and d["higher_is_better"] is False and d["value"] > 0
+    assert d["config"]["workload"] == "helmholtz_4cube_p4" and d["config"]["dofs"] == 4913
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
