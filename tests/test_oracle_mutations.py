@@ -74,6 +74,11 @@ MUTATIONS = {
     "hash_shift": (
         "oracle/oracle.c", "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;", 1,
         "test_hash_is_the_splitmix64_finaliser"),
+    # the strength test reversed (weak couplings kept), in the count and the fill pass alike
+    "strength_threshold": (
+        "oracle/oracle.c", "if (theta > 0.0 && !(fabs(A->v[t]) >= theta * sqrt(diag[i] * diag[j]))) continue;",
+        "if (theta > 0.0 && !(fabs(A->v[t]) <= theta * sqrt(diag[i] * diag[j]))) continue;", 2,
+        "test_strength_threshold_keeps_only_strong_couplings"),
     # MIS-2: the hash order reversed
     "mis2_hash_order": (
         "oracle/oracle.c", "if (ha != hb) return ha > hb;", "if (ha != hb) return ha < hb;", 1,

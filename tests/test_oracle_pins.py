@@ -881,6 +881,23 @@ def test_order_one_input_with_dirichlet_rows(n):
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
 
 
+
+def test_strength_threshold_keeps_only_strong_couplings():
+    """Opt-in strength graph (theta > 0): a_ij is kept when |a_ij| >= theta sqrt(a_ii a_jj).  On a
+    chain whose couplings alternate between -1 and -0.01 (diagonal 2.02), theta = 0.1 keeps only
+    the -1 links, the graph falls into disjoint pairs, and every pair becomes one aggregate
+    (roots numbered in ascending order: pair i is aggregate i); theta = 0 keeps the chain."""
+    n = 40
+    off = np.array([-1.0 if i % 2 == 0 else -0.01 for i in range(n - 1)])
+    A = sp.diags([off, np.full(n, 2.02), off], [-1, 0, 1]).tocsr()
+    A.sort_indices()
+    no_map = np.zeros((0, 1), np.int32)
+    H = oracle.Hierarchy(n, A.indptr, A.indices, A.data, no_map, 1, coarse_max=5, strength_theta=0.1)
+    agg = H.level(0)[3]
+    assert agg.tolist() == (np.arange(n) // 2).tolist() and H.level_info(1)["n"] == n // 2
+    H0 = oracle.Hierarchy(n, A.indptr, A.indices, A.data, no_map, 1, coarse_max=5, strength_theta=0.0)
+    assert H0.level(0)[3].tolist() != agg.tolist()
+
 # ----------------------------------------------------------------------------- block PCG
 # oracle/block_cg.py: O'Leary's block CG with A-conjugate directions and dependent directions
 # dropped.  Pins: m = 1 is the scalar PCG; finite termination after n/m steps; the iterate is
