@@ -156,6 +156,34 @@ def giamg_free(h):
     _check(lib().giamg_free(h))
 
 
+def _check_inputs(n, row_ptr, col, val, elem_dof, p, coords, device):
+    """Shapes, lengths and (device mode) dtypes of the setup arrays, checked before the C call:
+    the ABI takes plain pointers and cannot see how long a buffer is."""
+    if device:
+        want = (("row_ptr", row_ptr, "int64"), ("col", col, "int32"), ("val", val, "float64"),
+                ("elem_dof", elem_dof, "int32"), ("coords", coords, "float64"))
+        for name, a, dt in want:
+            if a is None:
+                continue
+            if not hasattr(a, "is_cuda") or not a.is_cuda:
+                raise TypeError(f"{name}: device_ptrs=1 needs a CUDA tensor")
+            if str(a.dtype) != "torch." + dt:
+                raise TypeError(f"{name}: dtype {a.dtype}, expected torch.{dt}")
+            if not a.is_contiguous():
+                raise ValueError(f"{name}: not contiguous")
+    shape = lambda a: tuple(a.shape)
+    if len(shape(row_ptr)) != 1 or shape(row_ptr)[0] != n + 1:
+        raise ValueError(f"row_ptr: shape {shape(row_ptr)}, expected ({n + 1},)")
+    nnz = int(row_ptr[n])
+    for name, a in (("col", col), ("val", val)):
+        if len(shape(a)) != 1 or shape(a)[0] < nnz:
+            raise ValueError(f"{name}: shape {shape(a)}, expected at least row_ptr[n] = {nnz} entries")
+    if elem_dof is not None and (len(shape(elem_dof)) != 2 or shape(elem_dof)[1] != (p + 1) ** 3):
+        raise ValueError(f"elem_dof: shape {shape(elem_dof)}, expected (n_elem, {(p + 1) ** 3}) for p = {p}")
+    if coords is not None and shape(coords) != (n, 3):
+        raise ValueError(f"coords: shape {shape(coords)}, expected ({n}, 3)")
+
+
 class Solver:
     """A GIAMG hierarchy on the GPU (one handle)."""
 
@@ -163,6 +191,15 @@ class Solver:
         self.opts = default_options(**opts)
         self.device = bool(self.opts.device_ptrs)
         self.n = int(n)
+        p = int(p)
+        if not self.device:
+            row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+            col = np.ascontiguousarray(col, np.int32)
+            val = np.ascontiguousarray(val, np.float64)
+            elem_dof = None if elem_dof is None else np.ascontiguousarray(elem_dof, np.int32)
+            coords = None if coords is None else np.ascontiguousarray(coords, np.float64)
+        if self.n >= 1:
+            _check_inputs(self.n, row_ptr, col, val, elem_dof, p, coords, self.device)
         if self.device:
             import torch
             ed = elem_dof
@@ -174,13 +211,9 @@ class Solver:
             elif int(stream) != int(cur.cuda_stream):
                 cur.synchronize()  # inputs written on torch's stream are read on `stream`
         else:
-            row_ptr = np.ascontiguousarray(row_ptr, np.int64)
-            col = np.ascontiguousarray(col, np.int32)
-            val = np.ascontiguousarray(val, np.float64)
-            ed = None if elem_dof is None else np.ascontiguousarray(elem_dof, np.int32)
+            ed = elem_dof
             n_elem = int(ed.shape[0]) if ed is not None else 0
             order = np.full(max(n_elem, 1), p, np.int32)
-            coords = None if coords is None else np.ascontiguousarray(coords, np.float64)
         self._h = giamg_setup(self.n, row_ptr, col, val, n_elem, ed, order if n_elem else None, coords,
                               self.opts, stream)
 

@@ -132,3 +132,33 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         g.lib()
     with pytest.raises(RuntimeError, match="not built"):
         g.default_options()
+
+
+def test_solver_checks_array_shapes_and_device_tensors():
+    """The binding checks what the C ABI cannot (buffer lengths, shapes, dtypes of device tensors)
+    and raises before any library or CUDA call."""
+    import numpy as np
+    import torch
+    n, p = 27, 2
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    v = np.ones(n)
+    ed = np.zeros((1, 27), np.int32)
+    bad = [
+        (dict(row_ptr=rp[:-1]), ValueError, "row_ptr"),
+        (dict(col=ci[:-1]), ValueError, "col"),
+        (dict(val=v[:-3]), ValueError, "val"),
+        (dict(elem_dof=np.zeros((1, 26), np.int32)), ValueError, "elem_dof"),
+        (dict(coords=np.zeros((n, 2))), ValueError, "coords"),
+    ]
+    for kw, exc, text in bad:
+        args = dict(row_ptr=rp, col=ci, val=v, elem_dof=ed, coords=None)
+        args.update(kw)
+        with pytest.raises(exc, match=text):
+            g.Solver(n, args["row_ptr"], args["col"], args["val"], args["elem_dof"], p, coords=args["coords"])
+    # device mode: host tensors, or the wrong dtype, are refused before touching CUDA
+    t = torch.from_numpy
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        g.Solver(n, t(rp), t(ci), t(v), t(ed), p, device_ptrs=1)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        g.Solver(n, rp, ci, v, ed, p, device_ptrs=1)
