@@ -254,10 +254,30 @@ class Solver:
             return v.to("cuda", torch.float64).contiguous()
         return np.ascontiguousarray(v, np.float64)
 
+    def _check_shape(self, name, a, shape):
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: shape {tuple(a.shape)}, expected {tuple(shape)}")
+
+    def _check_out(self, name, a, shape):
+        """A buffer the caller passes for the library to write: the right shape, float64, contiguous,
+        and on the device in device mode (the C call only sees a pointer)."""
+        self._check_shape(name, a, shape)
+        if self.device:
+            import torch
+            ok = isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+        else:
+            ok = isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+        if not ok:
+            kind = "CUDA tensor" if self.device else "numpy array"
+            raise TypeError(f"{name}: expected a contiguous float64 {kind}")
+
     # -------------------------------------------------------------- solve
     def solve(self, b, rtol=1e-8, precision=None, force_iters=None, x=None):
         """Returns (x, iters, relres); raises GiamgError on failure other than max_iter."""
         b = self._in(b)
+        self._check_shape("b", b, (self.n,))
+        if x is not None:
+            self._check_out("x", x, (self.n,))
         x = self._vec(self.n) if x is None else x
         prec = self.opts.precision if precision is None else precision
         force = self.opts.force_iters if force_iters is None else force_iters
@@ -274,6 +294,9 @@ class Solver:
         if not self.device:
             raise GiamgError(GIAMG_ERR_ARG, "solve_async needs device=True")
         b = b.to("cuda", torch.float64).contiguous()
+        self._check_shape("b", b, (self.n,))
+        if x is not None:
+            self._check_out("x", x, (self.n,))
         x = torch.empty_like(b) if x is None else x
         it = torch.zeros(1, dtype=torch.int32, device="cuda")
         rr = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -285,7 +308,11 @@ class Solver:
     def solve_batch(self, B, rtol=1e-8, precision=None, force_iters=None, X=None, block=False):
         """B: n x m (row-major, m <= 32).  Returns (X, iters[m], relres[m]).  block=True: the
         columns as one block in block CG (giamg_solve_block) instead of independent CGs."""
+        if len(B.shape) != 2 or B.shape[0] != self.n:
+            raise ValueError(f"B: shape {tuple(B.shape)}, expected ({self.n}, m)")
         m = int(B.shape[1])
+        if X is not None:
+            self._check_out("X", X, (self.n, m))
         if self.device:
             import torch
             B = B.to("cuda", torch.float64).contiguous()

@@ -162,3 +162,25 @@ def test_solver_checks_array_shapes_and_device_tensors():
         g.Solver(n, t(rp), t(ci), t(v), t(ed), p, device_ptrs=1)
     with pytest.raises(TypeError, match="CUDA tensor"):
         g.Solver(n, rp, ci, v, ed, p, device_ptrs=1)
+
+
+def test_solve_calls_check_their_buffers():
+    """solve / solve_batch refuse right-hand sides and output buffers of the wrong shape, dtype or
+    layout before calling the library (checked on an object that was never set up)."""
+    import numpy as np
+    S = g.Solver.__new__(g.Solver)
+    S.n, S.device, S.opts, S._h = 10, False, g.default_options(), ctypes.c_void_p()
+    with pytest.raises(ValueError, match="b: shape"):
+        S.solve(np.zeros(9))
+    with pytest.raises(ValueError, match="x: shape"):
+        S.solve(np.zeros(10), x=np.zeros(11))
+    with pytest.raises(TypeError, match="float64"):
+        S.solve(np.zeros(10), x=np.zeros(10, np.float32))
+    with pytest.raises(ValueError, match="B: shape"):
+        S.solve_batch(np.zeros((9, 2)))
+    with pytest.raises(ValueError, match="B: shape"):
+        S.solve_batch(np.zeros(10))
+    with pytest.raises(ValueError, match="X: shape"):
+        S.solve_batch(np.zeros((10, 2)), X=np.zeros((10, 3)))
+    with pytest.raises(TypeError, match="contiguous"):
+        S.solve_batch(np.zeros((10, 2)), X=np.zeros((2, 10)).T)
