@@ -419,12 +419,14 @@ class Solver:
     # -------------------------------------------------------------- single steps
     def vcycle(self, r, precision=0):
         r = self._in(r)
+        self._check_shape("r", r, (self.n,))
         z = self._vec(self.n)
         _check(lib().giamg_apply_vcycle(self._h, precision, _ptr(r), _ptr(z)))
         return z
 
     def spmv(self, l, x):
         x = self._in(x)
+        self._check_shape("x", x, (self.level_info(l)["n"],))
         y = self._vec(self.level_info(l)["n"])
         _check(lib().giamg_level_spmv(self._h, l, _ptr(x), _ptr(y)))
         return y
@@ -438,29 +440,38 @@ class Solver:
         else:
             x = np.ascontiguousarray(x, np.float32)
             y = np.empty(self.level_info(l)["n"], np.float32)
+        self._check_shape("x", x, tuple(y.shape))
         _check(lib().giamg_level_spmv32(self._h, l, _ptr(x), _ptr(y)))
         return y
 
     def smooth(self, l, b, x=None):
         b = self._in(b)
+        self._check_shape("b", b, (self.level_info(l)["n"],))
+        if x is not None:
+            self._check_shape("x", x, (self.level_info(l)["n"],))
         xo = self._vec(self.level_info(l)["n"]) if x is None else self._in(x).clone() if self.device else self._in(x).copy()
         _check(lib().giamg_level_smooth(self._h, l, _ptr(b), _ptr(xo), 1 if x is None else 0))
         return xo
 
     def restrict(self, l, rf):
         rf = self._in(rf)
+        self._check_shape("rf", rf, (self.level_info(l)["n"],))
         rc = self._vec(self.level_info(l)["n_next"])
         _check(lib().giamg_level_restrict(self._h, l, _ptr(rf), _ptr(rc)))
         return rc
 
     def prolong(self, l, ec, xf):
         ec = self._in(ec)
+        info = self.level_info(l)
+        self._check_shape("ec", ec, (info["n_next"],))
+        self._check_shape("xf", xf, (info["n"],))
         xo = self._in(xf).clone() if self.device else self._in(xf).copy()
         _check(lib().giamg_level_prolong(self._h, l, _ptr(ec), _ptr(xo)))
         return xo
 
     def coarse_solve(self, r):
         r = self._in(r)
+        self._check_shape("r", r, (self.level_info(self.num_levels - 1)["n"],))
         x = self._vec(self.level_info(self.num_levels - 1)["n"])
         _check(lib().giamg_coarse_solve(self._h, _ptr(r), _ptr(x)))
         return x

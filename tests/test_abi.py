@@ -184,3 +184,21 @@ def test_solve_calls_check_their_buffers():
         S.solve_batch(np.zeros((10, 2)), X=np.zeros((10, 3)))
     with pytest.raises(TypeError, match="contiguous"):
         S.solve_batch(np.zeros((10, 2)), X=np.zeros((2, 10)).T)
+
+
+def test_single_step_calls_check_lengths(monkeypatch):
+    """The per-step entry points refuse vectors whose length is not the level's (level sizes
+    stubbed on an object that was never set up)."""
+    import numpy as np
+    S = g.Solver.__new__(g.Solver)
+    S.n, S.device, S.opts, S._h = 10, False, g.default_options(), ctypes.c_void_p()
+    S.level_info = lambda l: {"n": 10 if l == 0 else 4, "n_next": 4}
+    monkeypatch.setattr(g.Solver, "num_levels", property(lambda self: 2))
+    short, fine, coarse = np.zeros(9), np.zeros(10), np.zeros(4)
+    calls = [lambda: S.vcycle(short), lambda: S.spmv(0, short), lambda: S.spmv32(0, short),
+             lambda: S.smooth(0, short), lambda: S.smooth(0, fine, short), lambda: S.restrict(0, short),
+             lambda: S.prolong(0, np.zeros(3), fine), lambda: S.prolong(0, coarse, short),
+             lambda: S.coarse_solve(short)]
+    for call in calls:
+        with pytest.raises(ValueError, match="shape"):
+            call()
