@@ -171,6 +171,13 @@ class Server:
 
     # ------------------------------------------------------------------ requests
     def submit(self, req: Request):
+        """Queue a request.  Its right-hand sides must be an n x r array with 1 <= r <= max_columns
+        (ValueError otherwise, raised here: a malformed request never reaches a batch)."""
+        rhs = req.rhs
+        if not isinstance(rhs, np.ndarray) or rhs.ndim != 2 or not 1 <= rhs.shape[1] <= self.max_columns:
+            shape = getattr(rhs, "shape", None)
+            raise ValueError(f"request {req.rid}: rhs must be an n x r array with 1 <= r <= "
+                             f"{self.max_columns}, got shape {shape}")
         with self.cv:
             req.arrival = self.clock() if req.arrival <= 0 else req.arrival
             # requests share a batch only when they share the operator, precision and tolerance
@@ -264,10 +271,23 @@ class Server:
     def _run(self, e: _Entry, batch: list, bid: int):
         t0 = self.clock()
         w0 = time.perf_counter()
-        B = np.concatenate([r.rhs for r in batch], axis=1)
+        # a request whose row count is not the operator's fails alone; the others are solved
+        rows = getattr(e.solver, "n", None)
+        rows = batch[0].rhs.shape[0] if rows is None else rows
+        misfit = [r for r in batch if r.rhs.shape[0] != rows]
+        batch = [r for r in batch if r.rhs.shape[0] == rows]
+        for r in misfit:
+            r.start, r.finish, r.batch_id = t0, self.clock(), bid
+            r.error = f"rhs has {r.rhs.shape[0]} rows, the operator {rows}"
+        if misfit:
+            with self.cv:
+                self.stats["failed_requests"] += len(misfit)
+        if not batch:
+            return
         prec = batch[0].precision
         rtol = min(r.rtol for r in batch)
         try:
+            B = np.concatenate([r.rhs for r in batch], axis=1)
             Xh, it, rr = self.runner(e, B, rtol, prec)
             err = None
         except Exception as ex:  # a failed batch fails its requests, not the server
@@ -286,6 +306,8 @@ class Server:
             self.stats["batches"] += 1
             self.stats["columns"] += c
             self.stats["solve_ms"] += (time.perf_counter() - w0) * 1e3
+            if err is not None:
+                self.stats["failed_requests"] += len(batch)
 
     def drain(self, timeout: float = 600.0):
         """Wait until every submitted request is done."""

@@ -178,3 +178,44 @@ def test_setups_of_different_operators_overlap():
     srv.close()
     assert peak[0] == 2 and srv.stats["setups"] == 2
     assert all(r.error is None for r in reqs)
+
+
+def test_malformed_requests_are_refused_at_submit():
+    """A right-hand side that is not an n x r array with 1 <= r <= max_columns is refused by
+    submit (it would otherwise stop a worker or wait forever); the server goes on."""
+    import pytest
+    srv, mem, batches = server_with_fakes(capacity=1 << 40, max_columns=8)
+    for rhs in (np.zeros(100), np.zeros((100, 0)), np.zeros((100, 9)), [[0.0]]):
+        r = make_request(1, key=("mesh", 0, 1.0))
+        r.rhs = rhs
+        with pytest.raises(ValueError, match="rhs"):
+            srv.submit(r)
+    good = make_request(2, key=("mesh", 0, 1.0), cols=8)
+    srv.submit(good)
+    srv.drain(30)
+    srv.close()
+    assert good.error is None and np.array_equal(good.x, 2.0 * good.rhs)
+
+
+def test_request_with_the_wrong_row_count_fails_alone():
+    """In a batch for one operator, a request whose rows are not the operator's n fails with its
+    own error; the other requests of the batch are solved."""
+    srv, mem, batches = server_with_fakes(capacity=1 << 40, delay=0.05)
+    inner = srv.solver_factory
+
+    def factory(op):
+        s, stream = inner(op)
+        s.n = op["n"]
+        return s, stream
+    srv.solver_factory = factory
+    key = ("mesh", 0, 1.0)
+    reqs = [make_request(i, key=key, n=100) for i in range(3)]
+    reqs[1].rhs = np.ones((101, 1))
+    for r in reqs:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert "rows" in reqs[1].error and reqs[1].x is None
+    for r in (reqs[0], reqs[2]):
+        assert r.error is None and np.array_equal(r.x, 2.0 * r.rhs)
+    assert srv.stats["failed_requests"] == 1
