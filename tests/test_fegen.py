@@ -137,7 +137,6 @@ def test_graded_mesh_aspect_ratio():
     assert abs(h[1] / h[0] - 1.37618) < 1e-4
 
 
-
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
 def test_patch_test_on_jittered_elements(p):
     """Irons' patch test on trilinear (non-affine) elements: a linear field lies in the mapped
