@@ -202,3 +202,37 @@ def test_single_step_calls_check_lengths(monkeypatch):
     for call in calls:
         with pytest.raises(ValueError, match="shape"):
             call()
+
+
+class _AsCuda:
+    """A CPU tensor that reports itself as a CUDA tensor (everything else forwarded), to run the
+    binding's device-mode checks on the path that accepts the arrays from_problem builds."""
+
+    def __init__(self, t):
+        self._t = t
+
+    is_cuda = True
+
+    def __getattr__(self, name):
+        return getattr(self._t, name)
+
+    def __getitem__(self, i):
+        return self._t[i]
+
+
+def test_device_mode_checks_accept_what_from_problem_builds():
+    import numpy as np
+    import torch
+
+    import fegen
+    prob = fegen.make(2, 2, mesh="jitter", lam=1.0)
+    t = lambda a: _AsCuda(torch.from_numpy(a))
+    g._check_inputs(prob.n, t(prob.row_ptr), t(prob.col), t(prob.val), t(prob.elem_dof), prob.p,
+                    t(prob.coords), True)
+    with pytest.raises(TypeError, match="int64"):
+        g._check_inputs(prob.n, t(prob.row_ptr.astype(np.int32)), t(prob.col), t(prob.val), None, 2, None, True)
+    with pytest.raises(TypeError, match="float64"):
+        g._check_inputs(prob.n, t(prob.row_ptr), t(prob.col), t(prob.val.astype(np.float32)), None, 2, None, True)
+    nc = _AsCuda(torch.from_numpy(np.ascontiguousarray(prob.elem_dof.T)).T)
+    with pytest.raises(ValueError, match="contiguous"):
+        g._check_inputs(prob.n, t(prob.row_ptr), t(prob.col), t(prob.val), nc, 2, None, True)
