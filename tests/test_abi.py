@@ -236,3 +236,16 @@ def test_device_mode_checks_accept_what_from_problem_builds():
     nc = _AsCuda(torch.from_numpy(np.ascontiguousarray(prob.elem_dof.T)).T)
     with pytest.raises(ValueError, match="contiguous"):
         g._check_inputs(prob.n, t(prob.row_ptr), t(prob.col), t(prob.val), nc, 2, None, True)
+
+
+def test_every_entry_point_is_documented_in_the_header():
+    """Each declared entry point has a comment of its own just above it, or is named in one (the
+    header states argument meaning, layout, ownership and errors there)."""
+    with open(os.path.join(ROOT, "include", "giamg.h")) as f:
+        text = f.read()
+    comments = " ".join(re.findall(r"/\*.*?\*/", text, re.S))
+    lines = text.splitlines()
+    for name in declared():
+        i = next(k for k, l in enumerate(lines) if "GIAMG_API" in l and re.search(r"\b" + name + r"\s*\(", l))
+        above = "\n".join(lines[max(0, i - 4):i])
+        assert name in comments or "*/" in above, name
