@@ -156,6 +156,28 @@ def test_patch_test_on_jittered_elements(p):
         assert np.max(np.abs(r[inner])) <= 1e-13 * scale * np.max(np.abs(u))
 
 
+
+@pytest.mark.parametrize("p", [2, 3, 4, 6])
+def test_patch_test_modal_basis(p):
+    """The patch test in the modal basis: the vertex modes are the trilinear shape functions, so a
+    linear field is its vertex values on the vertex modes and zero on every bubble; K u vanishes
+    at every mode whose support misses the domain's boundary.  A bubble derivative inconsistent
+    with its function (the Jacobi recurrence, the P^(1,1)' = (n+3)/2 P^(2,2) identity) breaks
+    the integral of phi' over an element and fails here."""
+    import numpy as np
+    n = 3
+    P = fegen.make(n, p, mesh="jitter", lam=0.0, dirichlet=False, rhs="none", basis="modal")
+    K = P.scipy()
+    N1 = n * p + 1
+    g = np.arange(P.n)
+    I, J, L = g // (N1 * N1), (g // N1) % N1, g % N1
+    vertex = (I % p == 0) & (J % p == 0) & (L % p == 0)
+    inner = (I > 0) & (I < N1 - 1) & (J > 0) & (J < N1 - 1) & (L > 0) & (L < N1 - 1)
+    scale = abs(K).max()
+    for d in range(3):
+        u = np.where(vertex, P.coords[:, d], 0.0)
+        assert np.max(np.abs((K @ u)[inner])) <= 1e-13 * scale * np.max(np.abs(u))
+
 @pytest.mark.parametrize("mesh", ["uniform", "jitter"])
 def test_fourier_load_moments(mesh):
     """rhs("fourier") loads f = sum c_k sin(k1 pi x) sin(k2 pi y) sin(k3 pi z), k in 1..4, by

@@ -27,7 +27,8 @@ import fegen
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# name: (source file, text, replacement, occurrences, pins that must catch it)
+# name: (source file, text, replacement, occurrences, pins that must catch it: a -k expression
+#        over the package's pin file, or (pin file, expression))
 MUTATIONS = {
     # GLL nodes: the Legendre three-term recurrence with a flipped sign
     "gll_recurrence_sign": (
@@ -239,6 +240,19 @@ MUTATIONS = {
     "generator_dirichlet_load": (
         "fegen/fegen.c", "    if (!c->bnd[g])\n      for (int64_t t", "    if (1)\n      for (int64_t t", 1,
         "test_variable_coefficient_manufactured_solution"),
+    # modal basis: the Jacobi recurrence's last term with the wrong sign
+    "generator_jacobi_recurrence": (
+        "fegen/fegen.c", "const double p2 = (a2 * p1 - a3 * p0) / a1;", "const double p2 = (a2 * p1 + a3 * p0) / a1;", 1,
+        ("test_oracle_pins.py", "test_modal_pcg_matches_dense_solve_and_nodal_energy")),
+    # modal basis: the derivative identity's factor (n + 2)/2 for (n + 3)/2
+    "generator_modal_derivative_factor": (
+        "fegen/fegen.c", "const double dp = n > 0 ? 0.5 * (n + 3.0) * fg_jacobi(n - 1, 2.0, 2.0, x) : 0.0;",
+        "const double dp = n > 0 ? 0.5 * (n + 2.0) * fg_jacobi(n - 1, 2.0, 2.0, x) : 0.0;", 1,
+        "test_patch_test_modal_basis"),
+    # modal basis: the product rule's first term with the wrong sign
+    "generator_modal_derivative_sign": (
+        "fegen/fegen.c", "return -0.5 * x * fg_jacobi(n, 1.0, 1.0, x) + 0.25", "return 0.5 * x * fg_jacobi(n, 1.0, 1.0, x) + 0.25", 1,
+        "test_patch_test_modal_basis"),
     # the Fourier modes start at k = 0
     "generator_fourier_mode": (
         "fegen/fegen.c", "sx[k] = sin((k + 1) * FG_PI * x[0]);", "sx[k] = sin(k * FG_PI * x[0]);", 1,
@@ -276,7 +290,8 @@ def _case(base, name):
     if name.startswith("control_"):
         package = name[len("control_"):]
         _copy_tree(dst, rebuild_generator=package == "fegen")
-        pins = " or ".join(sorted({m[4] for m in MUTATIONS.values() if m[0].startswith(package + "/")}))
+        pins = " or ".join(sorted({m[4] for m in MUTATIONS.values()
+                                   if m[0].startswith(package + "/") and isinstance(m[4], str)}))
         return name, _run_pins(dst, PIN_FILES[package], pins, package)
     fname, old, new, count, pins = MUTATIONS[name]
     package = fname.split("/")[0]
@@ -288,7 +303,8 @@ def _case(base, name):
         return name, ("missing", src.count(old), "")
     with open(path, "w") as f:
         f.write(src.replace(old, new))
-    return name, _run_pins(dst, PIN_FILES[package], pins, package)
+    pin_file, expr = pins if isinstance(pins, tuple) else (PIN_FILES[package], pins)
+    return name, _run_pins(dst, pin_file, expr, package)
 
 
 @pytest.fixture(scope="module")
