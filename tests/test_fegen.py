@@ -128,6 +128,28 @@ def test_renumbering_and_element_symmetries_give_the_same_operator():
     assert same_order < base.n_elem
 
 
+
+def test_jittered_mesh_recipe():
+    """Jittered meshes: boundary vertices stay on the grid (the cube is kept), every interior
+    vertex is moved per coordinate by an independent offset uniform in [-0.2 h, 0.2 h] (so at most
+    0.2 h, with mean magnitude 0.1 h and no correlation between the coordinates)."""
+    import numpy as np
+    n = 8
+    P = fegen.make(n, 1, mesh="jitter", rhs="none", with_values=False)
+    X = P.coords.reshape(n + 1, n + 1, n + 1, 3)
+    grid = np.stack(np.meshgrid(*[np.arange(n + 1) / n] * 3, indexing="ij"), axis=-1)
+    off = (X - grid) * n
+    bnd = np.zeros((n + 1,) * 3, bool)
+    bnd[[0, -1], :, :] = bnd[:, [0, -1], :] = bnd[:, :, [0, -1]] = True
+    assert np.all(off[bnd] == 0.0)
+    inner = off[~bnd]                                  # (n-1)^3 x 3 offsets in units of h
+    assert np.max(np.abs(inner)) <= 0.2
+    assert abs(np.mean(np.abs(inner)) - 0.1) < 0.01    # 1029 samples: standard error 0.0018
+    for d in range(3):                                 # 343 per coordinate
+        assert abs(inner[:, d].mean()) < 0.03          # mean 0, standard error 0.0062
+        assert abs(inner[:, d].std() - 0.2 / np.sqrt(3.0)) < 0.015
+    assert abs(np.corrcoef(inner[:, 0], inner[:, 1])[0, 1]) < 0.15
+
 def test_graded_mesh_aspect_ratio():
     P = fegen.make(12, 1, mesh="graded", rhs="none", with_values=False)
     z = np.unique(np.round(P.coords[:, 2], 12))

@@ -253,6 +253,11 @@ MUTATIONS = {
     "generator_modal_derivative_sign": (
         "fegen/fegen.c", "return -0.5 * x * fg_jacobi(n, 1.0, 1.0, x) + 0.25", "return 0.5 * x * fg_jacobi(n, 1.0, 1.0, x) + 0.25", 1,
         "test_patch_test_modal_basis"),
+    # the jitter drawn on [0, 1) instead of [-1, 1) times 0.2 h (every vertex pushed one way)
+    "generator_jitter_range": (
+        "fegen/fegen.c", "x += (2.0 * fg_unif(prm->mesh_seed, 3 * vid + 0) - 1.0) * prm->jitter / c->nx;",
+        "x += fg_unif(prm->mesh_seed, 3 * vid + 0) * prm->jitter / c->nx;", 1,
+        "test_jittered_mesh_recipe"),
     # the Fourier modes start at k = 0
     "generator_fourier_mode": (
         "fegen/fegen.c", "sx[k] = sin((k + 1) * FG_PI * x[0]);", "sx[k] = sin(k * FG_PI * x[0]);", 1,
