@@ -271,13 +271,17 @@ GIAMG_API int giamg_launch_count(int64_t* count);
  * Callers that cannot call cudaMalloc -- code whose device memory is owned by another allocator
  * that has reserved the GPU, or a loop that must keep a fixed memory footprint -- get the same
  * number as giamg_solve_stats, which allocates a small buffer on every call.
- *   b, x: device arrays of the handle's n (always device pointers, whatever device_ptrs says);
- *   *true_relres: host output.  Work runs on the handle's stream, which is synchronised.
+ *   b, x: device arrays of the handle's n on the handle's device (always device pointers, whatever
+ *     device_ptrs says); host memory or another device's memory is refused with GIAMG_ERR_ARG.
+ *   *true_relres: host output.  Work runs on the handle's stream, which is synchronised; the
+ *     handle's device is made current for the call and the caller's device restored after it.
  * The partial sums live in a static 1 MiB device array that every GPU loading the library holds
  * until the process exits; matrices with more than 16,777,216 rows are rejected with
- * GIAMG_ERR_ARG.  The first call on a device looks up that array's device address (make it
- * before any stream capture).  All calls on one device share the array, so calls that overlap
- * on the same GPU race; each call writes every entry it reads, so nothing needs clearing. */
+ * GIAMG_ERR_ARG.  giamg_setup loads that array (and this call's kernels) on the handle's device
+ * and looks up its device address, so the array exists once setup has returned and no call here
+ * loads or allocates anything, its first one included.  All calls on one device share the array,
+ * so calls that overlap on the same GPU race; each call writes every entry it reads, so nothing
+ * needs clearing. */
 GIAMG_API int giamg_true_relres_noalloc(giamg_handle h, const double* b, const double* x, double* true_relres);
 
 /* Release the handle and all of its device memory.  NULL is accepted. */

@@ -335,6 +335,21 @@ class Solver:
         """Block CG on the columns of B (n x m, m <= 32).  Returns (X, iters[m], relres[m])."""
         return self.solve_batch(B, rtol=rtol, precision=precision, force_iters=force_iters, X=X, block=True)
 
+    def true_relres_noalloc(self, b, x):
+        """||b - A x|| / ||b|| on the finest level through giamg_true_relres_noalloc, which allocates
+        no device memory.  b and x: contiguous float64 CUDA tensors of length n on the handle's
+        device (whatever the handle's pointer mode)."""
+        import torch
+        for name, a in (("b", b), ("x", x)):
+            if not isinstance(a, torch.Tensor) or not a.is_cuda:
+                raise TypeError(f"{name}: giamg_true_relres_noalloc needs a CUDA tensor")
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise TypeError(f"{name}: expected a contiguous float64 CUDA tensor")
+            self._check_shape(name, a, (self.n,))
+        out = ctypes.c_double()
+        _check(lib().giamg_true_relres_noalloc(self._h, _ptr(b), _ptr(x), ctypes.byref(out)))
+        return out.value
+
     def stats(self, hist_len=0):
         hist = np.zeros(max(hist_len, 1))
         tr = ctypes.c_double()

@@ -556,11 +556,8 @@ void bat_rows_launch32(const DCSR& A, int m, int mode, const float* val, const f
 template <typename V>
 static void bp_restrict_t(const Level& L, int m, const V* rf, V* rc, const V* p1d, V* part, cudaStream_t s) {
   const size_t sm = brestrict_smem<V>(L.p, L.q, m);
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(bp_restrict_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(bp_restrict_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); });
   GIAMG_CHECK(sm <= 200 * 1024, GIAMG_ERR_ARG, "batched restriction: too many columns for the element order");
   { bp_restrict_kernel<V><<<(unsigned)L.n_elem, 256, sm, s>>>(L.n_elem, L.p, L.q, m, L.l2g.get(), L.own.get(), p1d, rf, part); note_launch(); }
   { bp_gather_kernel<V><<<grid_for(L.n_next * m, 256), 256, 0, s>>>(L.n_next, m, L.cinc_ptr.get(), L.cinc.get(), part, rc); note_launch(); }
@@ -569,11 +566,8 @@ static void bp_restrict_t(const Level& L, int m, const V* rf, V* rc, const V* p1
 template <typename V>
 static void bp_prolong_t(const Level& L, int m, const V* ec, V* xf, const V* p1d, cudaStream_t s) {
   const size_t sm = bprolong_smem<V>(L.p, L.q, m);
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(bp_prolong_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(bp_prolong_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); });
   GIAMG_CHECK(sm <= 200 * 1024, GIAMG_ERR_ARG, "batched prolongation: too many columns for the element order");
   { bp_prolong_kernel<V><<<(unsigned)L.n_elem, 256, sm, s>>>(L.n_elem, L.p, L.q, m, L.l2g.get(), L.own.get(), L.l2g_c.get(), p1d, ec, xf); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());

@@ -397,6 +397,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     H.opt = opt;
     H.stream = s;
     GIAMG_CUDA(cudaGetDevice(&H.device));
+    noalloc_prepare();  // the allocation-free residual check's static scratch, loaded while allocating is allowed
     H.n = n;
     Level* L0 = new Level();
     H.lev.push_back(L0);

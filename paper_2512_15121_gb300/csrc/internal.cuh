@@ -36,6 +36,25 @@ void set_error(int code, const std::string& msg);
     if (!(cond)) throw ::giamg::Error{(code), (msg)}; \
   } while (0)
 
+// A per-function setting that belongs to one device (cudaFuncSetAttribute applies to the device
+// current at the call): once(f) runs f the first time it is reached with a given device current.
+// Two threads may both run f for the same device; every f here sets the same value, so that
+// is harmless.
+class PerDevice {
+  std::atomic<unsigned long long> done_{0};
+
+ public:
+  template <typename F>
+  void once(F&& f) {
+    int d = 0;
+    GIAMG_CUDA(cudaGetDevice(&d));
+    const unsigned long long bit = d >= 0 && d < 64 ? 1ull << d : 0ull;
+    if (bit && (done_.load(std::memory_order_acquire) & bit)) return;
+    f();
+    if (bit) done_.fetch_or(bit, std::memory_order_acq_rel);
+  }
+};
+
 // ------------------------------------------------------------------ device memory
 // Owning device buffer (stream-ordered allocation on the handle's stream).
 template <typename T>
@@ -282,6 +301,9 @@ struct Hierarchy {
 
 // the hierarchy behind a C handle (throws GIAMG_ERR_ARG for NULL)
 Hierarchy* hierarchy_of(giamg_handle h);
+// giamg_true_relres_noalloc's static scratch: load its module on the current device and look
+// up the array's address there (called by giamg_setup, while the caller can still allocate)
+void noalloc_prepare();
 
 // ------------------------------------------------------------------ kernels (launchers)
 // reductions: fixed-size grid, partial sums reduced in a fixed order (bitwise reproducible)

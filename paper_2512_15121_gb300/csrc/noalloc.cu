@@ -15,6 +15,11 @@
 // Every call overwrites the scratch entries it reads before reading them (nothing needs
 // clearing).  Each device has its own copy of the array, and all calls on one device share
 // it: two calls that overlap on the same GPU (for example on two streams) race.
+//
+// Loading: with lazy module loading (the CUDA default) this file's module, and with it the array,
+// is loaded on first use.  giamg_setup therefore loads it (noalloc_prepare: the array's address
+// and both kernels) on the handle's device, so a later call allocates nothing, not even on its
+// first use.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,20 +40,23 @@ constexpr int kThreads = 256;  // 8 warps, 32 rows each per chunk
 // [0, kChunks): partial sums of r_i^2; [kChunks, 2 kChunks): of b_i^2; then the two totals
 static __device__ __align__(256) double g_relres_scratch[2 * kChunks + 2];
 
-// The device address of g_relres_scratch, looked up once per device with that device current.
+// The device address of g_relres_scratch, looked up once per device with that device current
+// (in host code the array's name is a host-side stand-in, not a device address).
 std::mutex g_mu;
 double* g_addr[64] = {};
 
-double* scratch_address(int device) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  GIAMG_CHECK(device >= 0 && device < 64, GIAMG_ERR_ARG, "device ordinal out of range");
-  if (!g_addr[device]) {
-    void* p = nullptr;
-    GIAMG_CUDA(cudaGetSymbolAddress(&p, g_relres_scratch));
-    g_addr[device] = static_cast<double*>(p);
+// Makes a device current for the lifetime of the guard and restores the caller's device after.
+struct CurrentDevice {
+  int saved = -1;
+  explicit CurrentDevice(int device) {
+    GIAMG_CUDA(cudaGetDevice(&saved));
+    if (saved != device) GIAMG_CUDA(cudaSetDevice(device));
   }
-  return g_addr[device];
-}
+  ~CurrentDevice() {
+    int now = -1;
+    if (cudaGetDevice(&now) == cudaSuccess && now != saved) cudaSetDevice(saved);
+  }
+};
 
 __global__ void __launch_bounds__(kThreads) relres_chunks(int64_t n, const int64_t* __restrict__ rp,
                                                           const int32_t* __restrict__ ci,
@@ -117,7 +125,46 @@ __global__ void relres_total(int chunks, double* scratch) {
   }
 }
 
+// The scratch address on `device`, which must be current.  The first lookup loads the module
+// (allocating the array) and both kernels, so later launches load nothing.
+double* scratch_address(int device) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  GIAMG_CHECK(device >= 0 && device < 64, GIAMG_ERR_ARG, "device ordinal out of range");
+  if (!g_addr[device]) {
+    void* p = nullptr;
+    GIAMG_CUDA(cudaGetSymbolAddress(&p, g_relres_scratch));
+    cudaFuncAttributes fa;
+    GIAMG_CUDA(cudaFuncGetAttributes(&fa, relres_chunks));
+    GIAMG_CUDA(cudaFuncGetAttributes(&fa, relres_total));
+    g_addr[device] = static_cast<double*>(p);
+  }
+  return g_addr[device];
+}
+
+// b and x must be device (or managed) memory of the handle's device: a host address handed to
+// the kernels would fault, or read host memory through the GPU's mapping.
+void check_device_vector(const void* ptr, int device, const char* name) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error{GIAMG_ERR_ARG, std::string(name) + ": not a pointer the CUDA runtime knows"};
+  }
+  const bool dev = a.type == cudaMemoryTypeDevice && a.device == device;
+  const bool managed = a.type == cudaMemoryTypeManaged;
+  GIAMG_CHECK(dev || managed, GIAMG_ERR_ARG,
+              std::string(name) + ": giamg_true_relres_noalloc needs device memory of the handle's device "
+                                  "(host arrays and other devices' memory are refused)");
+}
+
 }  // namespace
+
+void noalloc_prepare() {
+  int device = 0;
+  GIAMG_CUDA(cudaGetDevice(&device));
+  (void)scratch_address(device);
+}
+
 }  // namespace giamg
 
 using namespace giamg;
@@ -131,9 +178,10 @@ extern "C" int giamg_true_relres_noalloc(giamg_handle h, const double* b, const 
     GIAMG_CHECK(A.n <= kMaxRows, GIAMG_ERR_ARG,
                 "giamg_true_relres_noalloc accepts at most 16,777,216 rows (its static scratch holds 65,536 "
                 "chunk sums of 256 rows); this matrix has " + std::to_string(A.n));
-    int device = 0;
-    GIAMG_CUDA(cudaGetDevice(&device));
-    double* scratch = scratch_address(device);
+    CurrentDevice on(H.device);
+    check_device_vector(b, H.device, "b");
+    check_device_vector(x, H.device, "x");
+    double* scratch = scratch_address(H.device);
     const int chunks = (int)((A.n + kRowsPerChunk - 1) / kRowsPerChunk);
     cudaStream_t s = H.stream;
     if (chunks > 0) {

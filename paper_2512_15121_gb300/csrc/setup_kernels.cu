@@ -858,11 +858,8 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
   C.v.alloc(std::max<int64_t>(C.nnz, 1), s);
   if (n > 0) {
     const size_t sm = sizeof(NumSmem) * kNumWarps;
-    static bool attr = false;
-    if (!attr) {
-      GIAMG_CUDA(cudaFuncSetAttribute(spgemm_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      attr = true;
-    }
+    static PerDevice attr;
+    attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(spgemm_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); });
     { spgemm_numeric<<<blocks_for(n, kNumWarps), kNumWarps * 32, sm, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), B.rp.get(),
                                                                         B.ci.get(), B.v.get(), cnt.get(), C.rp.get(),
                                                                         C.ci.get(), C.v.get()); note_launch(); }

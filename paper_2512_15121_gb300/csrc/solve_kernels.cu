@@ -596,11 +596,8 @@ void launch_grp(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
                 cudaStream_t s) {
   auto k = GrpKernel<V, MODE>::get();
   const size_t sm = sizeof(V) * (size_t)A.grp.cmax;
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)); });
   k<<<(unsigned)A.grp.n_groups, kThreads, sm, s>>>(A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(),
                                                    A.grp.grow.get(), A.rp.get(), val, x, b, y, d, dinv, c1, c2);
   note_launch();
@@ -611,11 +608,8 @@ void launch_hyb(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
                 cudaStream_t s) {
   auto k = HybKernel<V, MODE>::get();
   const size_t sm = sizeof(V) * (size_t)A.grp.cmax;
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)); });
   const int64_t rest_blocks = (A.grp.n_rest * 32 + kThreads - 1) / kThreads;
   k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
       A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
@@ -628,11 +622,8 @@ void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
                 cudaStream_t s) {
   auto k = HyvKernel<V, MODE>::get();
   const size_t sm = (size_t)A.grp.cpmax * sizeof(V);
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)); });
   const V* hv = A.grp.hv.get();
   const int64_t rest_blocks = (A.grp.n_rest * 32 + kThreads - 1) / kThreads;
   k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
@@ -647,11 +638,8 @@ void launch_hy4(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
                 cudaStream_t s) {
   auto k = Hy4Kernel<V, MODE>::get();
   const size_t sm = (size_t)A.grp.cpmax * sizeof(V);
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)); });
   const V* hv = A.grp.hv64.get();
   const int64_t rest_blocks = (A.grp.n_rest * 16 + kThreads - 1) / kThreads;
   k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
@@ -1382,19 +1370,16 @@ int cholesky_factor(double* L, int64_t nc, cudaStream_t s) {
   return h ? GIAMG_ERR_NOT_SPD : GIAMG_OK;
 }
 static void chol_smem_attr() {
-  static bool done = false;
-  if (done) return;
-  GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
-  GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
-  done = true;
+  static PerDevice done;
+  done.once([&] {
+    GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
+    GIAMG_CUDA(cudaFuncSetAttribute(chol_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
+  });
 }
 void chol_inverse(const double* L, int64_t nc, double* Ainv, cudaStream_t s) {
   chol_smem_attr();
-  static bool attr = false;
-  if (!attr) {
-    GIAMG_CUDA(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
-    attr = true;
-  }
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8)); });
   { chol_inverse_kernel<<<(unsigned)nc, 256, sizeof(double) * nc, s>>>(L, nc, Ainv); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
