@@ -247,6 +247,27 @@ GIAMG_API int giamg_level_smooth(giamg_handle h, int level, const double* b, dou
 GIAMG_API int giamg_level_restrict(giamg_handle h, int level, const double* r_f, double* r_c);
 GIAMG_API int giamg_level_prolong(giamg_handle h, int level, const double* e_c, double* x_f);
 GIAMG_API int giamg_coarse_solve(giamg_handle h, const double* r, double* x);
+/*   giamg_level_residual: r = b - A_l x (the residual step of Algorithm 1, FP64). */
+GIAMG_API int giamg_level_residual(giamg_handle h, int level, const double* b, const double* x, double* r);
+
+/* Single steps of the FP32 V-cycle (precision 1), through the same kernels it launches: A_l's
+ * FP32 values, the FP32 diagonal inverse, FP32 interpolation tables and FP32 vectors with FP32
+ * accumulation.  Vectors are float32 (host or device per device_ptrs, caller-owned; lengths n_l of
+ * the level, n_next for the coarse side of a transfer, n_L for the coarsest level).
+ *   giamg_level_residual32: r = b - A_l x.
+ *   giamg_level_smooth32:   Chebyshev smoothing of A_l x = b in place (Sec. 2's smoother with the
+ *                           level's coefficients rounded to FP32; x_is_zero: x enters as 0).
+ *   giamg_level_restrict32: r_c = R_l r_f (element form on p-levels, Algorithm 7's P transposed).
+ *   giamg_level_prolong32:  x_f += P_l e_c (element form on p-levels).
+ *   giamg_coarse_solve32:   x = A_L^-1 r on the coarsest level as the FP32 V-cycle applies it: r
+ *                           widened to FP64, the dense A_L^-1 formed at setup, x rounded to FP32.
+ * GIAMG_ERR_ARG for a level index out of range, a coarsest level passed to a transfer or to the
+ * smoother, or NULL vectors. */
+GIAMG_API int giamg_level_residual32(giamg_handle h, int level, const float* b, const float* x, float* r);
+GIAMG_API int giamg_level_smooth32(giamg_handle h, int level, const float* b, float* x, int x_is_zero);
+GIAMG_API int giamg_level_restrict32(giamg_handle h, int level, const float* r_f, float* r_c);
+GIAMG_API int giamg_level_prolong32(giamg_handle h, int level, const float* e_c, float* x_f);
+GIAMG_API int giamg_coarse_solve32(giamg_handle h, const float* r, float* x);
 
 /* Switch the pointer mode of later calls on this handle (0 host arrays, 1 device arrays). */
 GIAMG_API int giamg_set_device_ptrs(giamg_handle h, int device_ptrs);

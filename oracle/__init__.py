@@ -98,6 +98,13 @@ def _lib():
             L.orc_level_restrict.argtypes = [vp, i32, vp, vp]
             L.orc_level_prolong.argtypes = [vp, i32, vp, vp]
             L.orc_coarse_solve.argtypes = [vp, vp, vp]
+            L.orc_level_residual.argtypes = [vp, i32, vp, vp, vp]
+            L.orc_level_spmv32.argtypes = [vp, i32, vp, vp]
+            L.orc_level_residual32.argtypes = [vp, i32, vp, vp, vp]
+            L.orc_level_cheb32.argtypes = [vp, i32, vp, vp, i32]
+            L.orc_level_restrict32.argtypes = [vp, i32, vp, vp]
+            L.orc_level_prolong32.argtypes = [vp, i32, vp, vp]
+            L.orc_coarse_solve32.argtypes = [vp, vp, vp]
             L.orc_solve.argtypes = [vp, vp, vp, dbl, i32, i32, i32, i32, ctypes.POINTER(i32),
                                     ctypes.POINTER(dbl), vp]
             L.orc_num_threads.restype = i32
@@ -359,6 +366,50 @@ class Hierarchy:
         r = _f64(r)
         x = np.empty_like(r)
         _lib().orc_coarse_solve(self._h, _p(r), _p(x))
+        return x
+
+    def residual(self, l, b, x):
+        """r = b - A_l x (FP64)."""
+        b, x = _f64(b), _f64(x)
+        r = np.empty_like(b)
+        _lib().orc_level_residual(self._h, l, _p(b), _p(x), _p(r))
+        return r
+
+    # FP32 single steps: inputs rounded to float32, results float32
+    def spmv32(self, l, x):
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.empty(self.level_info(l)["n"], np.float32)
+        _lib().orc_level_spmv32(self._h, l, _p(x), _p(y))
+        return y
+
+    def residual32(self, l, b, x):
+        b, x = np.ascontiguousarray(b, np.float32), np.ascontiguousarray(x, np.float32)
+        r = np.empty_like(b)
+        _lib().orc_level_residual32(self._h, l, _p(b), _p(x), _p(r))
+        return r
+
+    def cheb32(self, l, b, x=None):
+        b = np.ascontiguousarray(b, np.float32)
+        x0 = np.zeros_like(b) if x is None else np.array(x, dtype=np.float32, copy=True)
+        _lib().orc_level_cheb32(self._h, l, _p(b), _p(x0), 1 if x is None else 0)
+        return x0
+
+    def restrict32(self, l, rf):
+        rf = np.ascontiguousarray(rf, np.float32)
+        rc = np.empty(self.level_info(l)["n_next"], np.float32)
+        _lib().orc_level_restrict32(self._h, l, _p(rf), _p(rc))
+        return rc
+
+    def prolong32(self, l, ec, xf):
+        ec = np.ascontiguousarray(ec, np.float32)
+        xf = np.array(xf, dtype=np.float32, copy=True)
+        _lib().orc_level_prolong32(self._h, l, _p(ec), _p(xf))
+        return xf
+
+    def coarse_solve32(self, r):
+        r = np.ascontiguousarray(r, np.float32)
+        x = np.empty_like(r)
+        _lib().orc_coarse_solve32(self._h, _p(r), _p(x))
         return x
 
     def solve(self, b, rtol=1e-8, max_iter=1000, force_iters=0, precision=0, flexible=None):

@@ -1048,27 +1048,40 @@ static void orc_vcycle_level(orc_hier* h, int l, const double* b, double* x) {
   orc_cheb(h, L, b, x, 0);                       /* postsmooth */
 }
 
+/* FP32 steps of Algorithm 1: the coarsest solve in FP64 on the widened right-hand side, rounded
+   back to FP32; the residual r = b - A x; the correction x += P e (t: an n-vector of scratch) */
+static void orc_coarse32(orc_level* L, const float* b, float* x) {
+  int64_t n = L->A.n;
+  double* bd = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* xd = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  for (int64_t i = 0; i < n; ++i) bd[i] = (double)b[i];
+  orc_chol_solve((int)n, L->L, bd, xd);
+  for (int64_t i = 0; i < n; ++i) x[i] = (float)xd[i];
+  free(bd); free(xd);
+}
+static void orc_residual32(orc_level* L, const float* b, const float* x, float* r) {
+  int64_t n = L->A.n;
+  orc_spmv32(n, L->A.rp, L->A.ci, L->A32, x, r);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+}
+static void orc_correct32(orc_level* L, const float* e, float* x, float* t) {
+  orc_spmv32(L->P.n, L->P.rp, L->P.ci, L->P32, e, t);
+  for (int64_t i = 0; i < L->A.n; ++i) x[i] = x[i] + t[i];
+}
+
 static void orc_vcycle_level32(orc_hier* h, int l, const float* b, float* x) {
   orc_level* L = &h->lev[l];
-  int64_t n = L->A.n;
   if (L->kind == ORC_KIND_COARSEST) {
-    double* bd = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
-    double* xd = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
-    for (int64_t i = 0; i < n; ++i) bd[i] = (double)b[i];
-    orc_chol_solve((int)n, L->L, bd, xd);
-    for (int64_t i = 0; i < n; ++i) x[i] = (float)xd[i];
-    free(bd); free(xd);
+    orc_coarse32(L, b, x);
     return;
   }
   orc_level* C = &h->lev[l + 1];
-  orc_cheb32(h, L, b, x, 1);
-  orc_spmv32(n, L->A.rp, L->A.ci, L->A32, x, L->r32);
-  for (int64_t i = 0; i < n; ++i) L->r32[i] = b[i] - L->r32[i];
-  orc_spmv32(L->R.n, L->R.rp, L->R.ci, L->R32, L->r32, C->b32);
-  orc_vcycle_level32(h, l + 1, C->b32, C->x32);
-  orc_spmv32(L->P.n, L->P.rp, L->P.ci, L->P32, C->x32, L->r32);
-  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + L->r32[i];
-  orc_cheb32(h, L, b, x, 0);
+  orc_cheb32(h, L, b, x, 1);                                       /* presmooth */
+  orc_residual32(L, b, x, L->r32);                                 /* residual */
+  orc_spmv32(L->R.n, L->R.rp, L->R.ci, L->R32, L->r32, C->b32);    /* restrict */
+  orc_vcycle_level32(h, l + 1, C->b32, C->x32);                    /* recurse */
+  orc_correct32(L, C->x32, x, L->r32);                             /* interpolate and correct */
+  orc_cheb32(h, L, b, x, 0);                                       /* postsmooth */
 }
 
 int orc_vcycle(orc_hier* h, int precision, const double* r, double* z) {
@@ -1111,6 +1124,49 @@ int orc_level_prolong(orc_hier* h, int l, const double* ec, double* xf) {
 int orc_coarse_solve(orc_hier* h, const double* r, double* x) {
   orc_level* L = &h->lev[h->nlev - 1];
   orc_chol_solve((int)L->A.n, L->L, r, x);
+  return ORC_OK;
+}
+int orc_level_residual(orc_hier* h, int l, const double* b, const double* x, double* r) {
+  if (l < 0 || l >= h->nlev) return ORC_ERR_ARG;
+  orc_level* L = &h->lev[l];
+  orc_spmv(&L->A, x, r);
+  for (int64_t i = 0; i < L->A.n; ++i) r[i] = b[i] - r[i];
+  return ORC_OK;
+}
+
+/* single steps of the FP32 V-cycle: the same functions orc_vcycle(precision = 1) applies */
+int orc_level_spmv32(orc_hier* h, int l, const float* x, float* y) {
+  if (l < 0 || l >= h->nlev) return ORC_ERR_ARG;
+  orc_level* L = &h->lev[l];
+  orc_spmv32(L->A.n, L->A.rp, L->A.ci, L->A32, x, y);
+  return ORC_OK;
+}
+int orc_level_residual32(orc_hier* h, int l, const float* b, const float* x, float* r) {
+  if (l < 0 || l >= h->nlev) return ORC_ERR_ARG;
+  orc_residual32(&h->lev[l], b, x, r);
+  return ORC_OK;
+}
+int orc_level_cheb32(orc_hier* h, int l, const float* b, float* x, int x_is_zero) {
+  if (l < 0 || l >= h->nlev || h->lev[l].kind == ORC_KIND_COARSEST) return ORC_ERR_ARG;
+  orc_cheb32(h, &h->lev[l], b, x, x_is_zero);
+  return ORC_OK;
+}
+int orc_level_restrict32(orc_hier* h, int l, const float* rf, float* rc) {
+  if (l < 0 || l >= h->nlev || h->lev[l].kind == ORC_KIND_COARSEST) return ORC_ERR_ARG;
+  orc_level* L = &h->lev[l];
+  orc_spmv32(L->R.n, L->R.rp, L->R.ci, L->R32, rf, rc);
+  return ORC_OK;
+}
+int orc_level_prolong32(orc_hier* h, int l, const float* ec, float* xf) {
+  if (l < 0 || l >= h->nlev || h->lev[l].kind == ORC_KIND_COARSEST) return ORC_ERR_ARG;
+  orc_level* L = &h->lev[l];
+  float* t = (float*)malloc(sizeof(float) * (size_t)(L->A.n > 0 ? L->A.n : 1));
+  orc_correct32(L, ec, xf, t);
+  free(t);
+  return ORC_OK;
+}
+int orc_coarse_solve32(orc_hier* h, const float* r, float* x) {
+  orc_coarse32(&h->lev[h->nlev - 1], r, x);
   return ORC_OK;
 }
 

@@ -101,6 +101,16 @@ int orc_level_cheb(orc_hier* h, int l, const double* b, double* x, int x_is_zero
 int orc_level_restrict(orc_hier* h, int l, const double* rf, double* rc);
 int orc_level_prolong(orc_hier* h, int l, const double* ec, double* xf);
 int orc_coarse_solve(orc_hier* h, const double* r, double* x);
+int orc_level_residual(orc_hier* h, int l, const double* b, const double* x, double* r);
+/* single steps of the FP32 V-cycle (orc_vcycle with precision 1): FP32 copies of A_l, D^-1, P_l
+   and R_l, FP32 vectors and accumulation; the coarsest solve in FP64 on the widened right-hand
+   side, rounded back to FP32 */
+int orc_level_spmv32(orc_hier* h, int l, const float* x, float* y);
+int orc_level_residual32(orc_hier* h, int l, const float* b, const float* x, float* r);
+int orc_level_cheb32(orc_hier* h, int l, const float* b, float* x, int x_is_zero);
+int orc_level_restrict32(orc_hier* h, int l, const float* rf, float* rc);
+int orc_level_prolong32(orc_hier* h, int l, const float* ec, float* xf);
+int orc_coarse_solve32(orc_hier* h, const float* r, float* x);
 
 /* PCG (flexible=0) or flexible CG (flexible=1) with one V-cycle per iteration, x0 = 0.
    force_iters > 0 runs exactly that many iterations.  hist[0..iters] receives the relative

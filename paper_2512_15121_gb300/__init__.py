@@ -27,7 +27,9 @@ EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_e
            "giamg_solve_async", "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
            "giamg_level_rho", "giamg_set_cheb_degree", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
-           "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_free",
+           "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_level_residual",
+           "giamg_level_residual32", "giamg_level_smooth32", "giamg_level_restrict32", "giamg_level_prolong32",
+           "giamg_coarse_solve32", "giamg_free",
            "giamg_last_error", "giamg_set_device_ptrs", "giamg_profile_enable", "giamg_profile_read",
            "giamg_launch_count", "giamg_true_relres_noalloc"]
 
@@ -88,6 +90,12 @@ def lib():
         L.giamg_level_restrict.argtypes = [vp, i32, vp, vp]
         L.giamg_level_prolong.argtypes = [vp, i32, vp, vp]
         L.giamg_coarse_solve.argtypes = [vp, vp, vp]
+        L.giamg_level_residual.argtypes = [vp, i32, vp, vp, vp]
+        L.giamg_level_residual32.argtypes = [vp, i32, vp, vp, vp]
+        L.giamg_level_smooth32.argtypes = [vp, i32, vp, vp, i32]
+        L.giamg_level_restrict32.argtypes = [vp, i32, vp, vp]
+        L.giamg_level_prolong32.argtypes = [vp, i32, vp, vp]
+        L.giamg_coarse_solve32.argtypes = [vp, vp, vp]
         L.giamg_free.argtypes = [vp]
         L.giamg_set_device_ptrs.argtypes = [vp, i32]
         L.giamg_profile_enable.argtypes = [vp, i32]
@@ -483,6 +491,78 @@ class Solver:
         xo = self._in(xf).clone() if self.device else self._in(xf).copy()
         _check(lib().giamg_level_prolong(self._h, l, _ptr(ec), _ptr(xo)))
         return xo
+
+    def residual(self, l, b, x):
+        """r = b - A_l x (FP64)."""
+        n = self.level_info(l)["n"]
+        b, x = self._in(b), self._in(x)
+        self._check_shape("b", b, (n,))
+        self._check_shape("x", x, (n,))
+        r = self._vec(n)
+        _check(lib().giamg_level_residual(self._h, l, _ptr(b), _ptr(x), _ptr(r)))
+        return r
+
+    # ---- single steps of the FP32 V-cycle (float32 vectors)
+    def _in32(self, v):
+        if self.device:
+            import torch
+            if not isinstance(v, torch.Tensor):
+                v = torch.from_numpy(np.ascontiguousarray(v))
+            return v.to("cuda", torch.float32).contiguous()
+        return np.ascontiguousarray(v, np.float32)
+
+    def _vec32(self, n):
+        if self.device:
+            import torch
+            return torch.empty(n, dtype=torch.float32, device="cuda")
+        return np.empty(n, np.float32)
+
+    def _copy32(self, v):
+        v = self._in32(v)
+        return v.clone() if self.device else v.copy()
+
+    def residual32(self, l, b, x):
+        n = self.level_info(l)["n"]
+        b, x = self._in32(b), self._in32(x)
+        self._check_shape("b", b, (n,))
+        self._check_shape("x", x, (n,))
+        r = self._vec32(n)
+        _check(lib().giamg_level_residual32(self._h, l, _ptr(b), _ptr(x), _ptr(r)))
+        return r
+
+    def smooth32(self, l, b, x=None):
+        n = self.level_info(l)["n"]
+        b = self._in32(b)
+        self._check_shape("b", b, (n,))
+        xo = self._vec32(n) if x is None else self._copy32(x)
+        self._check_shape("x", xo, (n,))
+        _check(lib().giamg_level_smooth32(self._h, l, _ptr(b), _ptr(xo), 1 if x is None else 0))
+        return xo
+
+    def restrict32(self, l, rf):
+        info = self.level_info(l)
+        rf = self._in32(rf)
+        self._check_shape("rf", rf, (info["n"],))
+        rc = self._vec32(info["n_next"])
+        _check(lib().giamg_level_restrict32(self._h, l, _ptr(rf), _ptr(rc)))
+        return rc
+
+    def prolong32(self, l, ec, xf):
+        info = self.level_info(l)
+        ec = self._in32(ec)
+        self._check_shape("ec", ec, (info["n_next"],))
+        xo = self._copy32(xf)
+        self._check_shape("xf", xo, (info["n"],))
+        _check(lib().giamg_level_prolong32(self._h, l, _ptr(ec), _ptr(xo)))
+        return xo
+
+    def coarse_solve32(self, r):
+        n = self.level_info(self.num_levels - 1)["n"]
+        r = self._in32(r)
+        self._check_shape("r", r, (n,))
+        x = self._vec32(n)
+        _check(lib().giamg_coarse_solve32(self._h, _ptr(r), _ptr(x)))
+        return x
 
     def coarse_solve(self, r):
         r = self._in(r)

@@ -1498,6 +1498,119 @@ int giamg_coarse_solve(giamg_handle h, const double* r, double* x) {
   });
 }
 
+int giamg_level_residual(giamg_handle h, int level, const double* b, const double* x, double* r) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(b && x && r, GIAMG_ERR_ARG, "b, x and r are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVec bi(b, L.A.n, dev, s);
+    InVec xi(x, L.A.n, dev, s);
+    OutVec ro(r, L.A.n, dev, s, false);
+    residual(L.A, bi.d, xi.d, ro.d, s, L.avg_row);
+    ro.finish();
+    return GIAMG_OK;
+  });
+}
+
+// ---- single steps of the FP32 V-cycle: the launchers vcycle32 uses, on FP32 vectors
+int giamg_level_residual32(giamg_handle h, int level, const float* b, const float* x, float* r) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(b && x && r, GIAMG_ERR_ARG, "b, x and r are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVecT<float> bi(b, L.A.n, dev, s);
+    InVecT<float> xi(x, L.A.n, dev, s);
+    OutVecT<float> ro(r, L.A.n, dev, s, false);
+    residual32(L.A, bi.d, xi.d, ro.d, s, L.avg_row);
+    ro.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_smooth32(giamg_handle h, int level, const float* b, float* x, int x_is_zero) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level is solved, not smoothed");
+    GIAMG_CHECK(b && x, GIAMG_ERR_ARG, "b and x are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    const int64_t n = L.A.n;
+    InVecT<float> bi(b, n, dev, s);
+    OutVecT<float> xo(x, n, dev, s, !x_is_zero);
+    const Cheb& c = C.ex[level].cheb;
+    float* xa = L.x32.get();
+    float* xb = L.x232.get();
+    int j0 = 0;
+    if (x_is_zero) {
+      cheb_first32(n, bi.d, L.dinv32.get(), (float)c.c2[0], xa, L.d32.get(), s);
+      j0 = 1;
+    } else if (n > 0) {
+      GIAMG_CUDA(cudaMemcpyAsync(xa, xo.d, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int j = j0; j < (int)c.c1.size(); ++j) {
+      cheb_step32(L.A, bi.d, xa, xb, L.d32.get(), L.dinv32.get(), (float)c.c1[j], (float)c.c2[j], s, L.avg_row);
+      std::swap(xa, xb);
+    }
+    if (n > 0) GIAMG_CUDA(cudaMemcpyAsync(xo.d, xa, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    xo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_restrict32(giamg_handle h, int level, const float* r_f, float* r_c) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level has no restriction");
+    GIAMG_CHECK(r_f && r_c, GIAMG_ERR_ARG, "r_f and r_c are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVecT<float> ri(r_f, L.A.n, dev, s);
+    OutVecT<float> ro(r_c, L.n_next, dev, s, false);
+    if (L.kind == GIAMG_LEVEL_P) p_restrict32(L, ri.d, ro.d, s);
+    else h_restrict32(L, ri.d, ro.d, s);
+    ro.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_level_prolong32(giamg_handle h, int level, const float* e_c, float* x_f) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(L.kind != GIAMG_LEVEL_COARSEST, GIAMG_ERR_ARG, "the coarsest level has no prolongation");
+    GIAMG_CHECK(e_c && x_f, GIAMG_ERR_ARG, "e_c and x_f are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVecT<float> ei(e_c, L.n_next, dev, s);
+    OutVecT<float> xo(x_f, L.A.n, dev, s, true);
+    if (L.kind == GIAMG_LEVEL_P) p_prolong32(L, ei.d, xo.d, s);
+    else h_prolong32(L, ei.d, xo.d, s);
+    xo.finish();
+    return GIAMG_OK;
+  });
+}
+
+int giamg_coarse_solve32(giamg_handle h, const float* r, float* x) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Level& L = *C.H->lev.back();
+    GIAMG_CHECK(r && x, GIAMG_ERR_ARG, "r and x are required");
+    cudaStream_t s = C.H->stream;
+    const bool dev = C.H->opt.device_ptrs != 0;
+    InVecT<float> ri(r, L.nc, dev, s);
+    OutVecT<float> xo(x, L.nc, dev, s, false);
+    inverse_apply32(L.Ainv.get(), L.nc, ri.d, xo.d, s);
+    xo.finish();
+    return GIAMG_OK;
+  });
+}
+
 int giamg_free(giamg_handle h) {
   if (!h) return GIAMG_OK;
   return guarded([&] {

@@ -13,6 +13,10 @@ to a minute on the host cores, so the checks are the ones of the small cases:
   FP64 PCG with the oracle's iteration count forced                             x within 1e-10
   FP64 PCG stopping freely                                                      iterations +-1
   FP32 V-cycle in FP64 flexible CG: true relative residual (oracle product)     <= 1.5e-8
+  FP32 V-cycle against the oracle's FP32 V-cycle, element by element            1e-5 of max |z|
+  finest level's FP32 residual and smoother (the headline kernels: the vector
+    hybrid row form at p = 6 and 8) against the oracle's, row by row            rounding bounds
+    (tests/fp32_bounds.py)
   32-column batch (Poisson): three columns against the oracle's single solves   x within 1e-10
                              every column's true residual (oracle product)      <= 1.5e-8
   32-column block CG (Poisson), both V-cycle precisions: every column's true
@@ -32,6 +36,7 @@ if not torch.cuda.is_available():
 import fegen  # noqa: E402
 import oracle  # noqa: E402
 import paper_2512_15121_gb300 as g  # noqa: E402
+from fp32_bounds import fp32_step_checks  # noqa: E402
 
 NAMES = ["helmholtz_4cube_p4", "helmholtz_16cube_jitter_p6", "poisson_24cube_jitter_p4",
          "helmholtz_12cube_graded_p8"]
@@ -97,6 +102,7 @@ def test_fp64_pcg_forced_and_free(full):
     x, it, _ = full.gpu.solve(b, rtol=1e-8, force_iters=ito)
     assert it == ito
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= 1e-10 * np.max(np.abs(xo))
     x2, it2, rr2 = full.gpu.solve(b, rtol=1e-8)
     assert abs(it2 - ito) <= 1 and rr2 <= 1e-8
 
@@ -107,6 +113,17 @@ def test_mixed_precision_true_residual(full):
     assert rr <= 1e-8
     r_true = b - full.orc.spmv(0, x.cpu().numpy())
     assert np.linalg.norm(r_true) <= 1.5e-8 * np.linalg.norm(b)
+
+
+def test_fp32_vcycle_and_finest_steps(full):
+    rng = np.random.default_rng(21)
+    r = rng.standard_normal(full.prob.n)
+    z32 = full.gpu.vcycle(dev(r), 1).cpu().numpy()
+    zo32 = full.orc.vcycle(r, 1)
+    assert np.max(np.abs(z32 - zo32)) <= 1e-5 * np.max(np.abs(zo32))
+    form = full.gpu.kernel(0, 1)[1]
+    fp32_step_checks(full.orc, full.gpu, full.k, rng, levels=[0], smooth_starts=(None,))
+    print(f"{full.name}: FP32 finest-level form {form}")
 
 
 def test_batch_32_columns(full):

@@ -136,6 +136,22 @@ MUTATIONS = {
     "chebyshev_fp32_coefficient": (
         "oracle/oracle.c", "float c1 = (float)(rho_new * rho)", "float c1 = (float)(rho_new)", 1,
         "test_fp32_vcycle_is_the_fp64_operator_to_fp32_rounding"),
+    # FP32 V-cycle: the residual step's sign flipped
+    "fp32_residual_sign": (
+        "oracle/oracle.c",
+        "  orc_spmv32(n, L->A.rp, L->A.ci, L->A32, x, r);\n  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];\n}",
+        "  orc_spmv32(n, L->A.rp, L->A.ci, L->A32, x, r);\n  for (int64_t i = 0; i < n; ++i) r[i] = r[i] - b[i];\n}", 1,
+        "test_fp32_single_steps_are_their_definitions"),
+    # FP32 V-cycle: the correction overwrites the smoothed iterate
+    "fp32_correction_overwrites": (
+        "oracle/oracle.c", "for (int64_t i = 0; i < L->A.n; ++i) x[i] = x[i] + t[i];",
+        "for (int64_t i = 0; i < L->A.n; ++i) x[i] = t[i];", 1,
+        "test_fp32_single_steps_are_their_definitions"),
+    # FP32 V-cycle: the coarsest step hands back its right-hand side instead of the solution
+    "fp32_coarse_returns_rhs": (
+        "oracle/oracle.c", "for (int64_t i = 0; i < n; ++i) x[i] = (float)xd[i];",
+        "for (int64_t i = 0; i < n; ++i) x[i] = (float)bd[i];", 1,
+        "test_fp32_single_steps_are_their_definitions"),
     # Algorithm 1: presmoothing left out (x stays zero before the residual)
     "vcycle_no_presmoothing": (
         "oracle/oracle.c", "orc_cheb(h, L, b, x, 1);                       /* presmooth */",
@@ -274,7 +290,7 @@ def _copy_tree(dst, rebuild_generator):
     shutil.copytree(os.path.join(ROOT, "fegen"), os.path.join(dst, "fegen"),
                     ignore=shutil.ignore_patterns(*gen_skip))
     os.makedirs(os.path.join(dst, "tests"))
-    for f in ("conftest.py", *PIN_FILES.values()):
+    for f in ("conftest.py", "fp32_bounds.py", *PIN_FILES.values()):
         shutil.copy2(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
 

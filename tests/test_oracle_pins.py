@@ -491,6 +491,52 @@ def test_single_steps_are_their_definitions():
         assert np.allclose(H.restrict(l, x), P.T @ x, rtol=1e-13, atol=1e-13 * np.abs(x).max())
         assert np.allclose(H.prolong(l, e, x), x + P @ e, rtol=1e-13, atol=1e-13 * np.abs(e).max())
 
+def test_fp32_single_steps_are_their_definitions():
+    """The FP32 steps of the V-cycle (the entry points the GPU's FP32 kernels are compared with):
+    each equals its FP64 definition on the same FP32 inputs -- b - A_l x, P_l^T r_f, x_f + P_l e_c,
+    and the Chebyshev smoother pinned above -- within the worst-case FP32 rounding bound of
+    tests/fp32_bounds.py, row by row; the coarsest step is A_L^-1 r in FP64 rounded to FP32 (one
+    unit in the last place).  A wrong coefficient or a dropped term moves a row by the size of a
+    term, 10^4 or more times the bound."""
+    from fp32_bounds import U, f32, csr, residual_bound, product_bound, cheb_bound, cheb_coeffs
+    prob = fegen.make(4, 4, mesh="jitter", lam=1.0)
+    for k in (2, 3):
+        H = oracle.Hierarchy.from_problem(prob, coarse_max=100, cheb_degree=k)
+        rng = np.random.default_rng(16 + k)
+        assert H.level_info(H.num_levels - 2)["kind"] == oracle.KIND_H
+        for l in range(H.num_levels):
+            info = H.level_info(l)
+            rp, ci, v, _ = H.level(l)
+            A = csr(rp, ci, v, info["n"])
+            b, x = f32(rng.standard_normal(info["n"])), f32(rng.standard_normal(info["n"]))
+            y = H.spmv32(l, x).astype(np.float64)
+            assert np.all(np.abs(y - A @ x) <= product_bound(A, x)), l
+            r = H.residual32(l, b, x).astype(np.float64)
+            assert np.all(np.abs(r - (b - A @ x)) <= residual_bound(A, b, x)), l
+            r64 = H.residual(l, b, x)
+            assert np.allclose(r64, b - A @ x, rtol=0, atol=1e-13 * (np.abs(b) + abs(A) @ np.abs(x)).max())
+            if info["kind"] == oracle.KIND_COARSEST:
+                z = H.coarse_solve32(b).astype(np.float64)
+                ze = np.linalg.solve(A.toarray(), b)
+                assert np.all(np.abs(z - ze) <= 2 * U * np.abs(ze) + 1e-12 * np.abs(ze).max()), l
+                continue
+            c1, c2 = cheb_coeffs(H.rho_hat(l), k)
+            dinv = 1.0 / A.diagonal()
+            for start in (None, x):
+                xs = H.cheb32(l, b, start).astype(np.float64)
+                xe, E = cheb_bound(A, dinv, c1, c2, b, start)
+                assert np.all(np.abs(xs - xe) <= E), (l, start is None)
+                # the FP64 smoother on the same inputs: the exact recurrence
+                assert np.allclose(H.cheb(l, b, start), xe, rtol=0, atol=1e-12 * np.abs(xe).max())
+            prp, pci, pv, m = H.prolongation(l)
+            P = csr(prp, pci, pv, m)
+            assert np.all(np.abs(H.restrict32(l, b).astype(np.float64) - P.T @ b) <= product_bound(P.T.tocsr(), b)), l
+            e = f32(rng.standard_normal(m))
+            xf = H.prolong32(l, e, x).astype(np.float64)
+            bound = product_bound(P, e) + U * (np.abs(x) + abs(P) @ np.abs(e))
+            assert np.all(np.abs(xf - (x + P @ e)) <= bound), l
+
+
 # ----------------------------------------------------------------------------- coarsest
 def test_cholesky_matches_numpy():
     rng = np.random.default_rng(5)
