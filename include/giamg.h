@@ -83,18 +83,22 @@ typedef struct {
                              with identical column sets (x gathered once per group); detection is
                              exact, plain CSR otherwise; 0: plain CSR everywhere */
   int autotune;           /* 1: time the row-kernel variants (CSR, row patterns, row groups,
-                             hybrid, vector hybrid) on every large level at setup and keep the
-                             fastest product; 0 (default): the variants measured best inside the
-                             solve (vector hybrid where there are at least 4096 groups of 16 or
-                             more rows averaging 192 or more columns; else FP32 rows on row
-                             patterns and FP64 rows on CSR with 16 threads per row) */
+                             hybrid, vector hybrid, sliced) on every large level at setup and keep
+                             the fastest product; 0 (default): the variants measured best inside
+                             the solve (FP64: the sliced form on levels of at least 2^18 rows;
+                             FP32: the vector hybrid where there are at least 4096 groups of 16 or
+                             more rows averaging 192 or more columns, else the sliced form on
+                             levels of at least 2^18 rows; on smaller levels FP32 rows on row
+                             patterns and FP64 rows on CSR) */
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
                              groups, 4 hybrid (groups of at least 16 rows by the group kernel, the
                              other rows by the row-pattern kernel), 5 vector hybrid (the big
                              groups' values from a group-major copy with rows padded to 16 bytes,
                              read with 16-byte loads: FP32 one warp per row, FP64 4 lanes per row
-                             and 8 rows of a group per warp); each falls back to CSR where the
-                             form is not available */
+                             and 8 rows of a group per warp), 6 sliced (every row in slices of
+                             32 rows of equal length, one lane per row, values interleaved by
+                             column and read with 16-byte loads, columns from the row group's
+                             list); each falls back to CSR where the form is not available */
   int row_threads;        /* force threads per row (4, 8, 16, 32); 0 automatic */
   int prefetch_rows;      /* row-pattern kernels: every block prefetches into L2 the values of the
                              block this many rows ahead; 0 off, -1 (default) automatic */
@@ -218,8 +222,8 @@ GIAMG_API int giamg_export_prolongation(giamg_handle h, int level, int64_t* row_
 GIAMG_API int giamg_level_templates(giamg_handle h, int level, int64_t* n_templates, int64_t* n_offsets);
 /* Row-kernel variant used on A_l for precision 0 (FP64) or 1 (FP32): threads per row and the
  * form (*pattern: 0 CSR, 1 row patterns, 2 row groups with identical column sets, 3 hybrid of
- * big row groups and row patterns, 4 vector hybrid), chosen by the setup-time tuner when
- * autotune is set. */
+ * big row groups and row patterns, 4 vector hybrid, 5 sliced), chosen by the setup-time tuner
+ * when autotune is set. */
 GIAMG_API int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern);
 /* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */
 GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);

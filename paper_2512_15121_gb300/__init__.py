@@ -427,7 +427,7 @@ class Solver:
     def kernel(self, l, precision):
         t, p = ctypes.c_int(), ctypes.c_int()
         _check(lib().giamg_level_kernel(self._h, l, precision, ctypes.byref(t), ctypes.byref(p)))
-        return t.value, ["csr", "pattern", "groups", "hybrid", "vector"][p.value]
+        return t.value, ["csr", "pattern", "groups", "hybrid", "vector", "sliced"][p.value]
 
     def set_cheb_degree(self, k: int):
         """Smoother degree k on every level, keeping the hierarchy (giamg_set_cheb_degree)."""

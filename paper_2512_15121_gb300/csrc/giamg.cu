@@ -356,7 +356,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
   GIAMG_CHECK(opt.max_levels >= 1 && opt.max_levels <= 64, GIAMG_ERR_ARG, "max_levels must be in [1, 64]");
   GIAMG_CHECK(opt.lanczos_steps >= 1, GIAMG_ERR_ARG, "lanczos_steps must be >= 1");
   GIAMG_CHECK(opt.precision == 0 || opt.precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
-  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 5, GIAMG_ERR_ARG, "row_form must be in 0..5");
+  GIAMG_CHECK(opt.row_form >= 0 && opt.row_form <= 6, GIAMG_ERR_ARG, "row_form must be in 0..6");
   GIAMG_CHECK(opt.row_threads == 0 || opt.row_threads == 4 || opt.row_threads == 8 || opt.row_threads == 16 ||
                   opt.row_threads == 32,
               GIAMG_ERR_ARG, "row_threads must be 0, 4, 8, 16 or 32");
@@ -520,6 +520,13 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       if (L.A.var64.vector) {
         L.A.var64.vector = hybrid_vector_build(L.A, 0, s);
         clk.mark("group-major FP64 copy", (int)l);
+      }
+      for (int prec = 0; prec < 2; ++prec) {
+        RowVariant& v = prec == 0 ? L.A.var64 : L.A.var32;
+        if (!v.sliced) continue;
+        v.sliced = sliced_build(L.A, prec, s);
+        if (!v.sliced) v.tpr = 0;  // the form does not apply: the default row kernel
+        clk.mark(prec == 0 ? "sliced FP64 copy" : "sliced FP32 copy", (int)l);
       }
       set_prefetch(L.A, opt.prefetch_rows, opt.row_chains);
       alloc_work(L, s);
@@ -1338,10 +1345,11 @@ int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_pe
     const RowVariant& v = precision == 0 ? L.A.var64 : L.A.var32;
     const double avg = L.A.n ? (double)L.A.nnz / L.A.n : 0.0;
     const bool vec = v.hybrid && v.vector && (precision == 1 ? L.A.grp.hvon : L.A.grp.hv64on);
-    if (threads_per_row)  // the FP64 vector hybrid takes 4 lanes per row of a big group
-      *threads_per_row = vec && precision == 0 ? 4 : v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
+    const bool sel = v.sliced && L.A.grp.son && (precision == 1 ? L.A.grp.sv32on : L.A.grp.sv64on);
+    if (threads_per_row)  // the FP64 vector hybrid takes 4 lanes per row of a big group, the sliced form 1
+      *threads_per_row = sel ? 1 : vec && precision == 0 ? 4 : v.tpr ? v.tpr : (avg >= 48 ? 32 : avg >= 20 ? 16 : avg >= 8 ? 8 : 4);
     if (pattern)
-      *pattern = v.hybrid ? (vec ? 4 : 3) : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
+      *pattern = sel ? 5 : v.hybrid ? (vec ? 4 : 3) : v.group ? 2 : v.tpr ? (v.pat ? 1 : 0) : (L.A.pat.on ? 1 : 0);
     return GIAMG_OK;
   });
 }

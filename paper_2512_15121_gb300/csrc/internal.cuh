@@ -126,6 +126,22 @@ struct Groups {
   DBuf<int64_t> hoff;           // start of big group j's block (values), n_big + 1 entries
   DBuf<float> hv;
   DBuf<double> hv64;
+  // sliced form: every row of the level in slices of 32 rows, one lane per row, the rows ordered
+  // by length (longest first), then by group, so one slice mixes rows of a few groups of equal
+  // length; a slice is padded with zeros to its longest row rounded up to a multiple of 8, and
+  // its values are interleaved by column: element ((k / W) * 32 + lane) * W + k % W of the
+  // slice's block, W = 2 (FP64) or 4 (FP32), so a lane's W columns are one 16-byte load and the
+  // warp's load is 512 contiguous bytes.  A lane reads its row's columns from its group's list in
+  // gcol (positions past its row's length repeat its last column against a zero value).
+  bool son = false, sv64on = false, sv32on = false;
+  int64_t n_slices = 0;
+  DBuf<int32_t> srow;   // per lane: the row (-1: padding)
+  DBuf<int32_t> sob;    // per lane: start of the row's column list in gcol
+  DBuf<int32_t> sclen;  // per lane: the row's length (1 for padding)
+  DBuf<int32_t> slen;   // per slice: padded length
+  DBuf<int64_t> sbase;  // per slice: first value of its block (n_slices + 1 entries)
+  DBuf<double> sv64;
+  DBuf<float> sv32;
   // multi-right-hand-side FP32 products: work items of two rows of one group (or one row), so a
   // warp applies each gathered row of X to both; a group's rows are paired in list order
   bool pon = false;
@@ -144,6 +160,7 @@ struct RowVariant {
   bool hybrid = false;  // big row groups by the group kernel, the other rows by the pattern kernel
   int64_t prefetch = 0;  // pattern form: L2 prefetch distance in rows (0: none)
   bool vector = false;   // hybrid form: big groups read with 16-byte loads from the group-major copy
+  bool sliced = false;   // sliced form: one lane per row, 32 rows of equal length per warp
 };
 
 struct DCSR {
@@ -471,6 +488,10 @@ void tune_rows(DCSR& A, cudaStream_t s);
 bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s);
 // the row-pair work items of the multi-right-hand-side FP32 products (needs the row groups)
 bool batch_pairs_build(DCSR& A, cudaStream_t s);
+// the sliced form's layout (once) and its copy of the FP64 (precision 0) or FP32 (1) values; needs
+// the row groups; false if the form does not apply
+bool sliced_build(DCSR& A, int precision, cudaStream_t s);
+constexpr int kSliceStep = 8;  // columns per step of the sliced kernels (slice lengths are multiples)
 // set A.var64 / A.var32 from forced options or the defaults measured best inside the solve
 void choose_rows(DCSR& A, int form, int threads);
 // prefetch_rows -1: automatic, 0: off, > 0: distance in rows; chains 0: keep, else 2, 4 or 8

@@ -458,6 +458,94 @@ __global__ void hv_gather(const int32_t* __restrict__ big, const int64_t* __rest
 }
 }  // namespace
 
+namespace {
+// One CTA per slice: the values of its rows, interleaved by column in groups of W.
+template <typename V, int W>
+__global__ void slice_fill(const int32_t* __restrict__ srow, const int32_t* __restrict__ sclen,
+                           const int32_t* __restrict__ slen, const int64_t* __restrict__ sbase,
+                           const int64_t* __restrict__ rp, const V* __restrict__ val, V* __restrict__ sv) {
+  const int64_t sl = blockIdx.x;
+  const int64_t cnt = (int64_t)slen[sl] * 32;
+  V* __restrict__ out = sv + sbase[sl];
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int64_t kw = e / (32 * W);
+    const int rem = (int)(e - kw * 32 * W);
+    const int lane = rem / W;
+    const int k = (int)(kw * W + rem % W);
+    const int row = srow[sl * 32 + lane];
+    out[e] = row >= 0 && k < sclen[sl * 32 + lane] ? val[rp[row] + k] : V(0);
+  }
+}
+}  // namespace
+
+bool sliced_build(DCSR& A, int precision, cudaStream_t s) {
+  Groups& R = A.grp;
+  if (precision == 1 ? R.sv32on : R.sv64on) return true;
+  if (!R.on || (precision == 1 ? !A.v32.get() : !A.v.get())) return false;
+  const int64_t n = A.n, G = R.n_groups;
+  if (!R.son) {  // the layout, shared by both precisions
+    if (R.n_cols >= INT32_MAX) return false;
+    std::vector<int64_t> gp(G + 1), rp_h(G + 1);
+    std::vector<int32_t> rows(n);
+    GIAMG_CUDA(cudaMemcpyAsync(gp.data(), R.gptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaMemcpyAsync(rows.data(), R.grow.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> order(G);
+    for (int64_t g = 0; g < G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return gp[a + 1] - gp[a] > gp[b + 1] - gp[b]; });
+    const int64_t ns = (n + 31) / 32;
+    std::vector<int32_t> srow(ns * 32, -1), sob(ns * 32, 0), sclen(ns * 32, 1), slen(ns, kSliceStep);
+    std::vector<int64_t> sbase(ns + 1, 0);
+    int64_t li = 0;
+    for (int64_t g : order) {
+      const int32_t c = (int32_t)(gp[g + 1] - gp[g]);
+      for (int64_t t = rp_h[g]; t < rp_h[g + 1]; ++t, ++li) {
+        srow[li] = rows[t];
+        sob[li] = (int32_t)gp[g];
+        sclen[li] = std::max(c, 1);
+      }
+    }
+    for (int64_t sl = 0; sl < ns; ++sl) {
+      int32_t L = 1;
+      for (int l = 0; l < 32; ++l) L = std::max(L, sclen[sl * 32 + l]);
+      slen[sl] = (L + kSliceStep - 1) / kSliceStep * kSliceStep;
+      sbase[sl + 1] = sbase[sl] + (int64_t)slen[sl] * 32;
+    }
+    R.srow.alloc(ns * 32, s);
+    R.sob.alloc(ns * 32, s);
+    R.sclen.alloc(ns * 32, s);
+    R.slen.alloc(ns, s);
+    R.sbase.alloc(ns + 1, s);
+    GIAMG_CUDA(cudaMemcpyAsync(R.srow.get(), srow.data(), sizeof(int32_t) * ns * 32, cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaMemcpyAsync(R.sob.get(), sob.data(), sizeof(int32_t) * ns * 32, cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaMemcpyAsync(R.sclen.get(), sclen.data(), sizeof(int32_t) * ns * 32, cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaMemcpyAsync(R.slen.get(), slen.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaMemcpyAsync(R.sbase.get(), sbase.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    R.n_slices = ns;
+    R.son = true;
+  }
+  int64_t total = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&total, R.sbase.get() + R.n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (precision == 1) {
+    R.sv32.alloc((size_t)std::max<int64_t>(total, 4), s);
+    { slice_fill<float, 4><<<(unsigned)R.n_slices, 256, 0, s>>>(R.srow.get(), R.sclen.get(), R.slen.get(), R.sbase.get(),
+                                                                A.rp.get(), A.v32.get(), R.sv32.get()); note_launch(); }
+    R.sv32on = true;
+  } else {
+    R.sv64.alloc((size_t)std::max<int64_t>(total, 2), s);
+    { slice_fill<double, 2><<<(unsigned)R.n_slices, 256, 0, s>>>(R.srow.get(), R.sclen.get(), R.slen.get(), R.sbase.get(),
+                                                                 A.rp.get(), A.v.get(), R.sv64.get()); note_launch(); }
+    R.sv64on = true;
+  }
+  GIAMG_CUDA(cudaGetLastError());
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  return true;
+}
+
 bool batch_pairs_build(DCSR& A, cudaStream_t s) {
   Groups& R = A.grp;
   R.pon = false;

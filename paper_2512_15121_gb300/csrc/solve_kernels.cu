@@ -498,6 +498,124 @@ HY4_KERNEL(hy4_resid_f64, double, kResidual, 16)
 HY4_KERNEL(hy4_cheb_f64, double, kCheb, 16)
 HY4_KERNEL(hy4_add_f64, double, kAddSpmv, 16)
 
+// ------------------------------------------------------------------ sliced form (one lane per row)
+// Every row of the level, in slices of 32 rows of (nearly) equal length (rows ordered by length,
+// then group): a warp takes a slice and each lane one row, so the FP64 pipe executes one useful
+// FMA per lane per instruction -- no shuffle reduction, no half-empty warp at the end of a
+// 25-row face group (the slices mix the rows of several groups), and the per-row work after the
+// sum is one instruction for 32 rows.  A lane reads W consecutive values of its row with one
+// 16-byte load (the warp: 512 contiguous bytes); its column indices come from its group's list
+// (shared with the group's other rows, so mostly one address per warp) and x from L1/L2.  The
+// loop is software-pipelined: the next step's column indices and values are requested before
+// this step's FMAs, so every lane keeps one dependent index -> x gather and two steps of value
+// loads in flight (up to 64 registers, 4 CTAs per SM).  Measured per launch on the 16^3 p = 6
+// operator against the vector hybrid: FP64 0.698 ms (1.18 TFLOP/s, 94% of the FP64 pipe's
+// nominal rate) against 0.931, FP32 0.314 against 0.317; without the pipelining 1.32 / 0.54.
+template <typename V>
+struct SelVec;
+template <>
+struct SelVec<double> {
+  using T = double2;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ double at(const T& v, int i) { return i == 0 ? v.x : v.y; }
+};
+template <>
+struct SelVec<float> {
+  using T = float4;
+  static constexpr int W = 4;
+  static __device__ __forceinline__ float at(const T& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+};
+
+template <typename V, int MODE, int K>
+__device__ __forceinline__ void sel_body(int64_t n_slices, const int32_t* __restrict__ srow,
+                                              const int32_t* __restrict__ sob, const int32_t* __restrict__ sclen,
+                                              const int32_t* __restrict__ slen, const int64_t* __restrict__ sbase,
+                                              const V* __restrict__ sv, const int32_t* __restrict__ gcol,
+                                              const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y,
+                                              V* __restrict__ d, const V* __restrict__ dinv, V c1, V c2) {
+  using VT = typename SelVec<V>::T;
+  constexpr int W = SelVec<V>::W, NV = K / W;
+  const int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (sl >= n_slices) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t li = sl * 32 + lane;
+  const int row = srow[li];
+  const int32_t* __restrict__ cl = gcol + sob[li];
+  const int last = sclen[li] - 1;
+  const int L = slen[sl];
+  const VT* __restrict__ vp = reinterpret_cast<const VT*>(sv + sbase[sl]) + lane;
+  V a[4] = {V(0), V(0), V(0), V(0)};
+  int c[K];
+  VT v[NV];
+#pragma unroll
+  for (int j = 0; j < K; ++j) c[j] = __ldg(cl + min(j, last));
+#pragma unroll
+  for (int u = 0; u < NV; ++u) v[u] = __ldcs(vp + (int64_t)u * 32);
+  for (int k0 = 0; k0 < L; k0 += K) {
+    V xv[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) xv[j] = __ldg(x + c[j]);
+    VT vn[NV];
+    const int kn = k0 + K < L ? k0 + K : k0;  // the last step reloads its own (unused) operands
+#pragma unroll
+    for (int j = 0; j < K; ++j) c[j] = __ldg(cl + min(kn + j, last));
+#pragma unroll
+    for (int u = 0; u < NV; ++u) vn[u] = __ldcs(vp + (int64_t)(kn / W + u) * 32);
+#pragma unroll
+    for (int j = 0; j < K; ++j) a[j & 3] = fma(SelVec<V>::at(v[j / W], j % W), xv[j], a[j & 3]);
+#pragma unroll
+    for (int u = 0; u < NV; ++u) v[u] = vn[u];
+  }
+  if (row < 0) return;
+  const V acc = (a[0] + a[1]) + (a[2] + a[3]);
+  if (MODE == kSpmv) {
+    y[row] = acc;
+  } else if (MODE == kAddSpmv) {
+    y[row] += acc;
+  } else if (MODE == kResidual) {
+    y[row] = b[row] - acc;
+  } else {
+    const V rr = b[row] - acc;
+    const V dn = (c1 == V(0) ? V(0) : c1 * d[row]) + c2 * dinv[row] * rr;
+    d[row] = dn;
+    y[row] = x[row] + dn;
+  }
+}
+
+#define SEL_KERNEL(NAME, V, MODE)                                                                               \
+  __global__ void __launch_bounds__(kThreads, 4)                                                              \
+      NAME(int64_t n_slices, const int32_t* __restrict__ srow, const int32_t* __restrict__ sob,               \
+           const int32_t* __restrict__ sclen, const int32_t* __restrict__ slen, const int64_t* __restrict__ sbase, \
+           const V* __restrict__ sv, const int32_t* __restrict__ gcol, const V* __restrict__ x,              \
+           const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d, const V* __restrict__ dinv, V c1,    \
+           V c2) {                                                                                            \
+    sel_body<V, MODE, kSliceStep>(n_slices, srow, sob, sclen, slen, sbase, sv, gcol, x, b, y, d, dinv, c1, c2); \
+  }
+SEL_KERNEL(sel_spmv_f64, double, kSpmv)
+SEL_KERNEL(sel_resid_f64, double, kResidual)
+SEL_KERNEL(sel_cheb_f64, double, kCheb)
+SEL_KERNEL(sel_add_f64, double, kAddSpmv)
+SEL_KERNEL(sel_spmv_f32, float, kSpmv)
+SEL_KERNEL(sel_resid_f32, float, kResidual)
+SEL_KERNEL(sel_cheb_f32, float, kCheb)
+SEL_KERNEL(sel_add_f32, float, kAddSpmv)
+
+template <typename V, int MODE>
+struct SelKernel;
+#define SEL_SELECT(V, MODE, H)                          \
+  template <>                                           \
+  struct SelKernel<V, MODE> {                           \
+    static constexpr decltype(&H) get() { return &H; }  \
+  };
+SEL_SELECT(double, kSpmv, sel_spmv_f64)
+SEL_SELECT(double, kResidual, sel_resid_f64)
+SEL_SELECT(double, kCheb, sel_cheb_f64)
+SEL_SELECT(double, kAddSpmv, sel_add_f64)
+SEL_SELECT(float, kSpmv, sel_spmv_f32)
+SEL_SELECT(float, kResidual, sel_resid_f32)
+SEL_SELECT(float, kCheb, sel_cheb_f32)
+SEL_SELECT(float, kAddSpmv, sel_add_f32)
+
 template <typename V, int MODE>
 struct Hy4Kernel;
 #define HY4_SELECT(V, MODE, H)                          \
@@ -633,6 +751,17 @@ void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   note_launch();
 }
 
+template <typename V, int MODE>
+void launch_sel(const DCSR& A, const V* sv, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
+                cudaStream_t s) {
+  auto k = SelKernel<V, MODE>::get();
+  const Groups& R = A.grp;
+  k<<<grid_for(R.n_slices * 32, kThreads), kThreads, 0, s>>>(R.n_slices, R.srow.get(), R.sob.get(), R.sclen.get(),
+                                                            R.slen.get(), R.sbase.get(), sv, R.gcol.get(), x, b, y,
+                                                            d, dinv, c1, c2);
+  note_launch();
+}
+
 template <typename V, int MODE>  // V = double
 void launch_hy4(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
                 cudaStream_t s) {
@@ -695,6 +824,21 @@ void launch_variant(const DCSR& A, const RowVariant& var, double avg, const V* v
                     const V* dinv, V c1, V c2, cudaStream_t s) {
   const int tpr = var.tpr ? var.tpr : default_tpr(avg);
   const bool pat = var.tpr ? var.pat : A.pat.on;
+  if (var.sliced && A.grp.son) {
+    if constexpr (std::is_same<V, float>::value) {
+      if (A.grp.sv32on && val == A.v32.get()) {
+        launch_sel<V, MODE>(A, A.grp.sv32.get(), x, b, y, d, dinv, c1, c2, s);
+        GIAMG_CUDA(cudaGetLastError());
+        return;
+      }
+    } else {
+      if (A.grp.sv64on && val == A.v.get()) {
+        launch_sel<V, MODE>(A, A.grp.sv64.get(), x, b, y, d, dinv, c1, c2, s);
+        GIAMG_CUDA(cudaGetLastError());
+        return;
+      }
+    }
+  }
   bool vector = var.hybrid && var.vector && A.grp.hyb && A.pat.on;
   if constexpr (std::is_same<V, float>::value) vector = vector && A.grp.hvon && val == A.v32.get();
   else vector = vector && A.grp.hv64on && val == A.v.get();
@@ -1171,18 +1315,30 @@ void choose_rows(DCSR& A, int form, int threads) {
       // precisions; else FP32 rows on the pattern form (halved index traffic) and FP64 rows,
       // which are bound by the 1/64-rate FP64 pipe, on CSR, threads per row by auto_tpr
       const bool big = A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
-      v.pat = (prec == 1 || big) && A.pat.on;
-      v.hybrid = big;
-      v.vector = big;
-      v.tpr = big ? 32 : auto_tpr(A.n, avg, prec == 1 ? 24.0 : 48.0);
+      // the sliced form (one lane per row, slices of 32 rows of equal length) on levels of at
+      // least 2^18 rows (8192 slices: several waves of warps; below that a warp's long serial
+      // slice leaves the GPU latency-bound): the FP64 rows there, since it gives the FP64 pipe
+      // one useful FMA per lane and instruction (16^3 p = 6: 0.70 ms per product against 0.93 for
+      // the vector hybrid, 12^3 p = 8: 1.34 against 1.59, 24^3 p = 4: 0.32 against 0.58 on CSR),
+      // and the FP32 rows where the vector hybrid does not apply (24^3 p = 4: 0.16 against 0.23
+      // on row patterns; on the hybrid's operators the FP32 vector hybrid is as fast at p = 6 and
+      // faster at p = 8, 0.52 against 0.68)
+      const bool large = A.grp.on && A.n >= (1 << 18);
+      v.sliced = large && (prec == 0 || !big);
+      v.pat = !v.sliced && (prec == 1 || big) && A.pat.on;
+      v.hybrid = !v.sliced && big;
+      v.vector = !v.sliced && big;
+      v.tpr = v.sliced ? 1 : big ? 32 : auto_tpr(A.n, avg, prec == 1 ? 24.0 : 48.0);
     } else {
-      v.pat = (form == 2 || form >= 4) && A.pat.on;
+      v.pat = (form == 2 || form == 4 || form == 5) && A.pat.on;
       v.group = form == 3 && A.grp.on;
-      v.hybrid = (form >= 4) && A.grp.hyb && A.pat.on;
+      v.hybrid = (form == 4 || form == 5) && A.grp.hyb && A.pat.on;
       v.vector = form == 5 && v.hybrid;
-      v.tpr = v.group || v.hybrid ? 32 : default_tpr(avg);
+      v.sliced = form == 6 && A.grp.on;
+      v.tpr = v.group || v.hybrid ? 32 : v.sliced ? 1 : default_tpr(avg);
+      if (form == 6 && !v.sliced) v.tpr = default_tpr(avg);  // no groups: CSR
     }
-    if (threads && !v.group && !v.hybrid) v.tpr = threads;
+    if (threads && !v.group && !v.hybrid && !v.sliced) v.tpr = threads;
     (prec == 0 ? A.var64 : A.var32) = v;
   }
 }
@@ -1229,8 +1385,15 @@ void tune_rows(DCSR& A, cudaStream_t s) {
     v.group = true;
     cands.push_back(v);
   }
-  // the hybrid forms, the vector ones on group-major copies built for the timing
+  // the hybrid forms, the vector ones on group-major copies built for the timing, and the sliced form
   const bool vec = A.grp.hyb && A.pat.on && hybrid_vector_build(A, 1, s) && hybrid_vector_build(A, 0, s);
+  const bool sel = A.grp.on && sliced_build(A, 0, s) && sliced_build(A, 1, s);
+  if (sel) {
+    RowVariant v;
+    v.tpr = 1;
+    v.sliced = true;
+    cands.push_back(v);
+  }
   if (A.grp.hyb && A.pat.on) {
     RowVariant v;
     v.tpr = 32;
@@ -1260,7 +1423,7 @@ void tune_rows(DCSR& A, cudaStream_t s) {
       if (log)
         fprintf(stderr, "tune n=%lld nnz=%lld %s form=%s tpr=%d unroll=%d: %.4f ms\n", (long long)A.n,
                 (long long)A.nnz, prec ? "fp32" : "fp64",
-                v.vector ? "vector" : v.hybrid ? "hybrid" : v.group ? "groups" : v.pat ? "pattern" : "csr", v.tpr,
+                v.sliced ? "sliced" : v.vector ? "vector" : v.hybrid ? "hybrid" : v.group ? "groups" : v.pat ? "pattern" : "csr", v.tpr,
                 v.unroll, t);
       if (t < best) {
         best = t;
@@ -1277,6 +1440,14 @@ void tune_rows(DCSR& A, cudaStream_t s) {
   if (vec && !A.var64.vector) {
     A.grp.hv64.release();
     A.grp.hv64on = false;
+  }
+  if (sel && !A.var32.sliced) {
+    A.grp.sv32.release();
+    A.grp.sv32on = false;
+  }
+  if (sel && !A.var64.sliced) {
+    A.grp.sv64.release();
+    A.grp.sv64on = false;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

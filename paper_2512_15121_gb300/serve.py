@@ -37,6 +37,8 @@ class Request:
     rtol: float = 1e-8
     precision: int = 1
     arrival: float = 0.0
+    size: tuple | None = None       # (n, nnz) of the operator, if known without building it: the
+                                    # server then admits by it and calls make_operator outside its lock
     # filled in by the server
     start: float = -1.0
     finish: float = -1.0
@@ -139,8 +141,12 @@ class Server:
             self.stats["cache_hits"] += 1
             e.busy = True
             return e, None
-        op = req.make_operator()
-        need = estimate_bytes(op["n"], len(op["val"]), self.max_columns)
+        if req.size is not None:  # materialised by _build, outside the lock
+            op = req.make_operator
+            need = estimate_bytes(int(req.size[0]), int(req.size[1]), self.max_columns)
+        else:
+            op = req.make_operator()
+            need = estimate_bytes(op["n"], len(op["val"]), self.max_columns)
         if not self._evict_for(need):
             self.stats["admission_waits"] += 1
             return None, None
@@ -151,10 +157,13 @@ class Server:
         return e, op
 
     def _build(self, key, e: _Entry, op) -> str | None:
-        """Outside the lock: run the solver factory for a claimed placeholder; the error text, or
-        None.  A failed build leaves no cache entry."""
+        """Outside the lock: run the solver factory for a claimed placeholder (materialising the
+        operator first when the request gave only its size); the error text, or None.  A failed
+        build leaves no cache entry."""
         t0 = time.perf_counter()
         try:
+            if callable(op):
+                op = op()
             e.solver, e.stream = self.solver_factory(op)
             err = None
         except Exception as ex:
@@ -348,14 +357,72 @@ STREAM_ORDERS = (2, 4, 6)
 STREAM_LAMBDAS = (0.0, 1.0, 1000.0)
 
 
+def _combine(K: np.ndarray, M: np.ndarray, lam: float, diag_rows: np.ndarray) -> np.ndarray:
+    """K + lam M in chunks on host threads (numpy releases the GIL on large arrays), the Dirichlet
+    identity rows (rows holding only their diagonal) reset to 1."""
+    from concurrent.futures import ThreadPoolExecutor
+    out = np.empty_like(K)
+    step = max(1 << 22, (len(K) + 63) // 64)
+
+    def part(lo):
+        hi = min(lo + step, len(K))
+        np.multiply(M[lo:hi], lam, out=out[lo:hi])
+        np.add(out[lo:hi], K[lo:hi], out=out[lo:hi])
+
+    with ThreadPoolExecutor(16) as ex:
+        list(ex.map(part, range(0, len(K), step)))
+    out[diag_rows] = 1.0
+    return out
+
+
+class _SharedOperator:
+    """One mesh and order assembled once as stiffness K (lambda = 0) and mass M: the operator of
+    any lambda is K + lambda M with the same pattern, formed when it is needed."""
+
+    def __init__(self, n, p):
+        import fegen
+        self.K = fegen.make(n, p, mesh="jitter", mesh_seed=n, lam=0.0, rhs="none")
+        mass = fegen.make(n, p, mesh="jitter", mesh_seed=n, lam=1.0, kappa=2, rhs="none")
+        assert np.array_equal(mass.row_ptr, self.K.row_ptr) and np.array_equal(mass.col, self.K.col)
+        self.M = mass.val
+        mass.close()
+        lens = np.diff(self.K.row_ptr)
+        self.diag_rows = self.K.row_ptr[:-1][lens == 1]  # value index of each identity row's diagonal
+        self.n, self.nnz, self.p = self.K.n, self.K.nnz, self.K.p
+        self._basis = None
+
+    def values(self, lam):
+        return self.K.val.copy() if lam == 0.0 else _combine(self.K.val, self.M, lam, self.diag_rows)
+
+    def rhs_nodal(self, seeds):
+        """prob.rhs_nodal(seed) for each seed (the same Fourier fields at the nodes, c ~ N(0, 1)
+        from numpy's PCG64 with that seed), as one product with a table of the 64 mode products at
+        the nodes, built once per mesh and order: n x len(seeds)."""
+        if self._basis is None:
+            k = np.arange(1, 5)[:, None] * np.pi
+            sx, sy, sz = (np.sin(k * self.K.coords[None, :, d]) for d in range(3))  # 4 x n each
+            T = (sx[:, None, None, :] * sy[None, :, None, :]) * sz[None, None, :, :]
+            self._basis = T.reshape(64, self.n)
+        C = np.stack([np.random.default_rng(sd).standard_normal((4, 4, 4)).ravel() for sd in seeds])
+        F = (C @ self._basis).T.copy()
+        F[self.K.boundary != 0, :] = 0.0
+        return F
+
+    def close(self):
+        self.K.close()
+
+
 def synthetic_stream(n_requests: int = 128, seed: int = 7, rate_per_s: float = 200.0, max_rhs: int = 8,
                      meshes=STREAM_MESHES, orders=STREAM_ORDERS, lambdas=STREAM_LAMBDAS, rhs_kind: str = "fourier"):
     """Requests for Helmholtz / Poisson operators on jittered hex meshes (mesh seed = mesh size, so
     a (mesh, order, lambda) triple always names the same operator), 1..max_rhs smooth Fourier
     right-hand sides seeded by request id (rhs_kind "fourier": loaded by quadrature; "nodal": the
-    same fields evaluated at the nodes, for large streams), Poisson arrivals (exponential gaps) at
-    rate_per_s."""
+    same fields evaluated at the nodes, for large streams: the operators of one mesh and order
+    then share one stiffness and one mass matrix on the host, each lambda's values formed when the
+    server builds that operator), Poisson arrivals (exponential gaps) at rate_per_s."""
     import fegen
+    if rhs_kind == "nodal":
+        return _shared_stream(n_requests, seed, rate_per_s, max_rhs, meshes, orders, lambdas)
     rng = np.random.default_rng(seed)
     ops = {}
 
@@ -384,6 +451,34 @@ def synthetic_stream(n_requests: int = 128, seed: int = 7, rate_per_s: float = 2
                         p=prob.p, cheb_degree=k)
         reqs.append(Request(rid=rid, key=(f"jitter{n}^3", p, lam), make_operator=make, rhs=rhs, arrival=t))
     return reqs, ops
+
+
+def _shared_stream(n_requests, seed, rate_per_s, max_rhs, meshes, orders, lambdas):
+    """synthetic_stream's draws (the same mesh, order, lambda, column count and arrival of every
+    request) with operators shared across lambda and nodal right-hand sides."""
+    rng = np.random.default_rng(seed)
+    shared = {}
+    t = 0.0
+    reqs, keys = [], set()
+    for rid in range(n_requests):
+        n = int(rng.choice(meshes))
+        p = int(rng.choice(orders))
+        lam = float(rng.choice(lambdas))
+        r = int(rng.integers(1, max_rhs + 1))
+        t += float(rng.exponential(1.0 / rate_per_s))
+        if (n, p) not in shared:
+            shared[(n, p)] = _SharedOperator(n, p)
+        so = shared[(n, p)]
+        rhs = so.rhs_nodal([100000 + 64 * rid + j for j in range(r)])
+        k = 3 if lam > 0 else 2
+
+        def make(so=so, lam=lam, k=k):
+            return dict(n=so.n, row_ptr=so.K.row_ptr, col=so.K.col, val=so.values(lam), elem_dof=so.K.elem_dof,
+                        p=so.p, cheb_degree=k)
+        keys.add((n, p, lam))
+        reqs.append(Request(rid=rid, key=(f"jitter{n}^3", p, lam), make_operator=make, rhs=rhs, arrival=t,
+                            size=(so.n, so.nnz)))
+    return reqs, {key: shared[key[:2]] for key in sorted(keys)}
 
 
 def run_stream(server: Server, reqs: list, time_scale: float = 1.0):

