@@ -240,8 +240,12 @@ void alloc_work(Level& L, cudaStream_t s) {
 void galerkin(Level& F, DCSR& Ac, bool keep_R, cudaStream_t s) {
   DCSR R, AP;
   csr_transpose(F.P, R, s);
-  spgemm(F.A, F.P, AP, s);
-  spgemm(R, AP, Ac, s);
+  // rows of A with identical column sets share A P's pattern: found once per row group
+  if (!spgemm_grouped(F.A, F.P, AP, s)) spgemm(F.A, F.P, AP, s);
+  // so do rows of R = P^T with identical fine supports (e.g. the coarse nodes inside one element)
+  if (R.n >= 1024) groups_build(R, s, 1 << 22, true);
+  if (!spgemm_grouped(R, AP, Ac, s)) spgemm(R, AP, Ac, s);
+  if (R.grp.on) R.grp = Groups();  // R is kept (h-levels) for its CSR product only
   if (keep_R) {
     F.R = std::move(R);
     csr_to32(F.R, s);
@@ -451,6 +455,11 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       F.n_elem = n_elem;
       p_level_build(F, *Cl, opt.basis, s);
       clk.mark("p-level map and P", (int)H.lev.size() - 1);
+      if (opt.compress_patterns && !F.A.grp.on) {  // the row groups serve A P below and the row kernels later
+        pattern_build(F.A, s, 1 << 16, 1 << 24);
+        groups_build(F.A, s, 1 << 22);
+        clk.mark("row patterns and groups", (int)H.lev.size() - 1);
+      }
       Cl->order = F.q;
       galerkin(F, Cl->A, false, s);
       clk.mark("p-level RAP", (int)H.lev.size() - 1);
@@ -505,9 +514,11 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       csr_to32(L.A, s);
       clk.mark("FP32 copy", (int)l);
       if (opt.compress_patterns) {
-        pattern_build(L.A, s, 1 << 16, 1 << 24);
-        clk.mark("row patterns", (int)l);
-        groups_build(L.A, s, 1 << 22);
+        if (!L.A.pat.on && !L.A.grp.on) {  // p-levels with groups have them from the Galerkin product
+          pattern_build(L.A, s, 1 << 16, 1 << 24);
+          clk.mark("row patterns", (int)l);
+          groups_build(L.A, s, 1 << 22);
+        }
         batch_pairs_build(L.A, s);
         clk.mark("row groups, hybrid", (int)l);
       }

@@ -479,6 +479,9 @@ void csr_transpose(const DCSR& A, DCSR& T, cudaStream_t s);
 // C = A B: symbolic union, no dropping, columns ascending, entries summed in ascending inner
 // index with separately rounded products (matches a sequential Gustavson product bit for bit)
 void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
+// the same product when A has row groups (A.grp.on): the pattern once per group; false (C
+// untouched) when the groups' patterns do not fit its tables
+bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 void csr_to32(DCSR& A, cudaStream_t s);
 // time the row-kernel variants on A (both precisions) and keep the fastest in A.var64 / A.var32
 void tune_rows(DCSR& A, cudaStream_t s);
@@ -496,8 +499,9 @@ constexpr int kSliceStep = 8;  // columns per step of the sliced kernels (slice 
 void choose_rows(DCSR& A, int form, int threads);
 // prefetch_rows -1: automatic, 0: off, > 0: distance in rows; chains 0: keep, else 2, 4 or 8
 void set_prefetch(DCSR& A, int prefetch_rows, int chains);
-// detect row groups with identical column sets (exact; leaves A.grp off if not worthwhile)
-bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups);
+// detect row groups with identical column sets (exact; leaves A.grp off if not worthwhile for the
+// row kernels, unless any_sharing: then kept whenever the detection succeeds, for SpGEMM)
+bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups, bool any_sharing = false);
 // detect repeated row patterns (exact; returns false and leaves A.pat off if not worthwhile)
 bool pattern_build(DCSR& A, cudaStream_t s, int64_t max_templates, int64_t max_offsets);
 // diagonal inverse (checks positivity; returns false if a diagonal entry is <= 0 or missing)

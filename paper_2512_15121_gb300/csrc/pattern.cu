@@ -300,7 +300,7 @@ bool pattern_build(DCSR& A, cudaStream_t s, int64_t max_templates, int64_t max_o
 // Row groups: rows with identical (absolute) column sets -- in a nodal high-order operator, the
 // interior nodes of one element, the interior nodes of one shared face or edge.  A group's rows
 // form a dense block over its columns, so the row kernels gather x once per group.
-bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
+bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups, bool any_sharing) {
   Groups& R = A.grp;
   R.on = false;
   const int64_t n = A.n;
@@ -335,7 +335,7 @@ bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
   int64_t G = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&G, pos.get() + cap, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GIAMG_CUDA(cudaStreamSynchronize(s));
-  if (G > max_groups || G * 2 > n) return false;  // groups of fewer than 2 rows on average
+  if (G > max_groups || (!any_sharing && G * 2 > n)) return false;  // groups of fewer than 2 rows on average
   DBuf<uint32_t> rep_key;
   DBuf<int64_t> slot_of;
   rep_key.alloc(G, s);
@@ -354,7 +354,7 @@ bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
   int64_t total = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&total, R.gptr.get() + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GIAMG_CUDA(cudaStreamSynchronize(s));
-  if (total * 4 > A.nnz) {  // fewer than 4 rows share a column list on average: no gain
+  if (!any_sharing && total * 4 > A.nnz) {  // fewer than 4 rows share a column list on average: no gain
     R.gptr.release();
     return false;
   }
@@ -392,7 +392,7 @@ bool groups_build(DCSR& A, cudaStream_t s, int64_t max_groups) {
   GIAMG_CUDA(cudaStreamSynchronize(s));
   int64_t cmax = 0;
   for (int64_t g = 0; g < G; ++g) cmax = std::max(cmax, gp[g + 1] - gp[g]);
-  if (cmax * 8 > 96 * 1024) {  // the FP64 x block must fit in shared memory
+  if (!any_sharing && cmax * 8 > 96 * 1024) {  // the FP64 x block must fit in shared memory
     R.gptr.release(); R.gcol.release(); R.rptr.release(); R.grow.release();
     return false;
   }

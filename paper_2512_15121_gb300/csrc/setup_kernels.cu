@@ -4,6 +4,10 @@
 // smoothed prolongation P = T - M A T, and the Chebyshev bound by Lanczos.
 #include <cuda_runtime.h>
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -818,6 +822,16 @@ void csr_transpose(const DCSR& A, DCSR& T, cudaStream_t s) {
 
 void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
   GIAMG_CHECK(A.m == B.n, GIAMG_ERR_ARG, "spgemm: inner dimensions differ");
+  static const bool log = getenv("GIAMG_SETUP_LOG") != nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  auto lap = [&](const char* what) {
+    if (!log) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "  spgemm %lld x %lld (A nnz %lld, B nnz %lld): %-10s %9.2f ms\n", (long long)A.n, (long long)B.m,
+            (long long)A.nnz, (long long)B.nnz, what, std::chrono::duration<double, std::milli>(now - t0).count());
+    t0 = now;
+  };
   const int64_t n = A.n, m = B.m;
   C.n = n;
   C.m = m;
@@ -851,6 +865,7 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
                                               acc.get()); note_launch(); }
     GIAMG_CUDA(cudaGetLastError());
   }
+  lap("symbolic");
   scan_i32_to_i64(cnt.get(), C.rp.get(), n, s);
   GIAMG_CUDA(cudaMemcpyAsync(&C.nnz, C.rp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GIAMG_CUDA(cudaStreamSynchronize(s));
@@ -865,6 +880,7 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
                                                                         C.ci.get(), C.v.get()); note_launch(); }
     GIAMG_CUDA(cudaGetLastError());
   }
+  lap("numeric");
   if (n_ovf > 0) {
     { spgemm_fallback<<<fb_blocks, 256, 0, s>>>(ovf_rows.get(), n_ovf, m, A.rp.get(), A.ci.get(), A.v.get(), B.rp.get(),
                                               B.ci.get(), B.v.get(), 1, cnt.get(), C.rp.get(), C.ci.get(), C.v.get(),
@@ -872,6 +888,226 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     GIAMG_CUDA(cudaGetLastError());
   }
   GIAMG_CUDA(cudaStreamSynchronize(s));
+  if (log) fprintf(stderr, "  spgemm: C nnz %lld, %d rows on the fallback path\n", (long long)C.nnz, n_ovf);
+  lap("fallback");
+}
+
+// ------------------------------------------------------------------ SpGEMM over row groups
+// C = A B where the rows of A come in groups with identical column sets (Groups, pattern.cu): the
+// rows of a group have identical rows in C's pattern (the union of B's rows over the group's
+// columns), so the pattern -- a hash count, then the sorted distinct columns -- is found once per
+// group instead of once per row, and the numeric pass only accumulates: each output position is
+// found by a binary search in the group's sorted list held in shared memory, and the sums run in
+// ascending inner index with separately rounded products, as in spgemm_numeric.
+__global__ void __launch_bounds__(kSymWarps * 32) gsym_count(int64_t G, const int64_t* __restrict__ gptr,
+                                                             const int32_t* __restrict__ gcol,
+                                                             const int64_t* __restrict__ brp,
+                                                             const int32_t* __restrict__ bci, int32_t* __restrict__ cnt) {
+  __shared__ int32_t table[kSymWarps][kHashCap];
+  __shared__ int32_t uc[kSymWarps];
+  __shared__ int32_t ovf[kSymWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kSymWarps + w;
+  if (g >= G) return;
+  int32_t* tab = table[w];
+  for (int i = lane; i < kHashCap; i += 32) tab[i] = -1;
+  if (lane == 0) { uc[w] = 0; ovf[w] = 0; }
+  __syncwarp();
+  for (int64_t t = gptr[g]; t < gptr[g + 1]; ++t) {
+    const int32_t k = gcol[t];
+    for (int64_t u = brp[k] + lane; u < brp[k + 1]; u += 32) {
+      const int r = hinsert(tab, bci[u]);
+      if (r == 1) atomicAdd(&uc[w], 1);
+      if (r < 0) ovf[w] = 1;
+    }
+    __syncwarp();
+    if (uc[w] > kMaxUnique || ovf[w]) break;
+  }
+  __syncwarp();
+  if (lane == 0) cnt[g] = (uc[w] > kMaxUnique || ovf[w]) ? -1 : uc[w];
+}
+
+// the group's distinct columns, ascending, at uoff[g] (the table again, then a bitonic sort)
+__global__ void __launch_bounds__(kNumWarps * 32) gsym_fill(int64_t G, const int64_t* __restrict__ gptr,
+                                                            const int32_t* __restrict__ gcol,
+                                                            const int64_t* __restrict__ brp,
+                                                            const int32_t* __restrict__ bci,
+                                                            const int64_t* __restrict__ uoff, int32_t* __restrict__ ulist) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  NumSmem* all = reinterpret_cast<NumSmem*>(smem_raw);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kNumWarps + w;
+  if (g >= G) return;
+  NumSmem& S = all[w];
+  for (int i = lane; i < kHashCap; i += 32) S.tab[i] = -1;
+  if (lane == 0) S.count = 0;
+  __syncwarp();
+  for (int64_t t = gptr[g]; t < gptr[g + 1]; ++t) {
+    const int32_t k = gcol[t];
+    for (int64_t u = brp[k] + lane; u < brp[k + 1]; u += 32) hinsert(S.tab, bci[u]);
+  }
+  __syncwarp();
+  for (int i = lane; i < kHashCap; i += 32) {
+    const int32_t key = S.tab[i];
+    if (key >= 0) S.sorted[atomicAdd(&S.count, 1)] = key;
+  }
+  __syncwarp();
+  const int u = S.count;
+  int np2 = 1;
+  while (np2 < u) np2 <<= 1;
+  for (int i = u + lane; i < np2; i += 32) S.sorted[i] = INT32_MAX;
+  __syncwarp();
+  for (int kk = 2; kk <= np2; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < np2; i += 32) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t a = S.sorted[i], b = S.sorted[ixj];
+          const bool up = (i & kk) == 0;
+          if ((a > b) == up) {
+            S.sorted[i] = b;
+            S.sorted[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  int32_t* out = ulist + uoff[g];
+  for (int i = lane; i < u; i += 32) out[i] = S.sorted[i];
+}
+
+__global__ void group_row_counts(int64_t G, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow,
+                                 const int32_t* __restrict__ ucnt, int32_t* __restrict__ gid, int32_t* __restrict__ cnt) {
+  GRID_STRIDE(g, G) {
+    for (int64_t t = rptr[g]; t < rptr[g + 1]; ++t) {
+      gid[grow[t]] = (int32_t)g;
+      cnt[grow[t]] = ucnt[g];
+    }
+  }
+}
+
+// numeric: a warp per row; smem per warp: the group's sorted list (umax int32) and the sums (umax doubles)
+__global__ void __launch_bounds__(kNumWarps * 32) gnum_rows(int64_t n, int umax, const int64_t* __restrict__ arp,
+                                                            const int32_t* __restrict__ aci,
+                                                            const double* __restrict__ av,
+                                                            const int64_t* __restrict__ brp,
+                                                            const int32_t* __restrict__ bci,
+                                                            const double* __restrict__ bv,
+                                                            const int32_t* __restrict__ gid,
+                                                            const int64_t* __restrict__ uoff,
+                                                            const int32_t* __restrict__ ulist,
+                                                            const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                                            double* __restrict__ cv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)w * umax;
+  int32_t* cols = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem_raw) + (size_t)kNumWarps * umax) +
+                  (size_t)w * umax;
+  const int64_t row = (int64_t)blockIdx.x * kNumWarps + w;
+  if (row >= n) return;
+  const int32_t g = gid[row];
+  const int32_t* __restrict__ ul = ulist + uoff[g];
+  const int u = (int)(uoff[g + 1] - uoff[g]);
+  for (int i = lane; i < u; i += 32) {
+    cols[i] = ul[i];
+    acc[i] = 0.0;
+  }
+  __syncwarp();
+  for (int64_t t = arp[row]; t < arp[row + 1]; ++t) {
+    const int32_t k = aci[t];
+    const double a = av[t];
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+      const int32_t c = bci[q];
+      int lo = 0, hi = u - 1;  // c is in the list by construction
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cols[mid] < c) lo = mid + 1;
+        else hi = mid;
+      }
+      acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, bv[q]));
+    }
+    __syncwarp();
+  }
+  const int64_t base = crp[row];
+  for (int i = lane; i < u; i += 32) {
+    cci[base + i] = cols[i];
+    cv[base + i] = acc[i];
+  }
+}
+
+bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
+  const Groups& R = A.grp;
+  if (!R.on || A.m != B.n) return false;
+  static const bool log = getenv("GIAMG_SETUP_LOG") != nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  auto lap = [&](const char* what) {
+    if (!log) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "  spgemm by row groups %lld x %lld (%lld groups): %-10s %9.2f ms\n", (long long)A.n,
+            (long long)B.m, (long long)R.n_groups, what, std::chrono::duration<double, std::milli>(now - t0).count());
+    t0 = now;
+  };
+  const int64_t n = A.n, G = R.n_groups;
+  DBuf<int32_t> ucnt;
+  ucnt.alloc(std::max<int64_t>(G, 1), s);
+  { gsym_count<<<blocks_for(G, kSymWarps), kSymWarps * 32, 0, s>>>(G, R.gptr.get(), R.gcol.get(), B.rp.get(), B.ci.get(),
+                                                                  ucnt.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  std::vector<int32_t> uc(G);
+  GIAMG_CUDA(cudaMemcpyAsync(uc.data(), ucnt.get(), sizeof(int32_t) * G, cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  int umax = 1;
+  for (int32_t v : uc) {
+    if (v < 0) return false;  // a group's pattern does not fit the table: the per-row product
+    umax = std::max(umax, (int)v);
+  }
+  const size_t sm = (size_t)kNumWarps * umax * (sizeof(double) + sizeof(int32_t));
+  if (sm > 200 * 1024) return false;
+  DBuf<int64_t> uoff;
+  uoff.alloc(G + 1, s);
+  scan_i32_to_i64(ucnt.get(), uoff.get(), G, s);
+  int64_t utot = 0;
+  GIAMG_CUDA(cudaMemcpyAsync(&utot, uoff.get() + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  DBuf<int32_t> ulist, gid, cnt;
+  ulist.alloc(std::max<int64_t>(utot, 1), s);
+  {
+    static PerDevice attr;
+    const int fsm = (int)(sizeof(NumSmem) * kNumWarps);
+    attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(gsym_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)); });
+    gsym_fill<<<blocks_for(G, kNumWarps), kNumWarps * 32, fsm, s>>>(G, R.gptr.get(), R.gcol.get(), B.rp.get(),
+                                                                   B.ci.get(), uoff.get(), ulist.get());
+    note_launch();
+  }
+  gid.alloc(n, s);
+  cnt.alloc(n, s);
+  { group_row_counts<<<blocks_for(G, 256, 65535), 256, 0, s>>>(G, R.rptr.get(), R.grow.get(), ucnt.get(), gid.get(),
+                                                              cnt.get()); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+  lap("symbolic");
+  C.n = n;
+  C.m = B.m;
+  C.rp.alloc(n + 1, s);
+  scan_i32_to_i64(cnt.get(), C.rp.get(), n, s);
+  GIAMG_CUDA(cudaMemcpyAsync(&C.nnz, C.rp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  C.ci.alloc(std::max<int64_t>(C.nnz, 1), s);
+  C.v.alloc(std::max<int64_t>(C.nnz, 1), s);
+  {
+    static PerDevice attr;
+    attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(gnum_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); });
+    gnum_rows<<<blocks_for(n, kNumWarps), kNumWarps * 32, sm, s>>>(n, umax, A.rp.get(), A.ci.get(), A.v.get(),
+                                                                  B.rp.get(), B.ci.get(), B.v.get(), gid.get(),
+                                                                  uoff.get(), ulist.get(), C.rp.get(), C.ci.get(),
+                                                                  C.v.get());
+    note_launch();
+  }
+  GIAMG_CUDA(cudaGetLastError());
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  lap("numeric");
+  return true;
 }
 
 void csr_to32(DCSR& A, cudaStream_t s) {

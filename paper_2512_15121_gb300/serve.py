@@ -83,9 +83,11 @@ class Server:
         self.max_columns = max_columns
         self.clock = clock or time.perf_counter
         self.device = device
+        self.release_cache = None
         if mem_info is None:
             import torch
             mem_info = lambda: torch.cuda.mem_get_info(device)  # noqa: E731
+            self.release_cache = torch.cuda.empty_cache  # torch's unused cached blocks back to the device
         self.mem_info = mem_info
         self.solver_factory = solver_factory or self._default_factory
         self.runner = runner or self._default_runner
@@ -104,16 +106,19 @@ class Server:
 
     # ------------------------------------------------------------------ hierarchy cache
     def _default_factory(self, op: dict):
+        """A hierarchy on its own stream.  The operator is handed over as host arrays, which the
+        library copies into memory it owns (no torch temporaries: freed blocks in torch's caching
+        allocator would stay invisible to the free-memory probe that admission relies on); solves
+        then take device arrays."""
         import torch
         from . import Solver
         stream = torch.cuda.Stream(device=self.device)
-        dev = torch.device("cuda", self.device)
-        with torch.cuda.stream(stream):
-            t = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
+        with torch.cuda.device(self.device):
             opts = dict(self.solver_options)
             opts.setdefault("cheb_degree", op.get("cheb_degree", 3))
-            S = Solver(op["n"], t(op["row_ptr"]), t(op["col"]), t(op["val"]), t(op["elem_dof"]), op["p"],
-                       stream=stream.cuda_stream, device_ptrs=1, **opts)
+            S = Solver(op["n"], op["row_ptr"], op["col"], op["val"], op["elem_dof"], op["p"],
+                       stream=stream.cuda_stream, device_ptrs=0, **opts)
+            S.set_device_ptrs(True)
         return S, stream
 
     def _free_bytes(self) -> int:
@@ -123,15 +128,25 @@ class Server:
     def _evict_for(self, need: int) -> bool:
         """Evict idle cached hierarchies (least recently used first) until `need` bytes fit next
         to the hierarchies that are being built (their memory is not allocated yet)."""
+        released = False
         while self._free_bytes() - self.reserve - self._building_bytes < need:
             idle = [(e.last_used, k) for k, e in self.cache.items() if not e.busy]
             if not idle:
-                return False
+                if self.release_cache is None or released:
+                    return False
+                self.release_cache()  # right-hand-side blocks torch keeps cached are not free to the library
+                released = True
+                continue
             _, k = min(idle)
             e = self.cache.pop(k)
             e.solver.close()
             self.stats["evictions"] += 1
         return True
+
+    def _never_fits(self, need: int) -> bool:
+        """Under the lock, after _evict_for failed: nothing is cached, built or running, so no
+        memory will be released and a request needing `need` bytes would wait forever."""
+        return not self.cache and self._building_bytes == 0 and self._running == 0
 
     def _claim(self, key, req: Request):
         """Under the lock: the cached hierarchy for `key` (marked busy), a new placeholder entry
@@ -148,6 +163,9 @@ class Server:
             op = req.make_operator()
             need = estimate_bytes(op["n"], len(op["val"]), self.max_columns)
         if not self._evict_for(need):
+            if self._never_fits(need):
+                raise MemoryError(f"the operator needs about {need} bytes of device memory, {self._free_bytes()} "
+                                  f"are free with nothing left to evict")
             self.stats["admission_waits"] += 1
             return None, None
         e = _Entry(None, None, need)
@@ -481,8 +499,9 @@ def _shared_stream(n_requests, seed, rate_per_s, max_rhs, meshes, orders, lambda
     return reqs, {key: shared[key[:2]] for key in sorted(keys)}
 
 
-def run_stream(server: Server, reqs: list, time_scale: float = 1.0):
-    """Submit the requests at their arrival times (relative to now) and wait for all of them."""
+def run_stream(server: Server, reqs: list, time_scale: float = 1.0, drain_timeout: float = 600.0):
+    """Submit the requests at their arrival times (relative to now) and wait for all of them
+    (TimeoutError if they are not all done drain_timeout seconds after the last submission)."""
     t0 = server.clock()
     offs = [r.arrival for r in reqs]
     for r, off in zip(reqs, offs):
@@ -491,5 +510,5 @@ def run_stream(server: Server, reqs: list, time_scale: float = 1.0):
             time.sleep(min(0.001, max(0.0, target - server.clock())))
         r.arrival = 0.0
         server.submit(r)
-    server.drain()
+    server.drain(drain_timeout)
     return latency_summary(reqs)

@@ -245,18 +245,17 @@ def test_size_hint_admits_by_size_and_builds_outside_the_lock():
     assert all(r.error is None and np.array_equal(r.x, 2.0 * r.rhs) for r in reqs)
     assert sorted(made) == [0, 1] and srv.stats["setups"] == 2
     assert held == [False, False]
-    # admission by the stated size: too large for the memory left, the request waits, then fails
-    # nothing until the server closes (no operator is built)
+    # admission by the stated size: larger than the whole device memory with nothing cached, built
+    # or running (nothing will ever be freed), the request fails at once instead of waiting
+    # forever, and its operator is never built
     srv2, mem2, _ = server_with_fakes(capacity=serve.estimate_bytes(n, 10 * n) - 1, slots=1)
     called = []
     big = serve.Request(rid=99, key=("mesh", 9, 1.0), make_operator=lambda: called.append(1),
                         rhs=np.ones((n, 1)), size=(n, 10 * n))
     srv2.submit(big)
-    time.sleep(0.05)
-    assert not called and srv2.stats["admission_waits"] >= 1
-    with srv2.cv:
-        srv2.pending.clear()
+    srv2.drain(10)
     srv2.close()
+    assert not called and big.error is not None and "device memory" in big.error
 
 
 def test_shared_operators_combine_stiffness_and_mass():
