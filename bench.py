@@ -76,6 +76,12 @@ def parse():
                     help="run only the 512-request serving stream and print it")
     ap.add_argument("--serving-meshes", default="4,8,12,16", help="mesh sizes of the served stream")
     ap.add_argument("--no-serving", action="store_true", help="skip the served stream")
+    ap.add_argument("--case", metavar="SPEC",
+                    help="run one case for a profiler and exit: setup, then --solves solves (or --rhs-columns "
+                         "multi-RHS solves); SPEC is a workload name or n,p,mesh,lambda,cheb_degree")
+    ap.add_argument("--precision", type=int, default=1, help="with --case: 0 FP64, 1 FP32 V-cycle")
+    ap.add_argument("--solves", type=int, default=1, help="with --case: number of solves")
+    ap.add_argument("--rhs-columns", type=int, default=1, help="with --case: right-hand sides per solve")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print a per-kernel summary of an ncu launch list and exit (no GPU work)")
     ap.add_argument("--split-at", metavar="KERNEL",
@@ -383,7 +389,31 @@ def gpu_uuid(dev):
         return None
 
 
-def measure_config(name, steps, warmup, profiled, peak, peak_kind, rtol=1e-8):
+def measure_autotuned(prob, k, b, steps, warmup, rtol, default_mixed, default_fp64):
+    """The same operator set up with autotune = 1 (the finest level's row kernels chosen by timing
+    forced-iteration solves inside setup): setup time, what it picked, and the solve times against
+    the defaults'."""
+    import torch
+    import paper_2512_15121_gb300 as g
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = g.Solver.from_problem(prob, device=True, cheb_degree=k, autotune=1)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    x = torch.empty_like(b)
+    stream = torch.cuda.current_stream()
+    mixed = timed_solves(S, b, x, stream, rtol, 1, steps, warmup, False)
+    fp64 = timed_solves(S, b, x, stream, rtol, 0, steps, warmup, False)
+    out = {"setup_ms": round(setup_ms, 1),
+           "picked": {"fp64": list(S.kernel(0, 0)), "fp32": list(S.kernel(0, 1))},
+           "mixed_p50_ms": round(mixed["p50"], 3), "fp64_p50_ms": round(fp64["p50"], 3),
+           "mixed_vs_default": round(mixed["p50"] / default_mixed, 3),
+           "fp64_vs_default": round(fp64["p50"] / default_fp64, 3)}
+    S.close()
+    return out
+
+
+def measure_config(name, steps, warmup, profiled, peak, peak_kind, rtol=1e-8, autotune=False):
     """One workload of the set with the default options: setup time, the FP32-V-cycle and FP64 solves
     (CUDA-event p50/p99 of the captured graph), with profiled=True the roofline of the finest row
     kernels, and the two solutions (host copies) for the comparison with the oracle."""
@@ -425,7 +455,10 @@ def measure_config(name, steps, warmup, profiled, peak, peak_kind, rtol=1e-8):
         out["fp64"]["roofline"] = roofline_fp64(fp64, S, prob, name, peak, peak_kind)
         out["vcycle_gbs"] = vcycle_gbs(mixed)
         out["fp64"]["vcycle_gbs"] = vcycle_gbs(fp64)
+    out["row_kernels"] = {"fp64": list(S.kernel(0, 0)), "fp32": list(S.kernel(0, 1))}
     S.close()
+    if autotune:
+        out["autotune"] = measure_autotuned(prob, k, b, steps, warmup, rtol, mixed["p50"], fp64["p50"])
     return out, (prob, k, prob.b, {"mixed": xm, "fp64": xd})
 
 
@@ -514,7 +547,8 @@ def run_ours(args):
         configs = {}
         # the latency case and the graded p = 8 case (with its own roofline)
         for name, profiled in (("helmholtz_4cube_p4", False), ("helmholtz_12cube_graded_p8", True)):
-            configs[name], later[name] = measure_config(name, steps, warmup, profiled, peak, peak_kind, args.rtol)
+            configs[name], later[name] = measure_config(name, steps, warmup, profiled, peak, peak_kind, args.rtol,
+                                                        autotune=profiled)
             phase(f"config {name} done")
         # 32 right-hand sides against single solves in both precisions
         configs["poisson_24cube_jitter_p4"], later["poisson_24cube_jitter_p4"] = measure_batch(g, torch)
@@ -831,8 +865,42 @@ def cpu_baseline(prob, k, rtol, sols, reps=3):
     return cpu, err
 
 
+def run_case(args):
+    """Setup and a few solves of one case, nothing timed: the command a profiler wraps."""
+    import numpy as np
+    import torch
+    import fegen
+    import paper_2512_15121_gb300 as g
+    if args.case in fegen.WORKLOADS:
+        k = fegen.WORKLOADS[args.case]["k"]
+        prob = fegen.workload(args.case)
+    else:
+        n, p, mesh, lam, k = args.case.split(",")
+        prob = fegen.make(int(n), int(p), mesh=mesh, mesh_seed=1, lam=float(lam), rhs="fourier")
+        k = int(k)
+    S = g.Solver.from_problem(prob, device=True, cheb_degree=k)
+    if args.rhs_columns == 1:
+        b = torch.from_numpy(prob.b).cuda()
+        for _ in range(args.solves):
+            _, it, rr = S.solve(b, rtol=args.rtol, precision=args.precision)
+    else:
+        B = np.stack([prob.rhs("fourier", 1000 + j) for j in range(args.rhs_columns)], axis=1)
+        Bd = torch.from_numpy(B).cuda()
+        for _ in range(args.solves):
+            _, its, rrs = S.solve_batch(Bd, rtol=args.rtol, precision=args.precision)
+        it, rr = int(its.max()), float(rrs.max())
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "dofs": prob.n, "nnz": prob.nnz, "precision": args.precision,
+                      "rhs_columns": args.rhs_columns, "iters": int(it), "relres": float(rr),
+                      "kernels": {"fp64": S.kernel(0, 0), "fp32": S.kernel(0, 1)}}), flush=True)
+    S.close()
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     if args.summarize_launches:
         print(summarize_launches(args.summarize_launches, args.split_at))
         return

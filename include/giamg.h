@@ -82,14 +82,17 @@ typedef struct {
                              (stored as a template id instead of column indices) and groups of rows
                              with identical column sets (x gathered once per group); detection is
                              exact, plain CSR otherwise; 0: plain CSR everywhere */
-  int autotune;           /* 1: time the row-kernel variants (CSR, row patterns, row groups,
-                             hybrid, vector hybrid, sliced) on every large level at setup and keep
-                             the fastest product; 0 (default): the variants measured best inside
-                             the solve (FP64: the sliced form on levels of at least 2^18 rows;
-                             FP32: the vector hybrid where there are at least 4096 groups of 16 or
-                             more rows averaging 192 or more columns, else the sliced form on
-                             levels of at least 2^18 rows; on smaller levels FP32 rows on row
-                             patterns and FP64 rows on CSR) */
+  int autotune;           /* 1: after setup, time the finest level's row-kernel variants (CSR,
+                             row patterns, hybrid, vector hybrid, sliced; several threads per row)
+                             inside the solve -- 3 forced CG iterations per candidate and
+                             precision on a fixed right-hand side, the faster of two runs -- and
+                             keep the fastest per precision (operators of at least 2^20
+                             nonzeros); 0 (default): the variants measured best inside the solve
+                             (FP64: the sliced form on levels of at least 2^18 rows; FP32: the
+                             vector hybrid where there are at least 4096 groups of 16 or more rows
+                             averaging 192 or more columns, else the sliced form on levels of at
+                             least 2^18 rows; on smaller levels FP32 rows on row patterns and FP64
+                             rows on CSR) */
   int row_form;           /* force the row-kernel form: 0 automatic, 1 CSR, 2 row patterns, 3 row
                              groups, 4 hybrid (groups of at least 16 rows by the group kernel, the
                              other rows by the row-pattern kernel), 5 vector hybrid (the big
@@ -225,6 +228,19 @@ GIAMG_API int giamg_level_templates(giamg_handle h, int level, int64_t* n_templa
  * big row groups and row patterns, 4 vector hybrid, 5 sliced), chosen by the setup-time tuner
  * when autotune is set. */
 GIAMG_API int giamg_level_kernel(giamg_handle h, int level, int precision, int* threads_per_row, int* pattern);
+/* Switch the row kernel of level `level` for precision 0 (FP64) or 1 (FP32) after setup: form 0
+ * the default rule, 1..6 as the row_form option (CSR, row patterns, row groups, hybrid, vector
+ * hybrid, sliced), threads 0 (automatic) or 4, 8, 16, 32 threads per row where the form has a
+ * choice.  Builds the value copy the form reads and releases copies no longer read; a form that
+ * does not apply to the level falls back to the default kernel (giamg_level_kernel reports what
+ * runs).  Results change only by rounding.  Synchronises the handle's stream; captured solve
+ * graphs are dropped and recaptured.  Used by the in-solve tuners (Python tune.py). */
+GIAMG_API int giamg_set_row_kernel(giamg_handle h, int level, int precision, int form, int threads);
+/* Rows per work item of the multi-right-hand-side FP32 products on `level` (giamg_solve_batch):
+ * 1 one row per warp, 2 two rows of one row group per warp sharing every gathered row of X
+ * (needs row groups), 0 automatic (2 when more than 16 columns).  Results of a column do not
+ * depend on the choice beyond rounding.  Synchronises the stream; batch graphs are dropped. */
+GIAMG_API int giamg_set_batch_rows(giamg_handle h, int level, int rows_per_item);
 /* Largest Ritz value rho_hat of D^-1/2 A_l D^-1/2 used by the level's smoother. */
 GIAMG_API int giamg_level_rho(giamg_handle h, int level, double* rho_hat);
 /* Change the degree k of every level's Chebyshev smoother (Sec. 2) after setup: the hierarchy

@@ -26,7 +26,7 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
            "giamg_solve_async", "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
-           "giamg_level_rho", "giamg_set_cheb_degree", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
+           "giamg_level_rho", "giamg_set_cheb_degree", "giamg_set_row_kernel", "giamg_set_batch_rows", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_level_residual",
            "giamg_level_residual32", "giamg_level_smooth32", "giamg_level_restrict32", "giamg_level_prolong32",
            "giamg_coarse_solve32", "giamg_free",
@@ -84,6 +84,8 @@ def lib():
         L.giamg_level_rho.argtypes = [vp, i32, P(dbl)]
         L.giamg_level_templates.argtypes = [vp, i32, P(i64), P(i64)]
         L.giamg_level_kernel.argtypes = [vp, i32, i32, P(i32), P(i32)]
+        L.giamg_set_row_kernel.argtypes = [vp, i32, i32, i32, i32]
+        L.giamg_set_batch_rows.argtypes = [vp, i32, i32]
         L.giamg_apply_vcycle.argtypes = [vp, i32, vp, vp]
         L.giamg_level_spmv.argtypes = [vp, i32, vp, vp]
         L.giamg_level_smooth.argtypes = [vp, i32, vp, vp, i32]
@@ -433,6 +435,14 @@ class Solver:
         """Smoother degree k on every level, keeping the hierarchy (giamg_set_cheb_degree)."""
         _check(lib().giamg_set_cheb_degree(self._h, int(k)))
         self.opts.cheb_degree = int(k)
+
+    def set_row_kernel(self, l, precision, form, threads=0):
+        """Switch level l's row kernel for precision 0/1 (form as the row_form option)."""
+        _check(lib().giamg_set_row_kernel(self._h, int(l), int(precision), int(form), int(threads)))
+
+    def set_batch_rows(self, l, rows_per_item):
+        """Rows per work item of level l's multi-RHS FP32 products (0 automatic, 1, 2)."""
+        _check(lib().giamg_set_batch_rows(self._h, int(l), int(rows_per_item)))
 
     def rho_hat(self, l):
         r = ctypes.c_double()

@@ -156,7 +156,8 @@ void launch_bat(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y
   const bool own = val == (sizeof(V) == 8 ? (const V*)A.v.get() : (const V*)A.v32.get());
   const bool pat = own && A.pat.on;
   if constexpr (sizeof(V) == 4) {
-    if (pat && A.grp.pon && m > 16) {
+    const bool pairs = A.batch_rows == 2 || (A.batch_rows == 0 && m > 16);
+    if (pat && A.grp.pon && pairs) {
       bat_pairs<MODE><<<grid_for(A.grp.n_items * 32, kThreads), kThreads, 0, s>>>(
           A.grp.n_items, A.grp.item_a.get(), A.grp.item_b.get(), A.grp.item_g.get(), A.grp.gptr.get(),
           A.grp.gcol.get(), A.rp.get(), m, val, X, B, Y, D, dinv, c1, c2);

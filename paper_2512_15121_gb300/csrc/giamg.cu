@@ -252,6 +252,27 @@ void galerkin(Level& F, DCSR& Ac, bool keep_R, cudaStream_t s) {
   }
 }
 
+// the value copies the chosen row variants read (group-major for the vector hybrid, slices for the
+// sliced form), built where missing; a variant whose copy cannot be built falls back to the
+// default row kernel.  Copies no variant reads any more are released.
+void build_variant_copies(DCSR& A, cudaStream_t s) {
+  for (int prec = 0; prec < 2; ++prec) {
+    RowVariant& v = prec == 0 ? A.var64 : A.var32;
+    if (v.vector && !hybrid_vector_build(A, prec, s)) {
+      v.vector = false;
+    }
+    if (v.sliced && !sliced_build(A, prec, s)) {
+      v.sliced = false;
+      v.tpr = 0;
+    }
+  }
+  Groups& R = A.grp;
+  if (R.hvon && !(A.var32.hybrid && A.var32.vector)) { R.hv.release(); R.hvon = false; }
+  if (R.hv64on && !(A.var64.hybrid && A.var64.vector)) { R.hv64.release(); R.hv64on = false; }
+  if (R.sv32on && !A.var32.sliced) { R.sv32.release(); R.sv32on = false; }
+  if (R.sv64on && !A.var64.sliced) { R.sv64.release(); R.sv64on = false; }
+}
+
 void check_coords(const double* coords_h, const std::vector<int32_t>& l2g, int32_t n_elem, int p, int64_t n) {
   // nodes must be the trilinear image of the GLL tensor points of each element
   const int n1 = p + 1, nl = n1 * n1 * n1;
@@ -522,23 +543,9 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
         batch_pairs_build(L.A, s);
         clk.mark("row groups, hybrid", (int)l);
       }
-      if (opt.autotune) tune_rows(L.A, s);
-      else choose_rows(L.A, opt.row_form, opt.row_threads);
-      if (L.A.var32.vector) {
-        L.A.var32.vector = hybrid_vector_build(L.A, 1, s);
-        clk.mark("group-major FP32 copy", (int)l);
-      }
-      if (L.A.var64.vector) {
-        L.A.var64.vector = hybrid_vector_build(L.A, 0, s);
-        clk.mark("group-major FP64 copy", (int)l);
-      }
-      for (int prec = 0; prec < 2; ++prec) {
-        RowVariant& v = prec == 0 ? L.A.var64 : L.A.var32;
-        if (!v.sliced) continue;
-        v.sliced = sliced_build(L.A, prec, s);
-        if (!v.sliced) v.tpr = 0;  // the form does not apply: the default row kernel
-        clk.mark(prec == 0 ? "sliced FP64 copy" : "sliced FP32 copy", (int)l);
-      }
+      choose_rows(L.A, opt.row_form, opt.row_threads);
+      build_variant_copies(L.A, s);
+      clk.mark("row-form copies", (int)l);
       set_prefetch(L.A, opt.prefetch_rows, opt.row_chains);
       alloc_work(L, s);
       if (L.kind != GIAMG_LEVEL_COARSEST) {
@@ -1150,6 +1157,102 @@ int solve_async_impl(Ctx& C, int precision, const double* b, double* x, double r
   return GIAMG_OK;
 }
 
+// The captured solve graphs hold kernels, their arguments and launch shapes: any change of a
+// level's row kernel or polynomial makes them stale.
+void drop_solve_graphs(Hierarchy& H) {
+  for (SolveGraph& G : H.graph)
+    if (G.exec) {
+      GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
+      G = SolveGraph{};
+    }
+  drop_batch_graphs(H);
+}
+
+// Row-kernel choice on the finest level by time to solution: each candidate variant runs
+// kTuneIters forced CG iterations (the whole solve loop: every level's V-cycle kernels and the
+// outer product) twice on a fixed right-hand side, and the faster of the two CUDA-event times
+// counts; per precision the fastest candidate is kept.  Isolated products mispredict the
+// solve (caches, the coarse levels' kernels and the vector passes between them), so the
+// candidates are timed where they run.  GIAMG_TUNE_LOG=1 prints the timings.
+constexpr int kTuneIters = 3;
+struct TuneCandidate {
+  int form, threads;
+};
+void autotune_in_solve(Ctx& C) {
+  Hierarchy& H = *C.H;
+  Level& L0 = *H.lev[0];
+  if (L0.A.nnz < (1 << 20)) return;  // small operators: the defaults
+  const bool log = getenv("GIAMG_TUNE_LOG") != nullptr;
+  cudaStream_t s = H.stream;
+  const int64_t n = H.n;
+  DBuf<double> b, x;
+  b.alloc(n, s);
+  x.alloc(n, s);
+  fill_tune_vector(n, b.get(), s);
+  cudaEvent_t e0, e1;
+  GIAMG_CUDA(cudaEventCreate(&e0));
+  GIAMG_CUDA(cudaEventCreate(&e1));
+  const giamg_options saved = H.opt;
+  H.opt.device_ptrs = 1;
+  H.opt.graphs = 0;  // every candidate on the host loop (the same kernels as the captured graph)
+  const std::vector<TuneCandidate> cands[2] = {
+      {{0, 0}, {1, 16}, {1, 32}, {2, 16}, {5, 0}, {6, 0}},            // FP64
+      {{0, 0}, {2, 8}, {2, 32}, {4, 0}, {5, 0}, {6, 0}}};             // FP32
+  try {
+    for (int prec = 0; prec < 2; ++prec) {
+      RowVariant best = prec == 0 ? L0.A.var64 : L0.A.var32;
+      float best_ms = 1e30f;
+      for (const TuneCandidate& c : cands[prec]) {
+        RowVariant& v = prec == 0 ? L0.A.var64 : L0.A.var32;
+        const RowVariant keep = v;
+        v = variant_for(L0.A, prec, c.form, c.threads);
+        const RowVariant want = v;
+        build_variant_copies(L0.A, s);
+        if (v.vector != want.vector || v.sliced != want.sliced) {  // the form does not apply here
+          v = keep;
+          build_variant_copies(L0.A, s);
+          continue;
+        }
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          int it = 0;
+          double rr = 0.0;
+          GIAMG_CUDA(cudaEventRecord(e0, s));
+          solve_impl(C, prec, kTuneIters, b.get(), x.get(), 0.0, &it, &rr);
+          GIAMG_CUDA(cudaEventRecord(e1, s));
+          GIAMG_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          GIAMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          t = std::min(t, ms);
+        }
+        if (log)
+          fprintf(stderr, "tune %s form=%d threads=%d (%s, %d lanes): %.3f ms for %d iterations\n",
+                  prec ? "fp32" : "fp64", c.form, c.threads,
+                  v.sliced ? "sliced" : v.vector ? "vector" : v.hybrid ? "hybrid" : v.group ? "groups" : v.pat ? "pattern" : "csr",
+                  v.tpr, t, kTuneIters);
+        if (t < best_ms) {
+          best_ms = t;
+          best = v;
+        }
+      }
+      (prec == 0 ? L0.A.var64 : L0.A.var32) = best;
+      build_variant_copies(L0.A, s);
+    }
+  } catch (...) {
+    H.opt = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  H.opt = saved;
+  H.hist.clear();
+  H.last_iters = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_solve_graphs(H);
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+}
+
 Ctx* ctx_of(giamg_handle h) {
   GIAMG_CHECK(h != nullptr, GIAMG_ERR_ARG, "NULL handle");
   return reinterpret_cast<Ctx*>(h);
@@ -1224,6 +1327,17 @@ int giamg_setup(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     GIAMG_CHECK(out != nullptr, GIAMG_ERR_ARG, "out is NULL");
     *out = nullptr;
     Ctx* C = setup_impl(n, row_ptr, col_idx, val, n_elem, elem_dof, elem_order, coords, opt, cuda_stream);
+    if (C->H->opt.autotune) {
+      try {
+        autotune_in_solve(*C);
+      } catch (...) {
+        cudaStream_t st = C->H->stream;
+        delete C->H;
+        delete C;
+        cudaStreamSynchronize(st);
+        throw;
+      }
+    }
     *out = reinterpret_cast<giamg_handle>(C);
     return GIAMG_OK;
   });
@@ -1376,11 +1490,36 @@ int giamg_set_cheb_degree(giamg_handle h, int degree) {
       if (H.lev[l]->kind != GIAMG_LEVEL_COARSEST)
         C.ex[l].cheb = cheb_coeffs(H.lev[l]->rho, H.opt.cheb_lo, H.opt.cheb_hi, degree);
     // the captured solve graphs hold the old coefficients as kernel arguments
-    for (SolveGraph& G : H.graph)
-      if (G.exec) {
-        GIAMG_CUDA(cudaGraphExecDestroy(G.exec));
-        G = SolveGraph{};
-      }
+    drop_solve_graphs(H);
+    return GIAMG_OK;
+  });
+}
+
+int giamg_set_row_kernel(giamg_handle h, int level, int precision, int form, int threads) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Hierarchy& H = *C.H;
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(precision == 0 || precision == 1, GIAMG_ERR_ARG, "precision must be 0 or 1");
+    GIAMG_CHECK(form >= 0 && form <= 6, GIAMG_ERR_ARG, "form must be in 0..6");
+    GIAMG_CHECK(threads == 0 || threads == 4 || threads == 8 || threads == 16 || threads == 32, GIAMG_ERR_ARG,
+                "threads must be 0, 4, 8, 16 or 32");
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));  // no solve of the old kernels in flight
+    (precision == 0 ? L.A.var64 : L.A.var32) = variant_for(L.A, precision, form, threads);
+    build_variant_copies(L.A, H.stream);
+    drop_solve_graphs(H);
+    return GIAMG_OK;
+  });
+}
+
+int giamg_set_batch_rows(giamg_handle h, int level, int rows_per_item) {
+  return guarded([&] {
+    Ctx& C = *ctx_of(h);
+    Hierarchy& H = *C.H;
+    Level& L = level_of(C, level);
+    GIAMG_CHECK(rows_per_item >= 0 && rows_per_item <= 2, GIAMG_ERR_ARG, "rows_per_item must be 0, 1 or 2");
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));
+    L.A.batch_rows = rows_per_item;
     drop_batch_graphs(H);
     return GIAMG_OK;
   });

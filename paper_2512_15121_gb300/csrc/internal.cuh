@@ -172,6 +172,8 @@ struct DCSR {
   Pattern pat;  // optional compressed column structure for the row kernels
   Groups grp;   // optional row groups with identical column sets
   RowVariant var64, var32;
+  int batch_rows = 0;  // multi-right-hand-side FP32 products: 0 automatic (two rows of a group per
+                       // warp when m > 16), 1 one row per warp, 2 two rows of a group per warp
 };
 
 // ------------------------------------------------------------------ hierarchy
@@ -483,8 +485,6 @@ void spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 // untouched) when the groups' patterns do not fit its tables
 bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 void csr_to32(DCSR& A, cudaStream_t s);
-// time the row-kernel variants on A (both precisions) and keep the fastest in A.var64 / A.var32
-void tune_rows(DCSR& A, cudaStream_t s);
 // the group-major copy of the big groups' values for the vector hybrid form from the FP32
 // (precision 1, A.v32) or FP64 (precision 0, A.v) values; needs the hybrid lists; false if the
 // form does not apply
@@ -495,8 +495,14 @@ bool batch_pairs_build(DCSR& A, cudaStream_t s);
 // the row groups; false if the form does not apply
 bool sliced_build(DCSR& A, int precision, cudaStream_t s);
 constexpr int kSliceStep = 8;  // columns per step of the sliced kernels (slice lengths are multiples)
+// the row-kernel variant of A for precision prec (0 FP64, 1 FP32): form 0 the defaults measured
+// best inside the solve, 1..6 forced (CSR, row patterns, row groups, hybrid, vector hybrid,
+// sliced); threads forces threads per row where the form has a choice
+RowVariant variant_for(const DCSR& A, int prec, int form, int threads);
 // set A.var64 / A.var32 from forced options or the defaults measured best inside the solve
 void choose_rows(DCSR& A, int form, int threads);
+// a deterministic, nonzero test vector (the tuner's right-hand side)
+void fill_tune_vector(int64_t n, double* x, cudaStream_t s);
 // prefetch_rows -1: automatic, 0: off, > 0: distance in rows; chains 0: keep, else 2, 4 or 8
 void set_prefetch(DCSR& A, int prefetch_rows, int chains);
 // detect row groups with identical column sets (exact; leaves A.grp off if not worthwhile for the

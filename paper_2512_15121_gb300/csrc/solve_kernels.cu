@@ -1291,56 +1291,56 @@ inline unsigned vec_grid(int64_t n) { return (unsigned)std::min<int64_t>(std::ma
 }  // namespace
 
 // ================================================================== launchers
-// Time every row-kernel variant (CSR, pattern with 2 or 4 chains, row groups; 4..32 threads
-// per row) on A with CUDA events and keep the fastest per precision: best of five runs on a
-// non-constant x after one warm-up run.  Only matrices large enough to matter are tuned.
-// GIAMG_TUNE_LOG=1 prints the timings to stderr.
-__global__ void tune_fill(int64_t n, double* x64, float* x32) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = 1.0 + 1e-3 * (double)(i % 97);
-    x64[i] = v;
-    x32[i] = (float)v;
+__global__ void tune_fill(int64_t n, double* x64) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x64[i] = 1.0 + 1e-3 * (double)(i % 97);
+}
+
+void fill_tune_vector(int64_t n, double* x, cudaStream_t s) {
+  if (n > 0) { tune_fill<<<vec_grid(n), 256, 0, s>>>(n, x); note_launch(); }
+  GIAMG_CUDA(cudaGetLastError());
+}
+
+RowVariant variant_for(const DCSR& A, int prec, int form, int threads) {
+  const double avg = A.n ? (double)A.nnz / A.n : 0.0;
+  RowVariant v;
+  if (form == 0) {
+    // defaults: the vector hybrid form (big row groups from a group-major copy with x in
+    // shared memory, the other rows on the pattern form) where there are enough big groups to
+    // fill the GPU for many waves and their rows are long (measured faster from 12^3 elements
+    // at p = 6 and on the 12^3, p = 8 operator; slower at 8^3 and at p = 4), in both
+    // precisions; else FP32 rows on the pattern form (halved index traffic) and FP64 rows,
+    // which are bound by the 1/64-rate FP64 pipe, on CSR, threads per row by auto_tpr
+    const bool big = A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
+    // the sliced form (one lane per row, slices of 32 rows of equal length) on levels of at
+    // least 2^18 rows (8192 slices: several waves of warps; below that a warp's long serial
+    // slice leaves the GPU latency-bound): the FP64 rows there, since it gives the FP64 pipe
+    // one useful FMA per lane and instruction (16^3 p = 6: 0.70 ms per product against 0.93 for
+    // the vector hybrid, 12^3 p = 8: 1.34 against 1.59, 24^3 p = 4: 0.32 against 0.58 on CSR),
+    // and the FP32 rows where the vector hybrid does not apply (24^3 p = 4: 0.16 against 0.23
+    // on row patterns; on the hybrid's operators the FP32 vector hybrid is as fast at p = 6 and
+    // faster at p = 8, 0.52 against 0.68)
+    const bool large = A.grp.on && A.n >= (1 << 18);
+    v.sliced = large && (prec == 0 || !big);
+    v.pat = !v.sliced && (prec == 1 || big) && A.pat.on;
+    v.hybrid = !v.sliced && big;
+    v.vector = !v.sliced && big;
+    v.tpr = v.sliced ? 1 : big ? 32 : auto_tpr(A.n, avg, prec == 1 ? 24.0 : 48.0);
+  } else {
+    v.pat = (form == 2 || form == 4 || form == 5) && A.pat.on;
+    v.group = form == 3 && A.grp.on;
+    v.hybrid = (form == 4 || form == 5) && A.grp.hyb && A.pat.on;
+    v.vector = form == 5 && v.hybrid;
+    v.sliced = form == 6 && A.grp.on;
+    v.tpr = v.group || v.hybrid ? 32 : v.sliced ? 1 : default_tpr(avg);
   }
+  if (threads && !v.group && !v.hybrid && !v.sliced) v.tpr = threads;
+  return v;
 }
 
 void choose_rows(DCSR& A, int form, int threads) {
-  const double avg = A.n ? (double)A.nnz / A.n : 0.0;
-  for (int prec = 0; prec < 2; ++prec) {
-    RowVariant v;
-    if (form == 0) {
-      // defaults: the vector hybrid form (big row groups from a group-major copy with x in
-      // shared memory, the other rows on the pattern form) where there are enough big groups to
-      // fill the GPU for many waves and their rows are long (measured faster from 12^3 elements
-      // at p = 6 and on the 12^3, p = 8 operator; slower at 8^3 and at p = 4), in both
-      // precisions; else FP32 rows on the pattern form (halved index traffic) and FP64 rows,
-      // which are bound by the 1/64-rate FP64 pipe, on CSR, threads per row by auto_tpr
-      const bool big = A.pat.on && A.grp.hyb && A.grp.n_big >= 4096 && A.grp.big_cols >= 192.0;
-      // the sliced form (one lane per row, slices of 32 rows of equal length) on levels of at
-      // least 2^18 rows (8192 slices: several waves of warps; below that a warp's long serial
-      // slice leaves the GPU latency-bound): the FP64 rows there, since it gives the FP64 pipe
-      // one useful FMA per lane and instruction (16^3 p = 6: 0.70 ms per product against 0.93 for
-      // the vector hybrid, 12^3 p = 8: 1.34 against 1.59, 24^3 p = 4: 0.32 against 0.58 on CSR),
-      // and the FP32 rows where the vector hybrid does not apply (24^3 p = 4: 0.16 against 0.23
-      // on row patterns; on the hybrid's operators the FP32 vector hybrid is as fast at p = 6 and
-      // faster at p = 8, 0.52 against 0.68)
-      const bool large = A.grp.on && A.n >= (1 << 18);
-      v.sliced = large && (prec == 0 || !big);
-      v.pat = !v.sliced && (prec == 1 || big) && A.pat.on;
-      v.hybrid = !v.sliced && big;
-      v.vector = !v.sliced && big;
-      v.tpr = v.sliced ? 1 : big ? 32 : auto_tpr(A.n, avg, prec == 1 ? 24.0 : 48.0);
-    } else {
-      v.pat = (form == 2 || form == 4 || form == 5) && A.pat.on;
-      v.group = form == 3 && A.grp.on;
-      v.hybrid = (form == 4 || form == 5) && A.grp.hyb && A.pat.on;
-      v.vector = form == 5 && v.hybrid;
-      v.sliced = form == 6 && A.grp.on;
-      v.tpr = v.group || v.hybrid ? 32 : v.sliced ? 1 : default_tpr(avg);
-      if (form == 6 && !v.sliced) v.tpr = default_tpr(avg);  // no groups: CSR
-    }
-    if (threads && !v.group && !v.hybrid && !v.sliced) v.tpr = threads;
-    (prec == 0 ? A.var64 : A.var32) = v;
-  }
+  A.var64 = variant_for(A, 0, form, threads);
+  A.var32 = variant_for(A, 1, form, threads);
 }
 
 // Default L2 prefetch distance of the pattern kernels, about the rows of half the warps resident
@@ -1353,104 +1353,6 @@ void set_prefetch(DCSR& A, int prefetch_rows, int chains) {
   A.var32.prefetch = pf;
   A.var64.prefetch = pf;
   if (chains) A.var32.unroll = A.var64.unroll = chains;
-}
-
-void tune_rows(DCSR& A, cudaStream_t s) {
-  if (A.nnz < (1 << 20)) return;
-  const bool log = getenv("GIAMG_TUNE_LOG") != nullptr;
-  DBuf<double> x64, y64;
-  DBuf<float> x32, y32;
-  x64.alloc(A.n, s); y64.alloc(A.n, s); x32.alloc(A.n, s); y32.alloc(A.n, s);
-  { tune_fill<<<vec_grid(A.n), 256, 0, s>>>(A.n, x64.get(), x32.get()); note_launch(); }
-  cudaEvent_t e0, e1;
-  GIAMG_CUDA(cudaEventCreate(&e0));
-  GIAMG_CUDA(cudaEventCreate(&e1));
-  const double avg = (double)A.nnz / A.n;
-  std::vector<RowVariant> cands;
-  for (int tpr : {4, 8, 16, 32}) {
-    RowVariant v;
-    v.tpr = tpr;
-    cands.push_back(v);  // CSR
-    if (A.pat.on) {
-      v.pat = true;
-      v.unroll = 2;
-      cands.push_back(v);
-      v.unroll = 4;
-      cands.push_back(v);
-    }
-  }
-  if (A.grp.on) {
-    RowVariant v;
-    v.tpr = 32;
-    v.group = true;
-    cands.push_back(v);
-  }
-  // the hybrid forms, the vector ones on group-major copies built for the timing, and the sliced form
-  const bool vec = A.grp.hyb && A.pat.on && hybrid_vector_build(A, 1, s) && hybrid_vector_build(A, 0, s);
-  const bool sel = A.grp.on && sliced_build(A, 0, s) && sliced_build(A, 1, s);
-  if (sel) {
-    RowVariant v;
-    v.tpr = 1;
-    v.sliced = true;
-    cands.push_back(v);
-  }
-  if (A.grp.hyb && A.pat.on) {
-    RowVariant v;
-    v.tpr = 32;
-    v.pat = true;
-    v.hybrid = true;
-    cands.push_back(v);
-    v.vector = true;
-    if (vec) cands.push_back(v);
-  }
-  for (int prec = 0; prec < 2; ++prec) {
-    float best = 1e30f;
-    RowVariant pick;
-    for (const RowVariant& v : cands) {
-      float t = 1e30f;
-      for (int rep = 0; rep < 6; ++rep) {
-        GIAMG_CUDA(cudaEventRecord(e0, s));
-        if (prec == 0)
-          launch_variant<double, kSpmv>(A, v, avg, A.v.get(), x64.get(), nullptr, y64.get(), nullptr, nullptr, 0.0, 0.0, s);
-        else
-          launch_variant<float, kSpmv>(A, v, avg, A.v32.get(), x32.get(), nullptr, y32.get(), nullptr, nullptr, 0.f, 0.f, s);
-        GIAMG_CUDA(cudaEventRecord(e1, s));
-        GIAMG_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        GIAMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0) t = std::min(t, ms);
-      }
-      if (log)
-        fprintf(stderr, "tune n=%lld nnz=%lld %s form=%s tpr=%d unroll=%d: %.4f ms\n", (long long)A.n,
-                (long long)A.nnz, prec ? "fp32" : "fp64",
-                v.sliced ? "sliced" : v.vector ? "vector" : v.hybrid ? "hybrid" : v.group ? "groups" : v.pat ? "pattern" : "csr", v.tpr,
-                v.unroll, t);
-      if (t < best) {
-        best = t;
-        pick = v;
-      }
-    }
-    (prec == 0 ? A.var64 : A.var32) = pick;
-  }
-  // a copy is kept only for the form that reads it
-  if (vec && !A.var32.vector) {
-    A.grp.hv.release();
-    A.grp.hvon = false;
-  }
-  if (vec && !A.var64.vector) {
-    A.grp.hv64.release();
-    A.grp.hv64on = false;
-  }
-  if (sel && !A.var32.sliced) {
-    A.grp.sv32.release();
-    A.grp.sv32on = false;
-  }
-  if (sel && !A.var64.sliced) {
-    A.grp.sv64.release();
-    A.grp.sv64on = false;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
 }
 
 void spmv(const DCSR& A, const double* x, double* y, cudaStream_t s, double avg) {

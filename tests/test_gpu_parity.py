@@ -373,8 +373,9 @@ def test_row_kernel_forms_match_oracle(form, threads):
 
 
 def test_autotuned_forms_match_oracle():
-    """autotune = 1 times every row-kernel form on the large levels at setup (the hybrid and vector
-    hybrid forms included) and keeps the fastest product; whatever it picks matches the oracle."""
+    """autotune = 1 times the finest level's row-kernel candidates inside the solve at setup (the
+    hybrid, vector hybrid and sliced forms included) and keeps the fastest per precision; whatever
+    it picks matches the oracle."""
     if "p" not in _forms_oracle:
         prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
         _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
@@ -399,6 +400,55 @@ def test_autotuned_forms_match_oracle():
         assert rrm <= 1e-8
         r = prob.b - orc.spmv(0, host(xm))
         assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(prob.b)
+    finally:
+        gpu.close()
+
+
+def test_switching_row_kernels_and_batch_rows_after_setup():
+    """giamg_set_row_kernel switches a level's kernel after setup (dropping the captured graphs) and
+    giamg_set_batch_rows the multi-RHS FP32 products: every choice matches the oracle, a switch
+    back gives the original bits, and the in-solve tuners leave a valid choice set."""
+    from paper_2512_15121_gb300 import tune
+    if "p" not in _forms_oracle:
+        prob = fegen.make(5, 6, mesh="jitter", lam=10.0)
+        _forms_oracle["p"] = (prob, oracle.Hierarchy.from_problem(prob, cheb_degree=3))
+    prob, orc = _forms_oracle["p"]
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=3, graphs=2)
+    try:
+        b = dev(prob.b)
+        xo, ito, _, _, _ = orc.solve(prob.b, rtol=1e-8)
+        x_ref, _, _ = gpu.solve(b, rtol=1e-8, precision=0, force_iters=ito)
+        for form in (1, 2, 3, 4, 5, 6, 0):
+            for prec in (0, 1):
+                gpu.set_row_kernel(0, prec, form)
+            assert gpu.kernel(0, 0)[1] == (FORMS[form - 1] if form else gpu.kernel(0, 0)[1])
+            x, it, _ = gpu.solve(b, rtol=1e-8, precision=0, force_iters=ito)
+            assert it == ito and np.max(np.abs(host(x) - xo)) <= 1e-10 * np.max(np.abs(xo)), form
+            xm, itm, rrm = gpu.solve(b, rtol=1e-8, precision=1)
+            assert rrm <= 1e-8, form
+        x_back, _, _ = gpu.solve(b, rtol=1e-8, precision=0, force_iters=ito)
+        assert torch.equal(x_back, x_ref)  # form 0 again: the setup's own kernels
+        with pytest.raises(g.GiamgError):
+            gpu.set_row_kernel(0, 0, 7)
+        with pytest.raises(g.GiamgError):
+            gpu.set_batch_rows(0, 3)
+        # multi-RHS FP32 products with one and two rows per item: each column as the oracle's
+        B = np.stack([prob.rhs("fourier", 1000 + j) for j in range(20)], axis=1)
+        for rows in (1, 2, 0):
+            gpu.set_batch_rows(0, rows)
+            X, its, rr = gpu.solve_batch(dev(B), rtol=1e-8, precision=1)
+            assert np.all(rr <= 1e-8), rows
+            for j in (0, 19):
+                r = B[:, j] - orc.spmv(0, host(X)[:, j])
+                assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(B[:, j]), (rows, j)
+        # the in-solve tuners: whatever they keep solves correctly
+        best, timings = tune.tune_row_kernels(gpu, b, precision=1, candidates=((0, 0), (2, 8), (6, 0)), reps=1,
+                                              warmup=1)
+        assert best in ((0, 0), (2, 8), (6, 0)) and len(timings) == 3
+        _, _, rr = gpu.solve(b, rtol=1e-8, precision=1)
+        assert rr <= 1e-8
+        rows, bt = tune.tune_batch_rows(gpu, dev(B), reps=1, warmup=1)
+        assert rows in (1, 2) and len(bt) == 2
     finally:
         gpu.close()
 

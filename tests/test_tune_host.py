@@ -40,3 +40,52 @@ def test_when_no_degree_reaches_rtol_the_fastest_is_kept():
     best, _ = tune.tune_cheb_degree(S, None, degrees=(1,), rtol=1e-8, reps=1, warmup=0,
                                     timer=lambda fn: (fn(), 1.0))
     assert best == 1 and S.k == 1
+
+
+class FakeKernelSolver:
+    """Row kernels and batch rows: times per choice from tables; one form misses the tolerance."""
+    MS = {(0, 0): 10.0, (1, 16): 12.0, (5, 0): 9.0, (6, 0): 8.0, (2, 8): 7.0}
+    BMS = {1: 5.0, 2: 4.0}
+
+    def __init__(self):
+        self.form = {0: (0, 0), 1: (0, 0)}
+        self.rows = {}
+        self.log = []
+
+    def set_row_kernel(self, level, precision, form, threads=0):
+        self.form[precision] = (form, threads)
+        self.log.append(("set", level, precision, form, threads))
+
+    def kernel(self, level, precision):
+        return (1, "sliced") if self.form[precision][0] == 6 else (32, "other")
+
+    def solve(self, b, rtol, precision):
+        rr = 1e-6 if self.form[precision] == (2, 8) else 0.5 * rtol  # (2, 8) is fast but wrong
+        return None, 9, rr
+
+    def set_batch_rows(self, level, rows):
+        self.rows[level] = rows
+
+    def solve_batch(self, B, rtol, precision):
+        import numpy as np
+        return None, np.array([11, 12]), np.array([1e-9, 2e-9])
+
+
+def test_row_kernel_tuner_keeps_the_fastest_valid_choice():
+    S = FakeKernelSolver()
+    timer = lambda fn: (fn(), FakeKernelSolver.MS[S.form[1]])
+    cands = ((0, 0), (1, 16), (2, 8), (5, 0), (6, 0))
+    best, timings = tune.tune_row_kernels(S, None, precision=1, candidates=cands, reps=2, warmup=1, timer=timer)
+    # (2, 8) is fastest but misses rtol; of the rest the sliced form (6, 0) wins and stays set
+    assert best == (6, 0) and S.form[1] == (6, 0) and S.form[0] == (0, 0)
+    assert [t.choice for t in timings] == list(cands)
+    assert timings[-1].kernel == (1, "sliced") and timings[0].ms == 10.0
+    assert S.log[-1] == ("set", 0, 1, 6, 0)
+
+
+def test_batch_rows_tuner_sets_every_level():
+    S = FakeKernelSolver()
+    timer = lambda fn: (fn(), FakeKernelSolver.BMS[S.rows[0]])
+    best, timings = tune.tune_batch_rows(S, None, choices=(1, 2), levels=(0, 1), reps=1, warmup=0, timer=timer)
+    assert best == 2 and S.rows == {0: 2, 1: 2}
+    assert [t.iterations for t in timings] == [12, 12] and timings[0].ms == 5.0
