@@ -173,6 +173,24 @@ GIAMG_API int giamg_solve_ex(giamg_handle h, int precision, int force_iters, con
 GIAMG_API int giamg_solve_async(giamg_handle h, int precision, const double* b, double* x, double rtol, int* iters,
                                 double* relres, int* status);
 
+/* The multi-right-hand-side solves of several hierarchies at once, for a server whose requests
+ * for different operators are ready together: every phase of an iteration (the outer product and
+ * CG updates, each V-cycle level's smoother steps, residual, transfers and coarsest solve) is ONE
+ * kernel launch over all hierarchies that take part in it, each hierarchy's share of the grid
+ * being the grid of its own launch, so each hierarchy's results are bit for bit those of
+ * giamg_solve_batch with the same arguments (FP32 V-cycle in FP64 flexible CG, precision 1,
+ * independent columns).  No counterpart in the paper (a serving feature).
+ *   count: number of hierarchies; handles[count]: distinct handles on one device, each with
+ *     device_ptrs = 1; work runs on handles[0]'s stream (the other handles' streams are
+ *     synchronised first).
+ *   m[count]: right-hand sides per hierarchy (1..32); B[i], X[i]: device arrays, row-major
+ *     n_i x m[i] (caller-owned).
+ *   iters, relres: host arrays of sum(m) entries, hierarchy after hierarchy (NULL to skip);
+ *   status[count] (NULL to skip): GIAMG_OK, GIAMG_ERR_MAXITER or GIAMG_ERR_BREAKDOWN per hierarchy.
+ * The return value reports argument and CUDA errors only; the call synchronises the stream. */
+GIAMG_API int giamg_solve_grouped(int count, const giamg_handle* handles, const int* m, const double* const* B,
+                                  double* const* X, double rtol, int* iters, double* relres, int* status);
+
 /* m independent solves A X_j = B_j sharing every matrix pass (multi-right-hand-side PCG: one
  * CG recurrence per column, each with its own alpha, beta and stopping test; the products and
  * the V-cycle work on all columns at once, so the matrix is read once per m solves).

@@ -24,7 +24,7 @@ GIAMG_LEVEL_P, GIAMG_LEVEL_H, GIAMG_LEVEL_COARSEST = 0, 1, 2
 
 # every entry point the header declares (checked by the CPU tests against the .so)
 EXPORTS = ["giamg_default_options", "giamg_setup", "giamg_solve", "giamg_solve_ex", "giamg_solve_stats",
-           "giamg_solve_async", "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block",
+           "giamg_solve_async", "giamg_solve_batch", "giamg_solve_batch_ex", "giamg_solve_block", "giamg_solve_grouped",
            "giamg_num_levels", "giamg_level_info", "giamg_level_templates", "giamg_level_kernel", "giamg_export_level", "giamg_export_prolongation",
            "giamg_level_rho", "giamg_set_cheb_degree", "giamg_set_row_kernel", "giamg_set_batch_rows", "giamg_apply_vcycle", "giamg_level_spmv", "giamg_level_spmv32", "giamg_level_smooth",
            "giamg_level_restrict", "giamg_level_prolong", "giamg_coarse_solve", "giamg_level_residual",
@@ -77,6 +77,7 @@ def lib():
         L.giamg_solve_batch_ex.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
         L.giamg_solve_block.argtypes = [vp, i32, i32, i32, vp, vp, dbl, vp, vp]
         L.giamg_solve_async.argtypes = [vp, i32, vp, vp, dbl, vp, vp, vp]
+        L.giamg_solve_grouped.argtypes = [i32, vp, vp, vp, vp, dbl, vp, vp, vp]
         L.giamg_num_levels.argtypes = [vp, P(i32)]
         L.giamg_level_info.argtypes = [vp, i32, P(i32), P(i64), P(i64), P(i32), P(i64), P(i64)]
         L.giamg_export_level.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -160,6 +161,39 @@ def launch_count() -> int:
     c = ctypes.c_int64()
     _check(lib().giamg_launch_count(ctypes.byref(c)))
     return c.value
+
+
+def solve_grouped(solvers, Bs, rtol=1e-8, Xs=None):
+    """The multi-RHS solves of several hierarchies at once (giamg_solve_grouped): one kernel launch
+    per phase for all of them, each with the bits of its own solve_batch (FP32 V-cycle).  solvers:
+    Solver objects in device mode on one device; Bs: CUDA float64 tensors n_i x m_i (m_i <= 32).
+    Returns [(X, iters, relres, status)] in solver order."""
+    import torch
+    k = len(solvers)
+    if k == 0 or len(Bs) != k:
+        raise ValueError("one right-hand-side block per solver is needed")
+    Bs = [B.to("cuda", torch.float64).contiguous() for B in Bs]
+    for S, B in zip(solvers, Bs):
+        if not S.device:
+            raise GiamgError(GIAMG_ERR_ARG, "solve_grouped needs device=True solvers")
+        if len(B.shape) != 2 or B.shape[0] != S.n or not 1 <= B.shape[1] <= 32:
+            raise ValueError(f"B: shape {tuple(B.shape)}, expected ({S.n}, m) with 1 <= m <= 32")
+    Xs = [torch.empty_like(B) for B in Bs] if Xs is None else Xs
+    for S, B, X in zip(solvers, Bs, Xs):
+        S._check_out("X", X, tuple(B.shape))
+    ms = np.array([B.shape[1] for B in Bs], np.int32)
+    hs = (ctypes.c_void_p * k)(*[S._h.value for S in solvers])
+    bp = (ctypes.c_void_p * k)(*[B.data_ptr() for B in Bs])
+    xp = (ctypes.c_void_p * k)(*[X.data_ptr() for X in Xs])
+    it = np.zeros(int(ms.sum()), np.int32)
+    rr = np.zeros(int(ms.sum()), np.float64)
+    st = np.zeros(k, np.int32)
+    _check(lib().giamg_solve_grouped(k, hs, _ptr(ms), bp, xp, rtol, _ptr(it), _ptr(rr), _ptr(st)))
+    out, o = [], 0
+    for i in range(k):
+        out.append((Xs[i], it[o:o + ms[i]], rr[o:o + ms[i]], int(st[i])))
+        o += int(ms[i])
+    return out
 
 
 def giamg_free(h):

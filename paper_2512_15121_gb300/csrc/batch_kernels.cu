@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -32,13 +33,18 @@ inline unsigned vec_grid(int64_t n) {
 enum BatchMode { kSpmm = 0, kResid = 1, kBatCheb = 2, kAdd = 3 };
 
 // One row per group of G lanes; lane j < m owns column j.  PAT: columns from the row's template.
+//
+// Every kernel body below takes the block index and the grid size as arguments (vb, nvb): the
+// standalone kernels pass blockIdx.x and gridDim.x, the grouped kernels (several hierarchies in
+// one launch) the block's index and count within its hierarchy's share of the grid, so a
+// hierarchy's arithmetic -- reduction partitions included -- is the same alone and in a group.
 template <int G, typename V, int MODE, bool PAT>
-__global__ void __launch_bounds__(kThreads)
-    bat_rows(int64_t n, int m, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-             const int32_t* __restrict__ obase, const int32_t* __restrict__ toff,
-             const V* __restrict__ val, const V* __restrict__ X, const V* __restrict__ B, V* __restrict__ Y,
-             V* __restrict__ D, const V* __restrict__ dinv, V c1, V c2) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bat_rows_body(int64_t vb, int64_t n, int m, const int64_t* __restrict__ rp,
+                                              const int32_t* __restrict__ ci, const int32_t* __restrict__ obase,
+                                              const int32_t* __restrict__ toff, const V* __restrict__ val,
+                                              const V* __restrict__ X, const V* __restrict__ B, V* __restrict__ Y,
+                                              V* __restrict__ D, const V* __restrict__ dinv, V c1, V c2) {
+  const int64_t gt = vb * blockDim.x + threadIdx.x;
   const int64_t row = gt / G;
   const int j = threadIdx.x % G;
   if (row >= n || j >= m) return;
@@ -78,19 +84,28 @@ __global__ void __launch_bounds__(kThreads)
     Y[o] = X[o] + dn;
   }
 }
+template <int G, typename V, int MODE, bool PAT>
+__global__ void __launch_bounds__(kThreads)
+    bat_rows(int64_t n, int m, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+             const int32_t* __restrict__ obase, const int32_t* __restrict__ toff,
+             const V* __restrict__ val, const V* __restrict__ X, const V* __restrict__ B, V* __restrict__ Y,
+             V* __restrict__ D, const V* __restrict__ dinv, V c1, V c2) {
+  bat_rows_body<G, V, MODE, PAT>(blockIdx.x, n, m, rp, ci, obase, toff, val, X, B, Y, D, dinv, c1, c2);
+}
 
 // FP32, m > 16 columns: one warp per work item of two rows of one row group (or one row), lane j
 // owning column j.  The two rows have the same columns (the group's column list), so each
 // gathered X row (128 bytes) serves both; values are those of each row's CSR entries.  The
 // products are summed in bat_rows' order (even and odd entries in two chains).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads)
-    bat_pairs(int64_t n_items, const int32_t* __restrict__ ia, const int32_t* __restrict__ ib,
-              const int32_t* __restrict__ ig, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gcol,
-              const int64_t* __restrict__ rp, int m, const float* __restrict__ val, const float* __restrict__ X,
-              const float* __restrict__ B, float* __restrict__ Y, float* __restrict__ D,
-              const float* __restrict__ dinv, float c1, float c2) {
-  const int64_t item = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+__device__ __forceinline__ void bat_pairs_body(int64_t vblock, int64_t n_items, const int32_t* __restrict__ ia,
+                                               const int32_t* __restrict__ ib, const int32_t* __restrict__ ig,
+                                               const int64_t* __restrict__ gptr, const int32_t* __restrict__ gcol,
+                                               const int64_t* __restrict__ rp, int m, const float* __restrict__ val,
+                                               const float* __restrict__ X, const float* __restrict__ B,
+                                               float* __restrict__ Y, float* __restrict__ D,
+                                               const float* __restrict__ dinv, float c1, float c2) {
+  const int64_t item = vblock * (kThreads / 32) + (threadIdx.x >> 5);
   const int j = threadIdx.x & 31;
   if (item >= n_items || j >= m) return;
   const int64_t ra = ia[item], rb = ib[item], g = ig[item];
@@ -140,6 +155,15 @@ __global__ void __launch_bounds__(kThreads)
   finish(ra, a0 + a1);
   if (rb >= 0) finish(rb, b0 + b1);
 }
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+    bat_pairs(int64_t n_items, const int32_t* __restrict__ ia, const int32_t* __restrict__ ib,
+              const int32_t* __restrict__ ig, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gcol,
+              const int64_t* __restrict__ rp, int m, const float* __restrict__ val, const float* __restrict__ X,
+              const float* __restrict__ B, float* __restrict__ Y, float* __restrict__ D,
+              const float* __restrict__ dinv, float c1, float c2) {
+  bat_pairs_body<MODE>(blockIdx.x, n_items, ia, ib, ig, gptr, gcol, rp, m, val, X, B, Y, D, dinv, c1, c2);
+}
 
 template <int G, typename V, int MODE, bool PAT>
 void launch_g(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y, V* D, const V* dinv, V c1, V c2,
@@ -187,9 +211,10 @@ void launch_bat(const DCSR& A, int m, const V* val, const V* X, const V* B, V* Y
 // ------------------------------------------------------------------ element transfers, m columns
 // The single-vector contractions with the column as the fastest index of every work array.
 template <typename V>
-__global__ void bp_prolong_kernel(int32_t n_elem, int p, int q, int m, const int32_t* __restrict__ l2g,
-                                  const uint8_t* __restrict__ own, const int32_t* __restrict__ l2g_c,
-                                  const V* __restrict__ p1d, const V* __restrict__ ec, V* __restrict__ xf) {
+__device__ __forceinline__ void bp_prolong_body(int64_t vb, int p, int q, int m, const int32_t* __restrict__ l2g,
+                                                const uint8_t* __restrict__ own, const int32_t* __restrict__ l2g_c,
+                                                const V* __restrict__ p1d, const V* __restrict__ ec,
+                                                V* __restrict__ xf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int n1 = p + 1, m1 = q + 1;
@@ -198,7 +223,7 @@ __global__ void bp_prolong_kernel(int32_t n_elem, int p, int q, int m, const int
   V* u = T + n1 * m1;             // nlc * m
   V* t1 = u + nlc * m;            // m1 * m1 * n1 * m
   V* t2 = t1 + m1 * m1 * n1 * m;  // m1 * n1 * n1 * m
-  const int e = blockIdx.x;
+  const int64_t e = vb;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < n1 * m1; i += nt) T[i] = p1d[i];
   for (int i = tid; i < nlc * m; i += nt) {
@@ -230,11 +255,17 @@ __global__ void bp_prolong_kernel(int32_t n_elem, int p, int q, int m, const int
     xf[(int64_t)l2g[slot] * m + j] += s;
   }
 }
+template <typename V>
+__global__ void bp_prolong_kernel(int32_t n_elem, int p, int q, int m, const int32_t* __restrict__ l2g,
+                                  const uint8_t* __restrict__ own, const int32_t* __restrict__ l2g_c,
+                                  const V* __restrict__ p1d, const V* __restrict__ ec, V* __restrict__ xf) {
+  bp_prolong_body<V>(blockIdx.x, p, q, m, l2g, own, l2g_c, p1d, ec, xf);
+}
 
 template <typename V>
-__global__ void bp_restrict_kernel(int32_t n_elem, int p, int q, int m, const int32_t* __restrict__ l2g,
-                                   const uint8_t* __restrict__ own, const V* __restrict__ p1d,
-                                   const V* __restrict__ rf, V* __restrict__ part) {
+__device__ __forceinline__ void bp_restrict_body(int64_t vb, int p, int q, int m, const int32_t* __restrict__ l2g,
+                                                 const uint8_t* __restrict__ own, const V* __restrict__ p1d,
+                                                 const V* __restrict__ rf, V* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int n1 = p + 1, m1 = q + 1;
@@ -243,7 +274,7 @@ __global__ void bp_restrict_kernel(int32_t n_elem, int p, int q, int m, const in
   V* v = T + n1 * m1;             // nlf * m
   V* t1 = v + nlf * m;            // n1 * n1 * m1 * m
   V* t2 = t1 + n1 * n1 * m1 * m;  // n1 * m1 * m1 * m
-  const int e = blockIdx.x;
+  const int64_t e = vb;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < n1 * m1; i += nt) T[i] = p1d[i];
   for (int i = tid; i < nlf * m; i += nt) {
@@ -274,17 +305,29 @@ __global__ void bp_restrict_kernel(int32_t n_elem, int p, int q, int m, const in
     part[((int64_t)e * nlc + b) * m + j] = s;
   }
 }
+template <typename V>
+__global__ void bp_restrict_kernel(int32_t n_elem, int p, int q, int m, const int32_t* __restrict__ l2g,
+                                   const uint8_t* __restrict__ own, const V* __restrict__ p1d,
+                                   const V* __restrict__ rf, V* __restrict__ part) {
+  bp_restrict_body<V>(blockIdx.x, p, q, m, l2g, own, p1d, rf, part);
+}
 
 template <typename V>
-__global__ void bp_gather_kernel(int64_t nc, int m, const int64_t* __restrict__ ptr, const int32_t* __restrict__ slot,
-                                 const V* __restrict__ part, V* __restrict__ rc) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bp_gather_body(int64_t vb, int64_t nc, int m, const int64_t* __restrict__ ptr,
+                                               const int32_t* __restrict__ slot, const V* __restrict__ part,
+                                               V* __restrict__ rc) {
+  const int64_t g = vb * blockDim.x + threadIdx.x;
   if (g >= nc * m) return;
   const int64_t c = g / m;
   const int j = (int)(g % m);
   V s = 0;
   for (int64_t t = ptr[c]; t < ptr[c + 1]; ++t) s += part[(int64_t)slot[t] * m + j];
   rc[g] = s;
+}
+template <typename V>
+__global__ void bp_gather_kernel(int64_t nc, int m, const int64_t* __restrict__ ptr, const int32_t* __restrict__ slot,
+                                 const V* __restrict__ part, V* __restrict__ rc) {
+  bp_gather_body<V>(blockIdx.x, nc, m, ptr, slot, part, rc);
 }
 
 template <typename V>
@@ -300,9 +343,9 @@ size_t brestrict_smem(int p, int q, int m) {
 
 // ------------------------------------------------------------------ coarsest solve, vectors
 template <typename V>
-__global__ void bat_inverse_apply(const double* __restrict__ Ainv, int64_t nc, int m, const V* __restrict__ B,
-                                  V* __restrict__ X) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bat_inverse_body(int64_t vb, const double* __restrict__ Ainv, int64_t nc, int m,
+                                                 const V* __restrict__ B, V* __restrict__ X) {
+  const int64_t g = vb * blockDim.x + threadIdx.x;
   if (g >= nc * m) return;
   const int64_t row = g / m;
   const int j = (int)(g % m);
@@ -310,15 +353,26 @@ __global__ void bat_inverse_apply(const double* __restrict__ Ainv, int64_t nc, i
   for (int64_t k = 0; k < nc; ++k) s += Ainv[row * nc + k] * (double)B[k * m + j];
   X[g] = (V)s;
 }
+template <typename V>
+__global__ void bat_inverse_apply(const double* __restrict__ Ainv, int64_t nc, int m, const V* __restrict__ B,
+                                  V* __restrict__ X) {
+  bat_inverse_body<V>(blockIdx.x, Ainv, nc, m, B, X);
+}
 
 template <typename V>
-__global__ void bat_cheb_first(int64_t n, int m, const V* __restrict__ B, const V* __restrict__ dinv, V c2,
-                               V* __restrict__ X, V* __restrict__ D) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * m; i += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void bat_cheb_first_body(int64_t vb, int64_t nvb, int64_t n, int m, const V* __restrict__ B,
+                                                    const V* __restrict__ dinv, V c2, V* __restrict__ X,
+                                                    V* __restrict__ D) {
+  for (int64_t i = vb * blockDim.x + threadIdx.x; i < n * m; i += nvb * blockDim.x) {
     const V v = c2 * dinv[i / m] * B[i];
     D[i] = v;
     X[i] = v;
   }
+}
+template <typename V>
+__global__ void bat_cheb_first(int64_t n, int m, const V* __restrict__ B, const V* __restrict__ dinv, V c2,
+                               V* __restrict__ X, V* __restrict__ D) {
+  bat_cheb_first_body<V>(blockIdx.x, gridDim.x, n, m, B, dinv, c2, X, D);
 }
 
 // Batched CG scalars, one entry per column.
@@ -330,14 +384,13 @@ struct BatchScalars {
   int pad;
 };
 
-__global__ void __launch_bounds__(kRedThreads) bat_init(int64_t n, int m, const double* __restrict__ B,
-                                                        double* __restrict__ X, double* __restrict__ R,
-                                                        double* partial) {
+__device__ __forceinline__ void bat_init_body(int64_t vb, int64_t nvb, int64_t n, int m, const double* __restrict__ B,
+                                              double* __restrict__ X, double* __restrict__ R, double* partial) {
   __shared__ double sh[32 * 32];
   const int l = threadIdx.x & 31;
   double s = 0.0;
-  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  const int64_t rows_per_block = (n + nvb - 1) / nvb;
+  const int64_t r0 = vb * rows_per_block, r1 = min(n, r0 + rows_per_block);
   for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
     if (l < m) {
       const double b = B[i * m + l];
@@ -346,19 +399,23 @@ __global__ void __launch_bounds__(kRedThreads) bat_init(int64_t n, int m, const 
       s += b * b;
     }
   }
-  column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
+  column_block_sum(s, m, sh, partial + vb * 32);
+}
+__global__ void __launch_bounds__(kRedThreads) bat_init(int64_t n, int m, const double* __restrict__ B,
+                                                        double* __restrict__ X, double* __restrict__ R,
+                                                        double* partial) {
+  bat_init_body(blockIdx.x, gridDim.x, n, m, B, X, R, partial);
 }
 
 // <r_j, z_j> and, for flexible CG, <z_j, r_j - rold_j>
-__global__ void __launch_bounds__(kRedThreads) bat_dot_rz(int64_t n, int m, const double* __restrict__ R,
-                                                          const double* __restrict__ Z,
-                                                          const double* __restrict__ Rold, int flexible,
-                                                          double* partial) {
+__device__ __forceinline__ void bat_dot_rz_body(int64_t vb, int64_t nvb, int64_t n, int m, const double* __restrict__ R,
+                                                const double* __restrict__ Z, const double* __restrict__ Rold,
+                                                int flexible, double* partial) {
   __shared__ double sh[32 * 32];
   const int l = threadIdx.x & 31;
   double s0 = 0.0, s1 = 0.0;
-  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  const int64_t rows_per_block = (n + nvb - 1) / nvb;
+  const int64_t r0 = vb * rows_per_block, r1 = min(n, r0 + rows_per_block);
   for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
     if (l < m) {
       const double z = Z[i * m + l], r = R[i * m + l];
@@ -366,20 +423,30 @@ __global__ void __launch_bounds__(kRedThreads) bat_dot_rz(int64_t n, int m, cons
       if (flexible) s1 += z * (r - Rold[i * m + l]);
     }
   }
-  column_block_sum(s0, m, sh, partial + (int64_t)blockIdx.x * 32);
-  column_block_sum(s1, m, sh, partial + (int64_t)(gridDim.x + blockIdx.x) * 32);
+  column_block_sum(s0, m, sh, partial + vb * 32);
+  column_block_sum(s1, m, sh, partial + (nvb + vb) * 32);
+}
+__global__ void __launch_bounds__(kRedThreads) bat_dot_rz(int64_t n, int m, const double* __restrict__ R,
+                                                          const double* __restrict__ Z,
+                                                          const double* __restrict__ Rold, int flexible,
+                                                          double* partial) {
+  bat_dot_rz_body(blockIdx.x, gridDim.x, n, m, R, Z, Rold, flexible, partial);
 }
 
-__global__ void __launch_bounds__(kRedThreads) bat_dot(int64_t n, int m, const double* __restrict__ P,
-                                                       const double* __restrict__ Q, double* partial) {
+__device__ __forceinline__ void bat_dot_body(int64_t vb, int64_t nvb, int64_t n, int m, const double* __restrict__ P,
+                                             const double* __restrict__ Q, double* partial) {
   __shared__ double sh[32 * 32];
   const int l = threadIdx.x & 31;
   double s = 0.0;
-  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  const int64_t rows_per_block = (n + nvb - 1) / nvb;
+  const int64_t r0 = vb * rows_per_block, r1 = min(n, r0 + rows_per_block);
   for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5)
     if (l < m) s += P[i * m + l] * Q[i * m + l];
-  column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
+  column_block_sum(s, m, sh, partial + vb * 32);
+}
+__global__ void __launch_bounds__(kRedThreads) bat_dot(int64_t n, int m, const double* __restrict__ P,
+                                                       const double* __restrict__ Q, double* partial) {
+  bat_dot_body(blockIdx.x, gridDim.x, n, m, P, Q, partial);
 }
 
 // Column sums of the block partials, by all kFinishThreads threads of the block: warp w sums the
@@ -399,7 +466,7 @@ __device__ double column_total(const double* partial, int blocks, double (*sh)[3
   return t;
 }
 
-__global__ void __launch_bounds__(kFinishThreads) bat_finish_bb(BatchScalars* sc, const double* partial, int blocks,
+__device__ __forceinline__ void bat_finish_bb_body(BatchScalars* sc, const double* partial, int blocks,
                                                                  int m) {
   __shared__ double sh[32][33];
   const int j = threadIdx.x;
@@ -410,8 +477,9 @@ __global__ void __launch_bounds__(kFinishThreads) bat_finish_bb(BatchScalars* sc
   sc->status[j] = 0;
   sc->active[j] = v > 0.0 ? 1 : 0;
 }
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_bb(BatchScalars* sc, const double* partial, int blocks, int m) { bat_finish_bb_body(sc, partial, blocks, m); }
 
-__global__ void __launch_bounds__(kFinishThreads) bat_finish_rz(BatchScalars* sc, const double* partial, int blocks,
+__device__ __forceinline__ void bat_finish_rz_body(BatchScalars* sc, const double* partial, int blocks,
                                                                  int m, int first, int flexible) {
   __shared__ double sh[32][33];
   const int j = threadIdx.x;
@@ -426,8 +494,9 @@ __global__ void __launch_bounds__(kFinishThreads) bat_finish_rz(BatchScalars* sc
   sc->beta[j] = first ? 0.0 : (flexible ? zd : rz) / sc->rho[j];
   sc->rho[j] = rz;
 }
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_rz(BatchScalars* sc, const double* partial, int blocks, int m, int first, int flexible) { bat_finish_rz_body(sc, partial, blocks, m, first, flexible); }
 
-__global__ void __launch_bounds__(kFinishThreads) bat_finish_pq(BatchScalars* sc, const double* partial, int blocks,
+__device__ __forceinline__ void bat_finish_pq_body(BatchScalars* sc, const double* partial, int blocks,
                                                                  int m) {
   __shared__ double sh[32][33];
   const int j = threadIdx.x;
@@ -441,9 +510,10 @@ __global__ void __launch_bounds__(kFinishThreads) bat_finish_pq(BatchScalars* sc
   if (!(pq > 0.0) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
   sc->alpha[j] = sc->rho[j] / pq;
 }
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_pq(BatchScalars* sc, const double* partial, int blocks, int m) { bat_finish_pq_body(sc, partial, blocks, m); }
 
 // after the update: record ||r_j||^2 and retire columns that reached the tolerance
-__global__ void __launch_bounds__(kFinishThreads) bat_finish_rr(BatchScalars* sc, const double* partial, int blocks,
+__device__ __forceinline__ void bat_finish_rr_body(BatchScalars* sc, const double* partial, int blocks,
                                                                  int m) {
   __shared__ double sh[32][33];
   const int j = threadIdx.x;
@@ -454,6 +524,7 @@ __global__ void __launch_bounds__(kFinishThreads) bat_finish_rr(BatchScalars* sc
   if (!(rr == rr) && sc->status[j] == 0) sc->status[j] = GIAMG_ERR_BREAKDOWN;
   if (sc->status[j] != 0 || (!sc->force && rr <= sc->tol2 * sc->bb[j])) sc->active[j] = 0;
 }
+__global__ void __launch_bounds__(kFinishThreads) bat_finish_rr(BatchScalars* sc, const double* partial, int blocks, int m) { bat_finish_rr_body(sc, partial, blocks, m); }
 
 // The loop captured as a CUDA graph: per-column iteration counts (a column counts the iterations
 // it entered active), and the loop condition (some column active, the limit not reached, no
@@ -489,27 +560,31 @@ __global__ void bat_graph_check(const BatchScalars* __restrict__ sc, int m, Batc
   cudaGraphSetConditional(more, cont);
 }
 
-__global__ void bat_update_p(int64_t n, int m, const double* __restrict__ Z, double* __restrict__ P,
-                             const BatchScalars* __restrict__ sc, int first) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * m; i += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void bat_update_p_body(int64_t vb, int64_t nvb, int64_t n, int m, const double* __restrict__ Z,
+                                                  double* __restrict__ P, const BatchScalars* __restrict__ sc,
+                                                  int first) {
+  for (int64_t i = vb * blockDim.x + threadIdx.x; i < n * m; i += nvb * blockDim.x) {
     const int j = (int)(i % m);
     if (!sc->active[j]) continue;
     P[i] = first ? Z[i] : Z[i] + sc->beta[j] * P[i];
   }
 }
+__global__ void bat_update_p(int64_t n, int m, const double* __restrict__ Z, double* __restrict__ P,
+                             const BatchScalars* __restrict__ sc, int first) {
+  bat_update_p_body(blockIdx.x, gridDim.x, n, m, Z, P, sc, first);
+}
 
-__global__ void __launch_bounds__(kRedThreads) bat_update_xr(int64_t n, int m, const double* __restrict__ P,
-                                                             const double* __restrict__ Q, double* __restrict__ X,
-                                                             double* __restrict__ R, double* __restrict__ Rold,
-                                                             int flexible, const BatchScalars* __restrict__ sc,
-                                                             double* partial) {
+__device__ __forceinline__ void bat_update_xr_body(int64_t vb, int64_t nvb, int64_t n, int m, const double* __restrict__ P,
+                                                   const double* __restrict__ Q, double* __restrict__ X,
+                                                   double* __restrict__ R, double* __restrict__ Rold, int flexible,
+                                                   const BatchScalars* __restrict__ sc, double* partial) {
   __shared__ double sh[32 * 32];
   const int l = threadIdx.x & 31;
   const bool act = l < m && sc->active[l];
   const double alpha = act ? sc->alpha[l] : 0.0;
   double s = 0.0;
-  const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+  const int64_t rows_per_block = (n + nvb - 1) / nvb;
+  const int64_t r0 = vb * rows_per_block, r1 = min(n, r0 + rows_per_block);
   for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
     if (act) {
       const int64_t o = i * m + l;
@@ -521,16 +596,128 @@ __global__ void __launch_bounds__(kRedThreads) bat_update_xr(int64_t n, int m, c
       s += rn * rn;
     }
   }
-  column_block_sum(s, m, sh, partial + (int64_t)blockIdx.x * 32);
+  column_block_sum(s, m, sh, partial + vb * 32);
+}
+__global__ void __launch_bounds__(kRedThreads) bat_update_xr(int64_t n, int m, const double* __restrict__ P,
+                                                             const double* __restrict__ Q, double* __restrict__ X,
+                                                             double* __restrict__ R, double* __restrict__ Rold,
+                                                             int flexible, const BatchScalars* __restrict__ sc,
+                                                             double* partial) {
+  bat_update_xr_body(blockIdx.x, gridDim.x, n, m, P, Q, X, R, Rold, flexible, sc, partial);
 }
 
 template <typename T, typename U>
+__device__ __forceinline__ void bat_convert_body(int64_t vb, int64_t nvb, int64_t count, const T* __restrict__ x,
+                                                 U* __restrict__ y) {
+  for (int64_t i = vb * blockDim.x + threadIdx.x; i < count; i += nvb * blockDim.x) y[i] = (U)x[i];
+}
+template <typename T, typename U>
 __global__ void bat_convert(int64_t count, const T* __restrict__ x, U* __restrict__ y) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (U)x[i];
+  bat_convert_body<T, U>(blockIdx.x, gridDim.x, count, x, y);
 }
 
 constexpr int kBatBlocks = 1024;
+
+// ------------------------------------------------------------------ grouped kernels
+// Several hierarchies' work of one phase in one launch: block b belongs to hierarchy i with
+// start[i] <= b < start[i + 1] and runs that hierarchy's body with block index b - start[i] in a
+// grid of start[i + 1] - start[i] blocks -- the grid its standalone launch would have -- so every
+// hierarchy computes exactly what it computes alone.  The descriptors travel as kernel arguments.
+template <class Args>
+struct GroupLaunch {
+  int count;
+  int start[kGroupMax + 1];
+  Args a[kGroupMax];
+};
+__device__ __forceinline__ int group_of_block(const int* start, int count, int b) {
+  int i = 0;
+  while (i + 1 < count && b >= start[i + 1]) ++i;
+  return i;
+}
+
+template <typename V, int MODE>
+__global__ void __launch_bounds__(kThreads) grp_rows_kernel(const GroupLaunch<GrpRowsArgs> P) {
+  const int i = group_of_block(P.start, P.count, blockIdx.x);
+  const GrpRowsArgs& a = P.a[i];
+  const int64_t vb = (int64_t)blockIdx.x - P.start[i];
+  const V* val = (const V*)a.val;
+  const V* X = (const V*)a.X;
+  const V* B = (const V*)a.B;
+  V* Y = (V*)a.Y;
+  V* D = (V*)a.D;
+  const V* dinv = (const V*)a.dinv;
+  const V c1 = (V)a.c1, c2 = (V)a.c2;
+  if constexpr (sizeof(V) == 4) {
+    if (a.pairs) {
+      bat_pairs_body<MODE>(vb, a.n_items, a.ia, a.ib, a.ig, a.gptr, a.gcol, a.rp, a.m, val, X, B, Y, D, dinv, c1, c2);
+      return;
+    }
+  }
+#define GRP_ROWS_CASE(GG)                                                                                        \
+  case GG:                                                                                                       \
+    if (a.pat) bat_rows_body<GG, V, MODE, true>(vb, a.n, a.m, a.rp, a.ci, a.obase, a.toff, val, X, B, Y, D, dinv, c1, c2); \
+    else bat_rows_body<GG, V, MODE, false>(vb, a.n, a.m, a.rp, a.ci, a.obase, a.toff, val, X, B, Y, D, dinv, c1, c2); \
+    break;
+  switch (a.G) {
+    GRP_ROWS_CASE(1)
+    GRP_ROWS_CASE(2)
+    GRP_ROWS_CASE(4)
+    GRP_ROWS_CASE(8)
+    GRP_ROWS_CASE(16)
+    GRP_ROWS_CASE(32)
+  }
+#undef GRP_ROWS_CASE
+}
+
+template <typename V>
+__global__ void grp_restrict_kernel(const GroupLaunch<GrpTransferArgs> P) {
+  const int i = group_of_block(P.start, P.count, blockIdx.x);
+  const GrpTransferArgs& a = P.a[i];
+  bp_restrict_body<V>((int64_t)blockIdx.x - P.start[i], a.p, a.q, a.m, a.l2g, a.own, (const V*)a.p1d,
+                      (const V*)a.in, (V*)a.part);
+}
+template <typename V>
+__global__ void grp_gather_kernel(const GroupLaunch<GrpTransferArgs> P) {
+  const int i = group_of_block(P.start, P.count, blockIdx.x);
+  const GrpTransferArgs& a = P.a[i];
+  bp_gather_body<V>((int64_t)blockIdx.x - P.start[i], a.n_next, a.m, a.cptr, a.cinc, (const V*)a.part, (V*)a.out);
+}
+template <typename V>
+__global__ void grp_prolong_kernel(const GroupLaunch<GrpTransferArgs> P) {
+  const int i = group_of_block(P.start, P.count, blockIdx.x);
+  const GrpTransferArgs& a = P.a[i];
+  bp_prolong_body<V>((int64_t)blockIdx.x - P.start[i], a.p, a.q, a.m, a.l2g, a.own, a.l2g_c, (const V*)a.p1d,
+                     (const V*)a.in, (V*)a.out);
+}
+
+// vector phases: op selects the body; a, b, c, d, e the operands in the order of the standalone call
+enum GrpVecOp { kGvInverse32 = 0, kGvChebFirst32, kGvTo32, kGvTo64, kGvInit, kGvDotRz, kGvDot, kGvUpdateXr, kGvUpdateP,
+                kGvFinishBb, kGvFinishRz, kGvFinishPq, kGvFinishRr };
+template <int OP>
+__global__ void __launch_bounds__(kFinishThreads) grp_vec_kernel(const GroupLaunch<GrpVecArgs> P) {
+  const int i = group_of_block(P.start, P.count, blockIdx.x);
+  const GrpVecArgs& a = P.a[i];
+  const int64_t vb = (int64_t)blockIdx.x - P.start[i], nvb = (int64_t)P.start[i + 1] - P.start[i];
+  BatchScalars* sc = (BatchScalars*)a.sc;
+  if (OP == kGvInverse32) bat_inverse_body<float>(vb, (const double*)a.a, a.n, a.m, (const float*)a.b, (float*)a.c);
+  if (OP == kGvChebFirst32)
+    bat_cheb_first_body<float>(vb, nvb, a.n, a.m, (const float*)a.a, (const float*)a.b, (float)a.v, (float*)a.c,
+                               (float*)a.d);
+  if (OP == kGvTo32) bat_convert_body<double, float>(vb, nvb, a.n, (const double*)a.a, (float*)a.c);
+  if (OP == kGvTo64) bat_convert_body<float, double>(vb, nvb, a.n, (const float*)a.a, (double*)a.c);
+  if (OP == kGvInit) bat_init_body(vb, nvb, a.n, a.m, (const double*)a.a, (double*)a.c, (double*)a.d, a.partial);
+  if (OP == kGvDotRz)
+    bat_dot_rz_body(vb, nvb, a.n, a.m, (const double*)a.a, (const double*)a.b, (const double*)a.e, a.flag1, a.partial);
+  if (OP == kGvDot) bat_dot_body(vb, nvb, a.n, a.m, (const double*)a.a, (const double*)a.b, a.partial);
+  if (OP == kGvUpdateXr)
+    bat_update_xr_body(vb, nvb, a.n, a.m, (const double*)a.a, (const double*)a.b, (double*)a.c, (double*)a.d,
+                       (double*)a.e, a.flag1, sc, a.partial);
+  if (OP == kGvUpdateP) bat_update_p_body(vb, nvb, a.n, a.m, (const double*)a.a, (double*)a.c, sc, a.flag1);
+  if (OP == kGvFinishBb) bat_finish_bb_body(sc, a.partial, kBatBlocks, a.m);
+  if (OP == kGvFinishRz) bat_finish_rz_body(sc, a.partial, kBatBlocks, a.m, a.flag1, a.flag2);
+  if (OP == kGvFinishPq) bat_finish_pq_body(sc, a.partial, kBatBlocks, a.m);
+  if (OP == kGvFinishRr) bat_finish_rr_body(sc, a.partial, kBatBlocks, a.m);
+}
 
 }  // namespace
 
@@ -639,6 +826,148 @@ void bat_pcg_update_xr(int64_t n, int m, const double* P, const double* Q, doubl
   { bat_finish_rr<<<1, kFinishThreads, 0, s>>>((BatchScalars*)sc, partial, kBatBlocks, m); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
 }
+// ------------------------------------------------------------------ grouped launches
+namespace {
+template <class Args, class Kernel>
+void launch_grouped(const std::vector<Args>& ops, const std::vector<int64_t>& blocks, Kernel k, int threads,
+                    size_t smem, cudaStream_t s) {
+  for (size_t c0 = 0; c0 < ops.size(); c0 += kGroupMax) {
+    const size_t c1 = std::min(ops.size(), c0 + kGroupMax);
+    GroupLaunch<Args> P{};
+    P.count = (int)(c1 - c0);
+    int64_t tot = 0;
+    for (size_t i = c0; i < c1; ++i) {
+      P.start[i - c0] = (int)tot;
+      P.a[i - c0] = ops[i];
+      tot += blocks[i];
+    }
+    P.start[c1 - c0] = (int)tot;
+    GIAMG_CHECK(tot < INT32_MAX, GIAMG_ERR_ARG, "grouped launch: too many blocks");
+    if (tot > 0) {
+      k<<<(unsigned)tot, threads, smem, s>>>(P);
+      note_launch();
+    }
+  }
+  GIAMG_CUDA(cudaGetLastError());
+}
+}  // namespace
+
+GrpRowsArgs grp_rows_args(const DCSR& A, int m, const void* val, const void* X, const void* B, void* Y, void* D,
+                          const void* dinv, double c1, double c2, bool fp32) {
+  GrpRowsArgs a{};
+  const bool own = fp32 ? val == (const void*)A.v32.get() : val == (const void*)A.v.get();
+  a.n = A.n;
+  a.m = m;
+  a.pat = own && A.pat.on;
+  a.pairs = fp32 && a.pat && A.grp.pon && (A.batch_rows == 2 || (A.batch_rows == 0 && m > 16));
+  a.G = m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32;
+  a.rp = A.rp.get();
+  a.ci = A.ci.get();
+  a.obase = A.pat.obase.get();
+  a.toff = A.pat.toff.get();
+  a.n_items = A.grp.n_items;
+  a.ia = A.grp.item_a.get();
+  a.ib = A.grp.item_b.get();
+  a.ig = A.grp.item_g.get();
+  a.gptr = A.grp.gptr.get();
+  a.gcol = A.grp.gcol.get();
+  a.val = val;
+  a.X = X;
+  a.B = B;
+  a.Y = Y;
+  a.D = D;
+  a.dinv = dinv;
+  a.c1 = c1;
+  a.c2 = c2;
+  return a;
+}
+
+template <typename V>
+static void grp_rows_t(int mode, const std::vector<GrpRowsArgs>& ops, cudaStream_t s) {
+  std::vector<GrpRowsArgs> act;
+  std::vector<int64_t> blocks;
+  for (const GrpRowsArgs& a : ops) {
+    if (a.n == 0) continue;
+    act.push_back(a);
+    blocks.push_back(a.pairs ? grid_for(a.n_items * 32, kThreads) : grid_for(a.n * a.G, kThreads));
+  }
+  switch (mode) {
+    case kSpmm: launch_grouped(act, blocks, grp_rows_kernel<V, kSpmm>, kThreads, 0, s); break;
+    case kResid: launch_grouped(act, blocks, grp_rows_kernel<V, kResid>, kThreads, 0, s); break;
+    case kBatCheb: launch_grouped(act, blocks, grp_rows_kernel<V, kBatCheb>, kThreads, 0, s); break;
+    default: launch_grouped(act, blocks, grp_rows_kernel<V, kAdd>, kThreads, 0, s); break;
+  }
+}
+void grp_rows64(int mode, const std::vector<GrpRowsArgs>& ops, cudaStream_t s) { grp_rows_t<double>(mode, ops, s); }
+void grp_rows32(int mode, const std::vector<GrpRowsArgs>& ops, cudaStream_t s) { grp_rows_t<float>(mode, ops, s); }
+
+GrpTransferArgs grp_transfer_args(const Level& L, int m, const float* in, float* out, float* part) {
+  GrpTransferArgs a{};
+  a.p = L.p;
+  a.q = L.q;
+  a.m = m;
+  a.n_elem = L.n_elem;
+  a.n_next = L.n_next;
+  a.l2g = L.l2g.get();
+  a.own = L.own.get();
+  a.l2g_c = L.l2g_c.get();
+  a.p1d = L.p1d32.get();
+  a.cptr = L.cinc_ptr.get();
+  a.cinc = L.cinc.get();
+  a.in = in;
+  a.out = out;
+  a.part = part;
+  return a;
+}
+void grp_p_restrict32(const std::vector<GrpTransferArgs>& ops, cudaStream_t s) {
+  std::vector<int64_t> eb, gb;
+  size_t sm = 0;
+  for (const GrpTransferArgs& a : ops) {
+    eb.push_back(a.n_elem);
+    gb.push_back(grid_for(a.n_next * a.m, 256));
+    sm = std::max(sm, brestrict_smem<float>(a.p, a.q, a.m));
+  }
+  GIAMG_CHECK(sm <= 200 * 1024, GIAMG_ERR_ARG, "grouped restriction: too many columns for the element order");
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(grp_restrict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); });
+  launch_grouped(ops, eb, grp_restrict_kernel<float>, 256, sm, s);
+  launch_grouped(ops, gb, grp_gather_kernel<float>, 256, 0, s);
+}
+void grp_p_prolong32(const std::vector<GrpTransferArgs>& ops, cudaStream_t s) {
+  std::vector<int64_t> eb;
+  size_t sm = 0;
+  for (const GrpTransferArgs& a : ops) {
+    eb.push_back(a.n_elem);
+    sm = std::max(sm, bprolong_smem<float>(a.p, a.q, a.m));
+  }
+  GIAMG_CHECK(sm <= 200 * 1024, GIAMG_ERR_ARG, "grouped prolongation: too many columns for the element order");
+  static PerDevice attr;
+  attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(grp_prolong_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); });
+  launch_grouped(ops, eb, grp_prolong_kernel<float>, 256, sm, s);
+}
+
+void grp_vec(int op, const std::vector<GrpVecArgs>& ops, cudaStream_t s) {
+  std::vector<int64_t> blocks;
+  int threads = 256;
+  for (const GrpVecArgs& a : ops) {
+    switch (op) {
+      case kGvInverse32: blocks.push_back(grid_for(a.n * a.m, 256)); break;
+      case kGvChebFirst32: case kGvUpdateP: blocks.push_back(vec_grid(a.n * a.m)); break;
+      case kGvTo32: case kGvTo64: blocks.push_back(vec_grid(a.n)); break;
+      case kGvInit: case kGvDotRz: case kGvDot: case kGvUpdateXr: blocks.push_back(kBatBlocks); break;
+      default: blocks.push_back(1); threads = kFinishThreads; break;
+    }
+  }
+  if (op == kGvInit || op == kGvDotRz || op == kGvDot || op == kGvUpdateXr) threads = kRedThreads;
+  switch (op) {
+#define GV(OP) case OP: launch_grouped(ops, blocks, grp_vec_kernel<OP>, threads, 0, s); break;
+    GV(kGvInverse32) GV(kGvChebFirst32) GV(kGvTo32) GV(kGvTo64) GV(kGvInit) GV(kGvDotRz) GV(kGvDot) GV(kGvUpdateXr)
+    GV(kGvUpdateP) GV(kGvFinishBb) GV(kGvFinishRz) GV(kGvFinishPq) GV(kGvFinishRr)
+#undef GV
+    default: GIAMG_CHECK(false, GIAMG_ERR_ARG, "grouped vector phase out of range");
+  }
+}
+
 void bat_graph_start_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle first,
                             cudaGraphConditionalHandle loop, cudaStream_t s) {
   { bat_graph_start<<<1, 1, 0, s>>>((const BatchScalars*)sc, m, st, first, loop); note_launch(); }

@@ -1125,6 +1125,262 @@ int solve_batch_impl(Ctx& C, int precision, int force_iters, int m, const double
   return GIAMG_OK;
 }
 
+// ------------------------------------------------------------------ grouped solves
+// The multi-right-hand-side solves of several hierarchies at once (FP32 V-cycle in FP64 flexible
+// CG): every phase of an iteration is one launch for all hierarchies that take part in it, and
+// each hierarchy runs exactly the kernel sequence of its own solve_batch_impl host loop, with the
+// same per-block arithmetic (the grouped kernels give each hierarchy its standalone grid), so its
+// results are bit for bit those of giamg_solve_batch.  The V-cycle is aligned by level index:
+// hierarchies with fewer levels reach their coarsest solve earlier and wait for the ascent.
+struct GroupMember {
+  Ctx* C;
+  int m;
+  const double* B;
+  double* X;
+  int it = 0;
+  bool running = false, breakdown = false;
+  std::vector<int> its;
+  std::vector<float*> x, x2;  // per level: the V-cycle iterate and its spare
+};
+
+GrpVecArgs gv(int64_t n, int m, const void* a = nullptr, const void* b = nullptr, void* c = nullptr, void* d = nullptr,
+              const void* e = nullptr, double v = 0.0, void* sc = nullptr, double* partial = nullptr, int f1 = 0,
+              int f2 = 0) {
+  GrpVecArgs g{};
+  g.n = n;
+  g.m = m;
+  g.a = a;
+  g.b = b;
+  g.c = c;
+  g.d = d;
+  g.e = e;
+  g.v = v;
+  g.sc = sc;
+  g.partial = partial;
+  g.flag1 = f1;
+  g.flag2 = f2;
+  return g;
+}
+
+void group_vcycle32(std::vector<GroupMember*>& ms, cudaStream_t s) {
+  std::vector<GrpVecArgs> va;
+  int maxL = 0, maxk = 0;
+  for (GroupMember* g : ms) {
+    Hierarchy& H = *g->C->H;
+    va.push_back(gv(H.lev[0]->A.n * g->m, g->m, H.bR.get(), nullptr, H.lev[0]->bb32.get()));
+    maxL = std::max(maxL, (int)H.lev.size());
+    for (size_t l = 0; l < H.lev.size(); ++l)
+      if (H.lev[l]->kind != GIAMG_LEVEL_COARSEST) maxk = std::max(maxk, (int)g->C->ex[l].cheb.c1.size());
+    g->x.assign(H.lev.size(), nullptr);
+    g->x2.assign(H.lev.size(), nullptr);
+  }
+  grp_vec(kGvTo32H, va, s);
+  auto smoothing = [&](int l, int j0, std::vector<GroupMember*>& S) {
+    for (int j = j0; j < maxk; ++j) {
+      std::vector<GrpRowsArgs> ra;
+      std::vector<GroupMember*> took;
+      for (GroupMember* g : S) {
+        const Cheb& c = g->C->ex[l].cheb;
+        if (j >= (int)c.c1.size()) continue;
+        Level& L = *g->C->H->lev[l];
+        ra.push_back(grp_rows_args(L.A, g->m, L.A.v32.get(), g->x[l], L.bb32.get(), g->x2[l], L.bd32.get(),
+                                   L.dinv32.get(), (float)c.c1[j], (float)c.c2[j], true));
+        took.push_back(g);
+      }
+      if (ra.empty()) continue;
+      grp_rows32(2, ra, s);
+      for (GroupMember* g : took) std::swap(g->x[l], g->x2[l]);
+    }
+  };
+  // descent: presmoothing, residual, restriction; coarsest solves where a hierarchy ends
+  for (int l = 0; l < maxL; ++l) {
+    std::vector<GroupMember*> S;
+    std::vector<GrpVecArgs> inv, first;
+    for (GroupMember* g : ms) {
+      Hierarchy& H = *g->C->H;
+      if (l >= (int)H.lev.size()) continue;
+      Level& L = *H.lev[l];
+      if (L.kind == GIAMG_LEVEL_COARSEST) {
+        inv.push_back(gv(L.nc, g->m, L.Ainv.get(), L.bb32.get(), L.bx32.get()));
+        g->x[l] = L.bx32.get();
+        continue;
+      }
+      g->x[l] = L.bx32.get();
+      g->x2[l] = L.bx232.get();
+      first.push_back(gv(L.A.n, g->m, L.bb32.get(), L.dinv32.get(), g->x[l], L.bd32.get(), nullptr,
+                         (double)(float)g->C->ex[l].cheb.c2[0]));
+      S.push_back(g);
+    }
+    if (!inv.empty()) grp_vec(kGvInverse32H, inv, s);
+    if (S.empty()) continue;
+    grp_vec(kGvChebFirst32H, first, s);
+    smoothing(l, 1, S);
+    std::vector<GrpRowsArgs> res, hres;
+    std::vector<GrpTransferArgs> pres;
+    for (GroupMember* g : S) {
+      Hierarchy& H = *g->C->H;
+      Level& L = *H.lev[l];
+      Level& Cn = *H.lev[l + 1];
+      res.push_back(grp_rows_args(L.A, g->m, L.A.v32.get(), g->x[l], L.bb32.get(), L.br32.get(), nullptr, nullptr,
+                                  0.0, 0.0, true));
+      if (L.kind == GIAMG_LEVEL_P) pres.push_back(grp_transfer_args(L, g->m, L.br32.get(), Cn.bb32.get(), L.bpart32.get()));
+      else hres.push_back(grp_rows_args(L.R, g->m, L.R.v32.get(), L.br32.get(), nullptr, Cn.bb32.get(), nullptr,
+                                        nullptr, 0.0, 0.0, true));
+    }
+    grp_rows32(1, res, s);
+    if (!pres.empty()) grp_p_restrict32(pres, s);
+    if (!hres.empty()) grp_rows32(0, hres, s);
+  }
+  // ascent: interpolation and correction, postsmoothing
+  for (int l = maxL - 2; l >= 0; --l) {
+    std::vector<GroupMember*> S;
+    std::vector<GrpRowsArgs> hpro;
+    std::vector<GrpTransferArgs> ppro;
+    for (GroupMember* g : ms) {
+      Hierarchy& H = *g->C->H;
+      if (l >= (int)H.lev.size() - 1) continue;
+      Level& L = *H.lev[l];
+      const float* xc = g->x[l + 1];
+      if (L.kind == GIAMG_LEVEL_P) ppro.push_back(grp_transfer_args(L, g->m, xc, g->x[l], nullptr));
+      else hpro.push_back(grp_rows_args(L.P, g->m, L.P.v32.get(), xc, nullptr, g->x[l], nullptr, nullptr, 0.0, 0.0,
+                                        true));
+      S.push_back(g);
+    }
+    if (S.empty()) continue;
+    if (!ppro.empty()) grp_p_prolong32(ppro, s);
+    if (!hpro.empty()) grp_rows32(3, hpro, s);
+    smoothing(l, 0, S);
+  }
+  va.clear();
+  for (GroupMember* g : ms) {
+    Hierarchy& H = *g->C->H;
+    va.push_back(gv(H.lev[0]->A.n * g->m, g->m, g->x[0], nullptr, H.bZ.get()));
+  }
+  grp_vec(kGvTo64H, va, s);
+}
+
+void group_precondition(std::vector<GroupMember*>& ms, int first, cudaStream_t s) {
+  group_vcycle32(ms, s);
+  std::vector<GrpVecArgs> rz, fin, up;
+  for (GroupMember* g : ms) {
+    Hierarchy& H = *g->C->H;
+    rz.push_back(gv(H.n, g->m, H.bR.get(), H.bZ.get(), nullptr, nullptr, H.bRold.get(), 0.0, nullptr, H.bpartial.get(), 1));
+    fin.push_back(gv(0, g->m, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, H.bsc.get(), H.bpartial.get(), first, 1));
+    up.push_back(gv(H.n, g->m, H.bZ.get(), nullptr, H.bP.get(), nullptr, nullptr, 0.0, H.bsc.get(), nullptr, first));
+  }
+  grp_vec(kGvDotRzH, rz, s);
+  grp_vec(kGvFinishRzH, fin, s);
+  grp_vec(kGvUpdatePH, up, s);
+}
+
+void group_step(std::vector<GroupMember*>& ms, cudaStream_t s) {
+  std::vector<GrpRowsArgs> q;
+  std::vector<GrpVecArgs> dot, fpq, uxr, frr;
+  for (GroupMember* g : ms) {
+    Hierarchy& H = *g->C->H;
+    Level& L0 = *H.lev[0];
+    q.push_back(grp_rows_args(L0.A, g->m, L0.A.v.get(), H.bP.get(), nullptr, H.bQ.get(), nullptr, nullptr, 0.0, 0.0, false));
+    dot.push_back(gv(H.n, g->m, H.bP.get(), H.bQ.get(), nullptr, nullptr, nullptr, 0.0, nullptr, H.bpartial.get()));
+    fpq.push_back(gv(0, g->m, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, H.bsc.get(), H.bpartial.get()));
+    uxr.push_back(gv(H.n, g->m, H.bP.get(), H.bQ.get(), g->X, H.bR.get(), H.bRold.get(), 0.0, H.bsc.get(),
+                     H.bpartial.get(), 1));
+    frr.push_back(gv(0, g->m, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, H.bsc.get(), H.bpartial.get()));
+  }
+  grp_rows64(0, q, s);
+  grp_vec(kGvDotH, dot, s);
+  grp_vec(kGvFinishPqH, fpq, s);
+  grp_vec(kGvUpdateXrH, uxr, s);
+  grp_vec(kGvFinishRrH, frr, s);
+}
+
+void solve_grouped_impl(std::vector<GroupMember>& mem, double rtol, int* iters, double* relres, int* status) {
+  GIAMG_CHECK(!mem.empty(), GIAMG_ERR_ARG, "no hierarchies");
+  GIAMG_CHECK(rtol >= 0.0, GIAMG_ERR_ARG, "rtol must be non-negative");
+  Hierarchy& H0 = *mem[0].C->H;
+  cudaStream_t s = H0.stream;
+  for (size_t i = 0; i < mem.size(); ++i) {
+    Hierarchy& H = *mem[i].C->H;
+    GIAMG_CHECK(mem[i].m >= 1 && mem[i].m <= 32, GIAMG_ERR_ARG, "m must be in [1, 32]");
+    GIAMG_CHECK(mem[i].B && mem[i].X, GIAMG_ERR_ARG, "B and X are required");
+    GIAMG_CHECK(H.opt.device_ptrs != 0, GIAMG_ERR_ARG, "a grouped solve needs device pointers (device_ptrs = 1)");
+    GIAMG_CHECK(H.device == H0.device, GIAMG_ERR_ARG, "the hierarchies of a grouped solve must share one device");
+    for (size_t j = 0; j < i; ++j)
+      GIAMG_CHECK(mem[j].C != mem[i].C, GIAMG_ERR_ARG, "a hierarchy appears twice in a grouped solve");
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));  // its earlier work (and allocations) done
+    alloc_batch(H, mem[i].m);
+    GIAMG_CUDA(cudaStreamSynchronize(H.stream));
+  }
+  std::vector<GrpVecArgs> ini, fbb;
+  for (GroupMember& g : mem) {
+    Hierarchy& H = *g.C->H;
+    BatchScalarsHost* hs = (BatchScalarsHost*)H.h_bsc;
+    hs->tol2 = rtol * rtol;
+    hs->force = 0;
+    GIAMG_CUDA(cudaMemcpyAsync((char*)H.bsc.get() + offsetof(BatchScalarsHost, tol2), &hs->tol2,
+                               sizeof(double) + 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    ini.push_back(gv(H.n, g.m, g.B, nullptr, g.X, H.bR.get(), nullptr, 0.0, nullptr, H.bpartial.get()));
+    fbb.push_back(gv(0, g.m, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, H.bsc.get(), H.bpartial.get()));
+  }
+  grp_vec(kGvInitH, ini, s);
+  grp_vec(kGvFinishBbH, fbb, s);
+  auto read_scalars = [&]() {
+    for (GroupMember& g : mem) {
+      Hierarchy& H = *g.C->H;
+      GIAMG_CUDA(cudaMemcpyAsync(H.h_bsc, H.bsc.get(), sizeof(BatchScalarsHost), cudaMemcpyDeviceToHost, s));
+    }
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+  };
+  read_scalars();
+  std::vector<GroupMember*> run;
+  for (GroupMember& g : mem) {
+    BatchScalarsHost* hs = (BatchScalarsHost*)g.C->H->h_bsc;
+    g.its.assign(g.m, 0);
+    int active = 0;
+    for (int j = 0; j < g.m; ++j) active += hs->active[j];
+    g.running = active > 0 && g.C->H->opt.max_iter > 0;
+    if (g.running) run.push_back(&g);
+  }
+  if (!run.empty()) group_precondition(run, 1, s);
+  while (!run.empty()) {
+    group_step(run, s);
+    std::vector<std::vector<int>> was;
+    for (GroupMember* g : run) {
+      BatchScalarsHost* hs = (BatchScalarsHost*)g->C->H->h_bsc;
+      was.emplace_back(hs->active, hs->active + g->m);
+    }
+    read_scalars();
+    std::vector<GroupMember*> next;
+    for (size_t i = 0; i < run.size(); ++i) {
+      GroupMember* g = run[i];
+      BatchScalarsHost* hs = (BatchScalarsHost*)g->C->H->h_bsc;
+      ++g->it;
+      int active = 0;
+      for (int j = 0; j < g->m; ++j) {
+        if (was[i][j]) g->its[j] = g->it;
+        if (hs->status[j] != 0) g->breakdown = true;
+        active += hs->active[j];
+      }
+      if (!(g->breakdown || active == 0 || g->it == g->C->H->opt.max_iter)) next.push_back(g);
+    }
+    run.swap(next);
+    if (!run.empty()) group_precondition(run, 0, s);
+  }
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  int64_t k = 0;
+  for (size_t i = 0; i < mem.size(); ++i) {
+    GroupMember& g = mem[i];
+    BatchScalarsHost* hs = (BatchScalarsHost*)g.C->H->h_bsc;
+    bool unconverged = false;
+    for (int j = 0; j < g.m; ++j, ++k) {
+      const double rr = hs->bb[j] > 0.0 ? std::sqrt(hs->rr[j] / hs->bb[j]) : 0.0;
+      if (iters) iters[k] = g.its[j];
+      if (relres) relres[k] = rr;
+      if (!(rr <= rtol)) unconverged = true;
+    }
+    if (status) status[i] = g.breakdown ? GIAMG_ERR_BREAKDOWN : unconverged ? GIAMG_ERR_MAXITER : GIAMG_OK;
+  }
+}
+
 // The solve enqueued on the handle's stream with no host synchronisation: the captured graph
 // (captured here on first use, which synchronises once), parameters passed as kernel arguments,
 // results written to device memory by a kernel after the graph.  b, x and the results are
@@ -1491,6 +1747,22 @@ int giamg_set_cheb_degree(giamg_handle h, int degree) {
         C.ex[l].cheb = cheb_coeffs(H.lev[l]->rho, H.opt.cheb_lo, H.opt.cheb_hi, degree);
     // the captured solve graphs hold the old coefficients as kernel arguments
     drop_solve_graphs(H);
+    return GIAMG_OK;
+  });
+}
+
+int giamg_solve_grouped(int count, const giamg_handle* handles, const int* m, const double* const* B,
+                        double* const* X, double rtol, int* iters, double* relres, int* status) {
+  return guarded([&] {
+    GIAMG_CHECK(count >= 1 && handles && m && B && X, GIAMG_ERR_ARG, "count >= 1 and handles, m, B, X are required");
+    std::vector<GroupMember> mem((size_t)count);
+    for (int i = 0; i < count; ++i) {
+      mem[i].C = ctx_of(handles[i]);
+      mem[i].m = m[i];
+      mem[i].B = B[i];
+      mem[i].X = X[i];
+    }
+    solve_grouped_impl(mem, rtol, iters, relres, status);
     return GIAMG_OK;
   });
 }

@@ -427,6 +427,53 @@ void bat_graph_start_launch(const void* sc, int m, BatchGraphState* st, cudaGrap
                             cudaGraphConditionalHandle loop, cudaStream_t s);
 void bat_graph_check_launch(const void* sc, int m, BatchGraphState* st, cudaGraphConditionalHandle loop,
                             cudaGraphConditionalHandle more, cudaStream_t s);
+// grouped multi-right-hand-side phases: several hierarchies' work of one phase in one launch,
+// each hierarchy computing exactly what its standalone launch computes (batch_kernels.cu)
+constexpr int kGroupMax = 16;  // hierarchies per launch (more are split into several launches)
+struct GrpRowsArgs {           // a multi-RHS row kernel on one matrix (bat_rows / bat_pairs)
+  int64_t n, n_items;
+  int m, G, pat, pairs;
+  const int64_t* rp;
+  const int32_t *ci, *obase, *toff, *ia, *ib, *ig;
+  const int64_t* gptr;
+  const int32_t* gcol;
+  const void *val, *X, *B;
+  void *Y, *D;
+  const void* dinv;
+  double c1, c2;
+};
+struct GrpTransferArgs {       // an FP32 element transfer of one p-level
+  int p, q, m;
+  int32_t n_elem;
+  int64_t n_next;
+  const int32_t *l2g, *l2g_c, *cinc;
+  const uint8_t* own;
+  const float* p1d;
+  const int64_t* cptr;
+  const float* in;
+  float *out, *part;
+};
+struct GrpVecArgs {            // a vector phase (GrpVecOp in batch_kernels.cu)
+  int64_t n;
+  int m, flag1, flag2;
+  const void *a, *b, *e;
+  void *c, *d;
+  double v;
+  void* sc;
+  double* partial;
+};
+enum GrpVecOpHost { kGvInverse32H = 0, kGvChebFirst32H, kGvTo32H, kGvTo64H, kGvInitH, kGvDotRzH, kGvDotH,
+                    kGvUpdateXrH, kGvUpdatePH, kGvFinishBbH, kGvFinishRzH, kGvFinishPqH, kGvFinishRrH };
+// mode: 0 SpMM, 1 residual, 2 Chebyshev step, 3 add (as bat_rows_launch64/32); fp32: val is A.v32
+GrpRowsArgs grp_rows_args(const DCSR& A, int m, const void* val, const void* X, const void* B, void* Y, void* D,
+                          const void* dinv, double c1, double c2, bool fp32);
+void grp_rows64(int mode, const std::vector<GrpRowsArgs>& ops, cudaStream_t s);
+void grp_rows32(int mode, const std::vector<GrpRowsArgs>& ops, cudaStream_t s);
+GrpTransferArgs grp_transfer_args(const Level& L, int m, const float* in, float* out, float* part);
+void grp_p_restrict32(const std::vector<GrpTransferArgs>& ops, cudaStream_t s);
+void grp_p_prolong32(const std::vector<GrpTransferArgs>& ops, cudaStream_t s);
+void grp_vec(int op, const std::vector<GrpVecArgs>& ops, cudaStream_t s);
+
 // host view of the batched CG scalars (layout shared with batch_kernels.cu)
 struct BatchScalarsHost {
   double rho[32], pq[32], alpha[32], beta[32], rr[32], bb[32];

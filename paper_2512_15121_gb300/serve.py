@@ -11,7 +11,11 @@ The server
   solved together as one multi-right-hand-side solve (giamg_solve_batch, up to 32 columns);
   requests that arrive while a batch runs join the next batch -- continuous batching;
 * overlaps: every cached hierarchy owns a CUDA stream and every worker slot is a host thread,
-  so batches for different operators run concurrently on the device.
+  so batches for different operators run concurrently on the device;
+* groups: a worker that takes a batch also takes the other waiting batches (same precision and
+  tolerance) whose hierarchies are cached and idle, up to max_group, and solves them together
+  with giamg_solve_grouped -- one kernel launch per phase of the V-cycle and the CG iteration
+  for all of them, each with the bits of its own multi-right-hand-side solve.
 
 A column's arithmetic in the batched kernels does not depend on the other columns, so a request
 gets the same bits alone and in a mix (tests/test_gpu_serve.py checks this).  The clock and the
@@ -54,19 +58,20 @@ class Request:
 
 
 def estimate_bytes(n: int, nnz: int, columns: int = 32) -> int:
-    """Device footprint of a hierarchy plus batch work: the finest CSR (FP64 + FP32 values,
-    indices) about doubled for the coarse levels and the compressed forms, and the n x 32 FP64 /
-    FP32 work blocks of the multi-right-hand-side solve."""
+    """Device footprint of a served hierarchy plus batch work: the finest CSR (FP64 + FP32 values,
+    column indices, row pointers) with a third more for the coarse levels, row patterns and
+    groups, and the n x 32 FP64 / FP32 work blocks of the multi-right-hand-side solve."""
     matrix = nnz * (8 + 4 + 4) + 16 * n
     work = n * columns * (12 * 8 + 5 * 4)
-    return int(2.0 * matrix + work)
+    return int(1.35 * matrix + work)
 
 
 class _Entry:
-    def __init__(self, solver, stream, nbytes):
+    def __init__(self, solver, stream, nbytes, nnz=0):
         self.solver = solver
         self.stream = stream
         self.nbytes = nbytes
+        self.nnz = nnz
         self.lock = threading.Lock()
         self.last_used = 0.0
         self.busy = False
@@ -76,7 +81,8 @@ class Server:
     def __init__(self, slots: int = 4, reserve_bytes: int = 2 << 30, max_columns: int = 32,
                  mem_info: Callable | None = None, clock: Callable | None = None,
                  solver_factory: Callable | None = None, runner: Callable | None = None, device: int = 0,
-                 solver_options: dict | None = None):
+                 solver_options: dict | None = None, max_group: int = 8, group_runner: Callable | None = None,
+                 group_max_nnz: int = 20_000_000):
         self.slots = slots
         self.solver_options = dict(solver_options or {})
         self.reserve = reserve_bytes
@@ -91,6 +97,13 @@ class Server:
         self.mem_info = mem_info
         self.solver_factory = solver_factory or self._default_factory
         self.runner = runner or self._default_runner
+        # grouped solves: the library's by default, none with an injected runner unless given one
+        self.group_runner = group_runner or (self._default_group_runner if runner is None else None)
+        self.max_group = max_group if self.group_runner is not None else 1
+        # only operators this small are grouped: their solves are bound by kernel launches, which
+        # a group shares; a large operator's kernels fill the GPU alone, and a grouped call
+        # returns when its slowest member is done, so a large member would hold the small ones
+        self.group_max_nnz = group_max_nnz
         self.cache: dict = {}
         self.pending: dict = collections.OrderedDict()   # key -> deque of requests
         self.done: list = []
@@ -116,6 +129,10 @@ class Server:
         with torch.cuda.device(self.device):
             opts = dict(self.solver_options)
             opts.setdefault("cheb_degree", op.get("cheb_degree", 3))
+            # served solves are multi-right-hand-side solves, whose kernels read the CSR values and
+            # row patterns: the single-right-hand-side row forms' value copies (group-major,
+            # sliced) would take a third of a large hierarchy's memory for nothing
+            opts.setdefault("row_form", 2)
             S = Solver(op["n"], op["row_ptr"], op["col"], op["val"], op["elem_dof"], op["p"],
                        stream=stream.cuda_stream, device_ptrs=0, **opts)
             S.set_device_ptrs(True)
@@ -158,17 +175,19 @@ class Server:
             return e, None
         if req.size is not None:  # materialised by _build, outside the lock
             op = req.make_operator
-            need = estimate_bytes(int(req.size[0]), int(req.size[1]), self.max_columns)
+            nnz = int(req.size[1])
+            need = estimate_bytes(int(req.size[0]), nnz, self.max_columns)
         else:
             op = req.make_operator()
-            need = estimate_bytes(op["n"], len(op["val"]), self.max_columns)
+            nnz = len(op["val"])
+            need = estimate_bytes(op["n"], nnz, self.max_columns)
         if not self._evict_for(need):
             if self._never_fits(need):
                 raise MemoryError(f"the operator needs about {need} bytes of device memory, {self._free_bytes()} "
                                   f"are free with nothing left to evict")
             self.stats["admission_waits"] += 1
             return None, None
-        e = _Entry(None, None, need)
+        e = _Entry(None, None, need, nnz)
         e.busy = True
         self.cache[key] = e
         self._building_bytes += need
@@ -234,8 +253,45 @@ class Server:
             del self.pending[best]
         return best, batch
 
+    def _take(self, pkey):
+        """Under the lock: the requests of pending key pkey for one batch (up to max_columns)."""
+        q = self.pending[pkey]
+        batch, cols = [], 0
+        while q and cols + q[0].columns <= self.max_columns:
+            r = q.popleft()
+            batch.append(r)
+            cols += r.columns
+        if not q:
+            del self.pending[pkey]
+        return batch
+
+    def _claim_group(self, pkey):
+        """Under the lock: further waiting batches to solve with pkey's in one grouped solve -- the
+        same precision and tolerance, hierarchies cached, built and idle (no setup in the group),
+        all of them small (group_max_nnz) -- oldest first, up to max_group - 1; each is marked busy
+        and given its batch id."""
+        extra = []
+        first = self.cache.get(pkey[0])
+        if self.max_group <= 1 or pkey[1] != 1 or first is None or first.nnz > self.group_max_nnz:
+            return extra
+        for k in sorted((k for k, q in self.pending.items() if q and k != pkey and k[1:] == pkey[1:]),
+                        key=lambda k: self.pending[k][0].arrival):
+            if len(extra) >= self.max_group - 1:
+                break
+            e = self.cache.get(k[0])
+            if e is None or e.busy or e.solver is None or e.nnz > self.group_max_nnz:
+                continue
+            batch = self._take(k)
+            e.busy = True
+            self.stats["cache_hits"] += 1
+            self.batch_seq += 1
+            self._running += 1
+            extra.append((e, batch, self.batch_seq))
+        return extra
+
     def _worker(self):
         while True:
+            extra = []
             with self.cv:
                 while True:
                     if self.closed and not any(self.pending.values()):
@@ -255,19 +311,29 @@ class Server:
                         self.batch_seq += 1
                         self._running += 1
                         bid = self.batch_seq
+                        extra = self._claim_group(key)
                         break
                     self.cv.wait(timeout=0.05)
             err = self._build(key[0], e, op) if op is not None else None
             if err is None:
-                self._run(e, batch, bid)
+                if extra:
+                    self._run_group([(e, batch, bid)] + extra)
+                else:
+                    self._run(e, batch, bid)
             with self.cv:
                 if err is not None:
                     self._fail(batch, err, bid)
-                e.busy = False
-                self._running -= 1
-                e.last_used = self.clock()
+                for ee, _, _ in [(e, batch, bid)] + extra:
+                    ee.busy = False
+                    self._running -= 1
+                    ee.last_used = self.clock()
                 if err is None:
-                    self.done.extend(batch)
+                    for _, bb, _ in [(e, batch, bid)] + extra:
+                        self.done.extend(bb)
+                else:  # the group's other batches were not solved: back to the front of their queues
+                    for _, bb, _ in extra:
+                        q = self.pending.setdefault((bb[0].key, bb[0].precision, bb[0].rtol), collections.deque())
+                        q.extendleft(reversed(bb))
                 self.cv.notify_all()
 
     def _fail(self, batch: list, err: str, bid: int = -1):
@@ -294,6 +360,78 @@ class Server:
             Bd = torch.from_numpy(np.ascontiguousarray(B)).to(f"cuda:{self.device}")
             X, it, rr = e.solver.solve_batch(Bd, rtol=rtol, precision=precision)
             return X[:, :m].cpu().numpy(), it[:m], rr[:m]
+
+    def _default_group_runner(self, items):
+        """One grouped solve (giamg_solve_grouped) of several hierarchies' batches: items are
+        (entry, B, rtol, precision) with one precision and tolerance; each B padded as in
+        _default_runner.  Returns [(X, iters, relres, status)]."""
+        import torch
+        from . import solve_grouped
+        e0 = items[0][0]
+        Bs, ms = [], []
+        with torch.cuda.stream(e0.stream):
+            for e, B, rtol, precision in items:
+                m = B.shape[1]
+                mp = 1 << (m - 1).bit_length()
+                if mp > m:
+                    B = np.concatenate([B, np.zeros((B.shape[0], mp - m))], axis=1)
+                Bs.append(torch.from_numpy(np.ascontiguousarray(B)).to(f"cuda:{self.device}"))
+                ms.append(m)
+            res = solve_grouped([it[0].solver for it in items], Bs, rtol=items[0][2])
+            return [(X[:, :m].cpu().numpy(), it[:m], rr[:m], st) for (X, it, rr, st), m in zip(res, ms)]
+
+    def _run_group(self, members: list):
+        """Solve several hierarchies' batches in one grouped solve; each request gets its columns,
+        iterations and residuals (or its member's error)."""
+        t0 = self.clock()
+        w0 = time.perf_counter()
+        items, kept = [], []
+        for e, batch, bid in members:
+            rows = getattr(e.solver, "n", None)
+            rows = batch[0].rhs.shape[0] if rows is None else rows
+            ok = [r for r in batch if r.rhs.shape[0] == rows]
+            for r in batch:
+                if r.rhs.shape[0] != rows:
+                    r.start, r.finish, r.batch_id = t0, self.clock(), bid
+                    r.error = f"rhs has {r.rhs.shape[0]} rows, the operator {rows}"
+                    with self.cv:
+                        self.stats["failed_requests"] += 1
+            if ok:
+                items.append((e, np.concatenate([r.rhs for r in ok], axis=1), min(r.rtol for r in ok), ok[0].precision))
+                kept.append((ok, bid))
+        if not items:
+            return
+        try:
+            res = self.group_runner(items)
+            err = None
+        except Exception as ex:  # a failed group fails its requests, not the server
+            res, err = None, str(ex)
+        t1 = self.clock()
+        c_total = 0
+        for i, (ok, bid) in enumerate(kept):
+            merr = err
+            if res is not None and res[i][3] not in (0, -8):  # GIAMG_OK, GIAMG_ERR_MAXITER
+                merr = f"grouped solve failed (status {res[i][3]})"
+            c = 0
+            for r in ok:
+                k = r.columns
+                r.start, r.finish, r.batch_id, r.error = t0, t1, bid, merr
+                if merr is None:
+                    Xh, it, rr, _ = res[i]
+                    r.x = Xh[:, c:c + k].copy()
+                    r.iters = np.asarray(it[c:c + k]).copy()
+                    r.relres = np.asarray(rr[c:c + k]).copy()
+                c += k
+            c_total += c
+            if merr is not None:
+                with self.cv:
+                    self.stats["failed_requests"] += len(ok)
+        with self.cv:
+            self.stats["batches"] += len(kept)
+            self.stats["grouped_solves"] += 1
+            self.stats["grouped_batches"] += len(kept)
+            self.stats["columns"] += c_total
+            self.stats["solve_ms"] += (time.perf_counter() - w0) * 1e3
 
     def _run(self, e: _Entry, batch: list, bid: int):
         t0 = self.clock()

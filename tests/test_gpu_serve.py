@@ -1,7 +1,8 @@
 """The solve server on the GPU: every request's result is the same alone and in a mix of
 concurrent requests (bit for bit: a column's arithmetic in the batched kernels does not depend on
-the other columns), every result meets its tolerance (true residual from the oracle's product),
-and the hierarchy cache is used."""
+the other columns, and a grouped solve of several operators gives each the bits of its own
+solve), every result meets its tolerance (true residual from the oracle's product), and the
+hierarchy cache is used."""
 import numpy as np
 import pytest
 
@@ -26,8 +27,13 @@ def test_alone_equals_in_the_mix():
         alone.drain()
         ref[r.rid] = rr
     alone.close()
-    # the mix: everything submitted at once to a three-slot server
+    # the mix: every operator built by one request first, then everything submitted at once to a
+    # three-slot server, whose workers solve the batches of cached operators in groups
     mix = serve.Server(slots=3)
+    for key in sorted({r.key for r in reqs}):
+        first = next(r for r in reqs if r.key == key)
+        mix.submit(serve.Request(rid=-1, key=key, make_operator=first.make_operator, rhs=first.rhs))
+    mix.drain()
     for r in reqs:
         r.arrival = 0.0
         mix.submit(r)
@@ -35,6 +41,7 @@ def test_alone_equals_in_the_mix():
     mix.close()
     batched = sum(1 for r in reqs if sum(q.batch_id == r.batch_id for q in reqs) > 1)
     assert batched > 0  # some requests really shared a batch
+    assert mix.stats["grouped_solves"] > 0  # and some batches of different operators a grouped solve
     for r in reqs:
         a = ref[r.rid]
         assert r.error is None and a.error is None

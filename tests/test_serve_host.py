@@ -278,3 +278,82 @@ def test_shared_operators_combine_stiffness_and_mass():
             assert np.allclose(F[:, j], so.K.rhs_nodal(sd), rtol=0, atol=1e-12 * np.abs(F).max())
     finally:
         so.close()
+
+
+def test_cached_operators_are_solved_in_groups():
+    """A worker that takes a batch also takes the waiting batches of other cached, idle operators
+    with the same precision and tolerance (up to max_group) and solves them in one grouped call;
+    every request still gets its own columns back.  Requests with another tolerance or precision,
+    and operators not yet built, are not pulled into a group."""
+    mem = Memory(1 << 40)
+    groups, singles = [], []
+
+    def factory(op):
+        s = FakeSolver(None)
+        s.n = op["n"]
+        return s, None
+
+    def runner(e, B, rtol, precision):
+        singles.append(B.shape[1])
+        return B * 2.0, np.full(B.shape[1], 3, np.int32), np.full(B.shape[1], 1e-9)
+
+    def group_runner(items):
+        groups.append([(it[1].shape[1], it[2], it[3]) for it in items])
+        assert len({(it[2], it[3]) for it in items}) == 1  # one tolerance and precision per group
+        return [(it[1] * 2.0, np.full(it[1].shape[1], 3, np.int32), np.full(it[1].shape[1], 1e-9), 0) for it in items]
+
+    srv = serve.Server(slots=1, reserve_bytes=0, mem_info=mem.info, solver_factory=factory, runner=runner,
+                       group_runner=group_runner, max_group=3)
+    # build four operators first (one request each), then a burst for all of them
+    warm = [make_request(i, key=("mesh", i, 1.0)) for i in range(4)]
+    for r in warm:
+        srv.submit(r)
+    srv.drain(30)
+    burst = [make_request(10 + i, key=("mesh", i % 4, 1.0), cols=2) for i in range(8)]
+    odd = make_request(99, key=("mesh", 0, 1.0))
+    odd.rtol = 1e-6                                             # another tolerance: its own batch
+    for r in burst + [odd]:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    for r in warm + burst + [odd]:
+        assert r.error is None and np.array_equal(r.x, 2.0 * r.rhs), r.rid
+    assert groups and all(len(g) <= 3 for g in groups)
+    assert all(t[1] == 1e-8 for g in groups for t in g)
+    assert srv.stats["grouped_solves"] == len(groups)
+    assert srv.stats["grouped_batches"] == sum(len(g) for g in groups)
+    assert srv.stats["setups"] == 4
+
+
+def test_large_operators_are_not_grouped():
+    """Operators above group_max_nnz are solved on their own: their kernels fill the GPU, and a
+    grouped call would hold its small members until the large one is done."""
+    mem = Memory(1 << 40)
+    groups = []
+
+    def factory(op):
+        s = FakeSolver(None)
+        s.n = op["n"]
+        return s, None
+
+    def runner(e, B, rtol, precision):
+        return B * 2.0, np.full(B.shape[1], 3, np.int32), np.full(B.shape[1], 1e-9)
+
+    def group_runner(items):
+        groups.append(sorted(it[1].shape[0] for it in items))
+        return [(it[1] * 2.0, np.full(it[1].shape[1], 3, np.int32), np.full(it[1].shape[1], 1e-9), 0) for it in items]
+
+    srv = serve.Server(slots=1, reserve_bytes=0, mem_info=mem.info, solver_factory=factory, runner=runner,
+                       group_runner=group_runner, max_group=4, group_max_nnz=5000)
+    sizes = {0: 100, 1: 100, 2: 100, 3: 800}  # nnz 10 n: the last one is large
+    warm = [make_request(i, key=("mesh", i, 1.0), n=sizes[i]) for i in range(4)]
+    for r in warm:
+        srv.submit(r)
+    srv.drain(30)
+    burst = [make_request(10 + i, key=("mesh", i % 4, 1.0), n=sizes[i % 4]) for i in range(12)]
+    for r in burst:
+        srv.submit(r)
+    srv.drain(30)
+    srv.close()
+    assert all(r.error is None and np.array_equal(r.x, 2.0 * r.rhs) for r in warm + burst)
+    assert groups and all(800 not in g for g in groups)
