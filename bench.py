@@ -553,6 +553,8 @@ def run_ours(args):
         # 32 right-hand sides against single solves in both precisions
         configs["poisson_24cube_jitter_p4"], later["poisson_24cube_jitter_p4"] = measure_batch(g, torch)
         phase("config poisson_24cube_jitter_p4 done")
+        extras["grouped_solve"] = measure_grouped()
+        phase("grouped solve done")
         extras["configs"] = configs
 
     value = max_over_ranks(td, mixed["p50"])
@@ -680,6 +682,54 @@ def measure_serving(n_requests=128, rate=150.0):
     stats.update({"rate_per_s": rate, "operators": len(ops), "errors": sum(r.error is not None for r in reqs),
                   "mix": "jittered 4^3/6^3/8^3, p in {2,4,6}, lambda in {0,1,1000}, 1-8 RHS, FP32 V-cycle"})
     return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()}
+
+
+def measure_grouped(reps=10, warmup=3):
+    """The grouped solve against separate ones: eight small operators of the served stream's
+    kind (jittered 4^3 and 8^3 meshes, p 2 and 4, lambda 1 and 1000), 4 right-hand sides each,
+    FP32 V-cycle: one giamg_solve_grouped call against the eight giamg_solve_batch calls one after
+    the other (CUDA-event medians), and the results compared bit for bit."""
+    import numpy as np
+    import torch
+    import fegen
+    import paper_2512_15121_gb300 as g
+    probs, solvers, Bs = [], [], []
+    for mesh in (4, 8):
+        for p in (2, 4):
+            for lam in (1.0, 1000.0):
+                prob = fegen.make(mesh, p, mesh="jitter", mesh_seed=mesh, lam=lam, rhs="none")
+                S = g.Solver.from_problem(prob, device=True, cheb_degree=3, row_form=2)
+                Bs.append(torch.from_numpy(np.stack([prob.rhs("fourier", 500 + j) for j in range(4)], axis=1)).cuda())
+                probs.append(prob)
+                solvers.append(S)
+
+    def separate():
+        return [S.solve_batch(B, rtol=1e-8, precision=1) for S, B in zip(solvers, Bs)]
+
+    def grouped():
+        return g.solve_grouped(solvers, Bs, rtol=1e-8)
+
+    out = {}
+    for name, fn in (("separate", separate), ("grouped", grouped)):
+        for _ in range(warmup):
+            fn()
+        ts = []
+        launches = g.launch_count()
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[name] = {"p50_ms": round(pct(ts, 0.5), 3), "launches_per_call": (g.launch_count() - launches) // reps}
+        out[name + "_x"] = [r[0] for r in res]
+    same = all(torch.equal(a, b) for a, b in zip(out.pop("separate_x"), out.pop("grouped_x")))
+    for S, pr in zip(solvers, probs):
+        S.close()
+        pr.close()
+    return {"operators": [[pr.n, pr.nnz, pr.p] for pr in probs], "rhs_per_operator": 4, **out,
+            "speedup": round(out["separate"]["p50_ms"] / out["grouped"]["p50_ms"], 2), "bitwise_equal": same}
 
 
 def measure_serving_full(n_requests=512, load=0.8, meshes=(4, 8, 12, 16)):
