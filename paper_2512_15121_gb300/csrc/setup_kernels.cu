@@ -978,61 +978,110 @@ __global__ void __launch_bounds__(kNumWarps * 32) gsym_fill(int64_t G, const int
 }
 
 __global__ void group_row_counts(int64_t G, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow,
-                                 const int32_t* __restrict__ ucnt, int32_t* __restrict__ gid, int32_t* __restrict__ cnt) {
+                                 const int32_t* __restrict__ ucnt, int32_t* __restrict__ cnt) {
   GRID_STRIDE(g, G) {
     for (int64_t t = rptr[g]; t < rptr[g + 1]; ++t) {
-      gid[grow[t]] = (int32_t)g;
       cnt[grow[t]] = ucnt[g];
     }
   }
 }
 
-// numeric: a warp per row; smem per warp: the group's sorted list (umax int32) and the sums (umax doubles)
-__global__ void __launch_bounds__(kNumWarps * 32) gnum_rows(int64_t n, int umax, const int64_t* __restrict__ arp,
-                                                            const int32_t* __restrict__ aci,
-                                                            const double* __restrict__ av,
-                                                            const int64_t* __restrict__ brp,
-                                                            const int32_t* __restrict__ bci,
-                                                            const double* __restrict__ bv,
-                                                            const int32_t* __restrict__ gid,
-                                                            const int64_t* __restrict__ uoff,
-                                                            const int32_t* __restrict__ ulist,
-                                                            const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
-                                                            double* __restrict__ cv) {
+// numeric pass by warp work items: a warp takes `nr` rows of one group with `ns` lanes per row
+// (ns = 32 / nr rounded down, so groups of few rows still fill the warp), the group's sorted
+// output columns and the rows' sums ([position][row]) in shared memory.  For each inner index k of
+// the group (ascending) the lanes find the positions of B's row k in the column list once for all
+// of the warp's rows; the lanes of one row then split that row's entries (distinct positions), so
+// every sum still runs in ascending k with separately rounded products, as in the per-row passes;
+// a warp barrier between two k orders the updates of one sum made by different lanes.  Two entries
+// are applied per step (their positions differ), which halves the dependent shared-memory chain.
+struct GnumItem {
+  int32_t g, r0, nr, ns;  // group, first row (offset in the group's row list), rows, lanes per row
+};
+constexpr int kGnumCap = 4096;  // sums per warp item (doubles): 32 KB of shared memory
+
+__global__ void __launch_bounds__(32) gnum_warp(const GnumItem* __restrict__ items,
+                                                const int64_t* __restrict__ arp, const double* __restrict__ av,
+                                                const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                                                const double* __restrict__ bv, const int64_t* __restrict__ gptr,
+                                                const int32_t* __restrict__ gcol, const int64_t* __restrict__ rptr,
+                                                const int32_t* __restrict__ grow, const int64_t* __restrict__ uoff,
+                                                const int32_t* __restrict__ ulist, const int64_t* __restrict__ crp,
+                                                int32_t* __restrict__ cci, double* __restrict__ cv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)w * umax;
-  int32_t* cols = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem_raw) + (size_t)kNumWarps * umax) +
-                  (size_t)w * umax;
-  const int64_t row = (int64_t)blockIdx.x * kNumWarps + w;
-  if (row >= n) return;
-  const int32_t g = gid[row];
-  const int32_t* __restrict__ ul = ulist + uoff[g];
+  constexpr unsigned kFull = 0xffffffffu;
+  const GnumItem it = items[blockIdx.x];
+  const int lane = threadIdx.x;
+  const int R = it.nr, S = it.ns;
+  const int64_t g = it.g;
   const int u = (int)(uoff[g + 1] - uoff[g]);
-  for (int i = lane; i < u; i += 32) {
-    cols[i] = ul[i];
-    acc[i] = 0.0;
-  }
+  double* acc = reinterpret_cast<double*>(smem_raw);  // u * R sums, position-major
+  int32_t* cols = reinterpret_cast<int32_t*>(acc + kGnumCap);
+  const int32_t* __restrict__ ul = ulist + uoff[g];
+  for (int i = lane; i < u; i += 32) cols[i] = ul[i];
+  for (int i = lane; i < u * R; i += 32) acc[i] = 0.0;
+  const int r = lane % R, sl = lane / R;
+  const bool active = sl < S;
+  const int64_t rbase = rptr[g] + it.r0;
+  const double* __restrict__ arow = av + arp[grow[rbase + r]];
+  double* accr = acc + r;
+  const int64_t k0 = gptr[g], nk = gptr[g + 1] - k0;
   __syncwarp();
-  for (int64_t t = arp[row]; t < arp[row + 1]; ++t) {
-    const int32_t k = aci[t];
-    const double a = av[t];
-    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
-      const int32_t c = bci[q];
-      int lo = 0, hi = u - 1;  // c is in the list by construction
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (cols[mid] < c) lo = mid + 1;
-        else hi = mid;
+  int32_t kn = 0;
+  int64_t qn0 = 0, qn1 = 0;
+  double an = 0.0;
+  if (nk > 0) {
+    kn = gcol[k0];
+    qn0 = brp[kn];
+    qn1 = brp[kn + 1];
+    an = arow[0];
+  }
+  for (int64_t t = 0; t < nk; ++t) {
+    const int64_t q0 = qn0, q1 = qn1;
+    const double a = an;
+    if (t + 1 < nk) {
+      kn = gcol[k0 + t + 1];
+      qn0 = brp[kn];
+      qn1 = brp[kn + 1];
+      an = arow[t + 1];
+    }
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int nb = q1 - qb < 32 ? (int)(q1 - qb) : 32;
+      int pos = 0;
+      double pv = 0.0;
+      if (lane < nb) {
+        const int32_t c = bci[qb + lane];
+        pv = bv[qb + lane];
+        int lo = 0, hi = u - 1;  // c is in the list by construction
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (cols[mid] < c) lo = mid + 1;
+          else hi = mid;
+        }
+        pos = lo;
       }
-      acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, bv[q]));
+      for (int j0 = 0; j0 < nb; j0 += 2 * S) {  // uniform trip count: every lane joins the shuffles
+        const int ja = j0 + sl, jb = ja + S;      // this lane's row: entries ja and jb
+        const int p0 = __shfl_sync(kFull, pos, ja & 31), p1 = __shfl_sync(kFull, pos, jb & 31);
+        const double v0 = __shfl_sync(kFull, pv, ja & 31), v1 = __shfl_sync(kFull, pv, jb & 31);
+        if (active && jb < nb) {
+          double x0 = accr[p0 * R], x1 = accr[p1 * R];
+          x0 = __dadd_rn(x0, __dmul_rn(a, v0));
+          x1 = __dadd_rn(x1, __dmul_rn(a, v1));
+          accr[p0 * R] = x0;
+          accr[p1 * R] = x1;
+        } else if (active && ja < nb) {
+          accr[p0 * R] = __dadd_rn(accr[p0 * R], __dmul_rn(a, v0));
+        }
+      }
     }
     __syncwarp();
   }
-  const int64_t base = crp[row];
-  for (int i = lane; i < u; i += 32) {
-    cci[base + i] = cols[i];
-    cv[base + i] = acc[i];
+  for (int rr = 0; rr < R; ++rr) {
+    const int64_t base = crp[grow[rbase + rr]];
+    for (int i = lane; i < u; i += 32) {
+      cci[base + i] = cols[i];
+      cv[base + i] = acc[i * R + rr];
+    }
   }
 }
 
@@ -1063,15 +1112,13 @@ bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     if (v < 0) return false;  // a group's pattern does not fit the table: the per-row product
     umax = std::max(umax, (int)v);
   }
-  const size_t sm = (size_t)kNumWarps * umax * (sizeof(double) + sizeof(int32_t));
-  if (sm > 200 * 1024) return false;
   DBuf<int64_t> uoff;
   uoff.alloc(G + 1, s);
   scan_i32_to_i64(ucnt.get(), uoff.get(), G, s);
   int64_t utot = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&utot, uoff.get() + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GIAMG_CUDA(cudaStreamSynchronize(s));
-  DBuf<int32_t> ulist, gid, cnt;
+  DBuf<int32_t> ulist, cnt;
   ulist.alloc(std::max<int64_t>(utot, 1), s);
   {
     static PerDevice attr;
@@ -1081,9 +1128,8 @@ bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
                                                                    B.ci.get(), uoff.get(), ulist.get());
     note_launch();
   }
-  gid.alloc(n, s);
   cnt.alloc(n, s);
-  { group_row_counts<<<blocks_for(G, 256, 65535), 256, 0, s>>>(G, R.rptr.get(), R.grow.get(), ucnt.get(), gid.get(),
+  { group_row_counts<<<blocks_for(G, 256, 65535), 256, 0, s>>>(G, R.rptr.get(), R.grow.get(), ucnt.get(),
                                                               cnt.get()); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
   lap("symbolic");
@@ -1095,14 +1141,40 @@ bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
   GIAMG_CUDA(cudaStreamSynchronize(s));
   C.ci.alloc(std::max<int64_t>(C.nnz, 1), s);
   C.v.alloc(std::max<int64_t>(C.nnz, 1), s);
-  {
+  // warp work items: each group in pieces of the largest power of two of rows (at most 32) whose
+  // sums fit kGnumCap, the remainder last
+  std::vector<int64_t> rp_h(G + 1);
+  GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+  GIAMG_CUDA(cudaStreamSynchronize(s));
+  std::vector<GnumItem> items;
+  items.reserve((size_t)G * 2);
+  for (int64_t g = 0; g < G; ++g) {
+    const int u = std::max(uc[g], 1);
+    int rb = 32;
+    while (rb > 1 && (int64_t)rb * u > kGnumCap) rb >>= 1;
+    const int64_t nr = rp_h[g + 1] - rp_h[g];
+    for (int64_t r0 = 0; r0 < nr; r0 += rb) {
+      const int rows = (int)std::min<int64_t>(rb, nr - r0);
+      items.push_back(GnumItem{(int32_t)g, (int32_t)r0, rows, 32 / rows});
+    }
+  }
+  if (!items.empty()) {
+    DBuf<GnumItem> items_d;
+    items_d.alloc(items.size(), s);
+    GIAMG_CUDA(cudaMemcpyAsync(items_d.get(), items.data(), sizeof(GnumItem) * items.size(), cudaMemcpyHostToDevice, s));
+    const int wsm = (int)(kGnumCap * sizeof(double) + (size_t)umax * sizeof(int32_t));
     static PerDevice attr;
-    attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(gnum_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); });
-    gnum_rows<<<blocks_for(n, kNumWarps), kNumWarps * 32, sm, s>>>(n, umax, A.rp.get(), A.ci.get(), A.v.get(),
-                                                                  B.rp.get(), B.ci.get(), B.v.get(), gid.get(),
-                                                                  uoff.get(), ulist.get(), C.rp.get(), C.ci.get(),
-                                                                  C.v.get());
+    attr.once([&] {
+      GIAMG_CUDA(cudaFuncSetAttribute(gnum_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kGnumCap * sizeof(double) + kMaxUnique * sizeof(int32_t))));
+    });
+    gnum_warp<<<(unsigned)items.size(), 32, wsm, s>>>(items_d.get(), A.rp.get(), A.v.get(), B.rp.get(), B.ci.get(),
+                                                      B.v.get(), R.gptr.get(), R.gcol.get(), R.rptr.get(),
+                                                      R.grow.get(), uoff.get(), ulist.get(), C.rp.get(), C.ci.get(),
+                                                      C.v.get());
     note_launch();
+    GIAMG_CUDA(cudaGetLastError());
+    GIAMG_CUDA(cudaStreamSynchronize(s));  // items_d is released at scope end
   }
   GIAMG_CUDA(cudaGetLastError());
   GIAMG_CUDA(cudaStreamSynchronize(s));
