@@ -389,17 +389,31 @@ def gpu_uuid(dev):
         return None
 
 
+def timed_setup(prob, **opts):
+    """The library's setup on input arrays already in device memory, and the upload of those arrays
+    from host memory before it, timed apart: (Solver, setup_ms, upload_ms)."""
+    import torch
+    import paper_2512_15121_gb300 as g
+    dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    arrs = [torch.from_numpy(a).to(dev) for a in (prob.row_ptr, prob.col, prob.val, prob.elem_dof)]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    S = g.Solver(prob.n, *arrs, prob.p, None, device_ptrs=1, **opts)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del arrs
+    return S, (t2 - t1) * 1e3, (t1 - t0) * 1e3
+
+
 def measure_autotuned(prob, k, b, steps, warmup, rtol, default_mixed, default_fp64):
     """The same operator set up with autotune = 1 (the finest level's row kernels chosen by timing
     forced-iteration solves inside setup): setup time, what it picked, and the solve times against
     the defaults'."""
     import torch
     import paper_2512_15121_gb300 as g
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    S = g.Solver.from_problem(prob, device=True, cheb_degree=k, autotune=1)
-    torch.cuda.synchronize()
-    setup_ms = (time.perf_counter() - t0) * 1e3
+    S, setup_ms, _ = timed_setup(prob, cheb_degree=k, autotune=1)
     x = torch.empty_like(b)
     stream = torch.cuda.current_stream()
     mixed = timed_solves(S, b, x, stream, rtol, 1, steps, warmup, False)
@@ -423,11 +437,7 @@ def measure_config(name, steps, warmup, profiled, peak, peak_kind, rtol=1e-8, au
     k = fegen.WORKLOADS[name]["k"]
     prob = fegen.workload(name)
     dev = torch.device("cuda", torch.cuda.current_device())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    S = g.Solver.from_problem(prob, device=True, cheb_degree=k)
-    torch.cuda.synchronize()
-    setup_ms = (time.perf_counter() - t0) * 1e3
+    S, setup_ms, upload_ms = timed_setup(prob, cheb_degree=k)
     b = torch.from_numpy(prob.b).to(dev)
     x = torch.empty_like(b)
     stream = torch.cuda.current_stream(dev)
@@ -443,7 +453,7 @@ def measure_config(name, steps, warmup, profiled, peak, peak_kind, rtol=1e-8, au
     out = {"workload": name, "description": WORKLOAD_TEXT.get(name, ""), "dofs": prob.n, "nnz": prob.nnz,
            "cheb_degree": k, "levels": [[L["n"], L["nnz"], L["order"]] for L in
                                         (S.level_info(l) for l in range(S.num_levels))],
-           "setup_ms": round(setup_ms, 1),
+           "setup_ms": round(setup_ms, 1), "upload_ms": round(upload_ms, 1),
            "mixed": {"p50_ms": round(mixed["p50"], 3), "p99_ms": round(mixed["p99"], 3), "iters": mixed["iters"],
                      "true_relres": mixed["true_relres"], "launches_per_solve": mixed["launches"] // steps},
            "fp64": {"p50_ms": round(fp64["p50"], 3), "p99_ms": round(fp64["p99"], 3), "iters": fp64["iters"],
@@ -495,11 +505,7 @@ def run_ours(args):
     prob = fegen.workload(args.workload)
     stream = torch.cuda.current_stream(dev)
 
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    S = g.Solver.from_problem(prob, device=True, cheb_degree=k)
-    torch.cuda.synchronize()
-    setup_ms = (time.perf_counter() - t0) * 1e3
+    S, setup_ms, upload_ms = timed_setup(prob, cheb_degree=k)
     levels = [S.level_info(l) for l in range(S.num_levels)]
     b = torch.from_numpy(prob.b).to(dev)
     x = torch.empty_like(b)
@@ -595,6 +601,8 @@ def run_ours(args):
         "profiled_p50_ms": {"mixed": round(mixed_prof["p50"], 3), "fp64": round(fp64_prof["p50"], 3)},
         "vcycle_gbs": vcycle_gbs(mixed),
         "setup_ms": round(setup_ms, 1),
+        "setup_note": "giamg_setup on the input arrays already in device memory; their upload from "
+                      f"host memory before it: {upload_ms:.1f} ms",
         "roofline": roof_mixed,
         "cpu_baseline": cpu,
         "e2e": {"value": round(pct(e2e, 0.5), 3), "unit": "ms", "h2d_bytes_per_step": 8 * n_dofs,
@@ -617,11 +625,7 @@ def measure_batch(g, torch, m=32, reps=5):
     k = fegen.WORKLOADS[name]["k"]
     prob = fegen.workload(name, rhs="none")
     B = np.stack([prob.rhs("fourier", 1000 + j) for j in range(m)], axis=1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    S = g.Solver.from_problem(prob, device=True, cheb_degree=k)
-    torch.cuda.synchronize()
-    setup_ms = (time.perf_counter() - t0) * 1e3
+    S, setup_ms, upload_ms = timed_setup(prob, cheb_degree=k)
     Bd = torch.from_numpy(B).cuda()
     b0 = Bd[:, 0].contiguous()
     for _ in range(2):
@@ -653,7 +657,7 @@ def measure_batch(g, torch, m=32, reps=5):
     S.close()
     pb, ps, p64, pk = pct(tb, 0.5), pct(ts, 0.5), pct(t64, 0.5), pct(tk, 0.5)
     out = {"workload": name, "description": WORKLOAD_TEXT[name], "dofs": prob.n, "nnz": prob.nnz, "cheb_degree": k,
-           "setup_ms": round(setup_ms, 1), "m": m, "reps": reps,
+           "setup_ms": round(setup_ms, 1), "upload_ms": round(upload_ms, 1), "m": m, "reps": reps,
            "batch_mixed": {"p50_ms": round(pb, 3), "per_solve_ms": round(pb / m, 3),
                            "iters": [int(it.min()), int(it.max())], "max_relres": float(rr.max())},
            "single_mixed": {"p50_ms": round(ps, 3), "iters": int(it1)},

@@ -433,6 +433,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     upload(L0->A.rp, row_ptr, (size_t)n + 1, dev, s);
     upload(L0->A.ci, col_idx, (size_t)nnz, dev, s);
     upload(L0->A.v, val, (size_t)nnz, dev, s);
+    clk.mark("input copy");
     {
       DBuf<unsigned long long> bad;
       bad.alloc(1, s);
@@ -445,6 +446,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       GIAMG_CUDA(cudaStreamSynchronize(s));
       GIAMG_CHECK(hb == 0, GIAMG_ERR_ARG, "CSR invalid: row pointers decrease, or columns out of range / not ascending");
     }
+    clk.mark("CSR check");
     L0->avg_row = (double)nnz / n;
     const int nl0 = (p + 1) * (p + 1) * (p + 1);
     if (p > 1) {
@@ -453,6 +455,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
       GIAMG_CHECK(bad == 0, GIAMG_ERR_MAP,
                   "element map inconsistent with A: " + std::to_string(bad) + " entries out of range or missing from the pattern");
       L0->n_elem = n_elem;
+      clk.mark("element map check");
     }
     if (coords && p >= 1 && n_elem > 0 && elem_dof) {
       std::vector<double> ch((size_t)n * 3);
@@ -466,7 +469,7 @@ Ctx* setup_impl(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const
     GIAMG_CHECK(diag_inverse(L0->A, L0->dinv.get(), L0->dinv32.get(), s), GIAMG_ERR_NOT_SPD,
                 "A has a non-positive or missing diagonal entry");
 
-    clk.mark("input, validation");
+    clk.mark("coordinates, diagonal");
     // p-coarsening (Algorithms 2-4, 7) down to order 1
     while (H.lev.back()->order > 1 && (int)H.lev.size() < opt.max_levels) {
       Level& F = *H.lev.back();

@@ -255,6 +255,11 @@ struct NumSmem {
   double acc[kHashCap];
   int32_t count;
 };
+struct FillSmem {  // the pattern pass of the grouped product: no sums
+  int32_t tab[kHashCap];
+  int32_t sorted[kMaxUnique];
+  int32_t count;
+};
 
 __global__ void __launch_bounds__(kNumWarps * 32) spgemm_numeric(int64_t n, const int64_t* __restrict__ arp,
                                                                  const int32_t* __restrict__ aci,
@@ -707,30 +712,81 @@ __global__ void sa_smooth(int64_t n, const int64_t* __restrict__ arp, const int3
 __device__ __forceinline__ bool dirichlet_row(const int64_t* rp, const int32_t* ci, int64_t g) {
   return rp[g + 1] - rp[g] == 1 && ci[rp[g]] == g;
 }
-__global__ void validate_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                const int32_t* __restrict__ l2g, int32_t n_elem, int nloc,
-                                unsigned long long* __restrict__ bad) {
-  GRID_STRIDE(t, (int64_t)n_elem * nloc) {
-    const int64_t e = t / nloc;
-    const int32_t g = l2g[t];
-    if (g < 0 || g >= n) {
-      atomicAdd(bad, 1ull);
-      continue;
+// The element map against A's pattern: every pair of one element's nodes must be an entry of A,
+// except where either node is a Dirichlet (identity) row.  A block per element: its valid,
+// non-Dirichlet nodes sorted in shared memory (bitonic), then a warp per local row merges that
+// list with the row's ascending columns, a lane per piece of the list (one binary search for the
+// piece's first node, then a forward walk).  Counts the pairs missing from the pattern and the map
+// entries out of range.
+constexpr int kValThreads = 256;
+__global__ void __launch_bounds__(kValThreads) validate_kernel(int64_t n, const int64_t* __restrict__ rp,
+                                                               const int32_t* __restrict__ ci,
+                                                               const int32_t* __restrict__ l2g, int nloc, int np2,
+                                                               unsigned long long* __restrict__ bad) {
+  extern __shared__ int32_t vsm[];
+  int32_t* sorted = vsm;       // np2 keys: the checked nodes, then INT32_MAX
+  int32_t* rows = vsm + np2;   // nloc: the node if its row is checked, else -1
+  const int64_t e = blockIdx.x;
+  unsigned long long nbad = 0;
+  for (int a = threadIdx.x; a < np2; a += kValThreads) {
+    int32_t key = INT32_MAX;
+    if (a < nloc) {
+      const int32_t g = l2g[e * nloc + a];
+      int32_t row = -1;
+      if (g < 0 || g >= n) ++nbad;
+      else if (!dirichlet_row(rp, ci, g)) key = row = g;
+      rows[a] = row;
     }
-    if (dirichlet_row(rp, ci, g)) continue;
-    for (int b = 0; b < nloc; ++b) {
-      const int32_t c = l2g[e * nloc + b];
-      if (c < 0 || c >= n) continue;  // counted by its own slot
-      if (dirichlet_row(rp, ci, c)) continue;
-      int64_t lo = rp[g], hi = rp[g + 1];
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (ci[mid] < c) lo = mid + 1;
-        else hi = mid;
+    sorted[a] = key;
+  }
+  __syncthreads();
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np2; i += kValThreads) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t x = sorted[i], y = sorted[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            sorted[i] = y;
+            sorted[ixj] = x;
+          }
+        }
       }
-      if (lo >= rp[g + 1] || ci[lo] != c) atomicAdd(bad, 1ull);
+      __syncthreads();
     }
   }
+  int m = 0;
+  {
+    int lo = 0, hi = np2;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sorted[mid] < INT32_MAX) lo = mid + 1;
+      else hi = mid;
+    }
+    m = lo;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cs = (m + 31) / 32, b0 = lane * cs, b1 = min(m, b0 + cs);
+  for (int a = w; a < nloc; a += kValThreads / 32) {
+    const int32_t g = rows[a];
+    if (g < 0 || b0 >= b1) continue;
+    const int64_t r1 = rp[g + 1];
+    int64_t lo = rp[g], hi = r1;
+    const int32_t x0 = sorted[b0];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ci[mid] < x0) lo = mid + 1;
+      else hi = mid;
+    }
+    int64_t q = lo;
+    for (int b = b0; b < b1; ++b) {
+      const int32_t x = sorted[b];
+      while (q < r1 && ci[q] < x) ++q;
+      if (q >= r1 || ci[q] != x) ++nbad;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+  if (lane == 0 && nbad) atomicAdd(bad, nbad);
 }
 __global__ void dense_cm(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const double* __restrict__ v, double* __restrict__ D) {
@@ -934,11 +990,11 @@ __global__ void __launch_bounds__(kNumWarps * 32) gsym_fill(int64_t G, const int
                                                             const int32_t* __restrict__ bci,
                                                             const int64_t* __restrict__ uoff, int32_t* __restrict__ ulist) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  NumSmem* all = reinterpret_cast<NumSmem*>(smem_raw);
+  FillSmem* all = reinterpret_cast<FillSmem*>(smem_raw);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g = (int64_t)blockIdx.x * kNumWarps + w;
   if (g >= G) return;
-  NumSmem& S = all[w];
+  FillSmem& S = all[w];
   for (int i = lane; i < kHashCap; i += 32) S.tab[i] = -1;
   if (lane == 0) S.count = 0;
   __syncwarp();
@@ -978,28 +1034,82 @@ __global__ void __launch_bounds__(kNumWarps * 32) gsym_fill(int64_t G, const int
 }
 
 __global__ void group_row_counts(int64_t G, const int64_t* __restrict__ rptr, const int32_t* __restrict__ grow,
-                                 const int32_t* __restrict__ ucnt, int32_t* __restrict__ cnt) {
+                                 const int32_t* __restrict__ ucnt, int32_t* __restrict__ gid, int32_t* __restrict__ cnt) {
   GRID_STRIDE(g, G) {
     for (int64_t t = rptr[g]; t < rptr[g + 1]; ++t) {
+      gid[grow[t]] = (int32_t)g;
       cnt[grow[t]] = ucnt[g];
     }
   }
 }
 
-// numeric pass by warp work items: a warp takes `nr` rows of one group with `ns` lanes per row
-// (ns = 32 / nr rounded down, so groups of few rows still fill the warp), the group's sorted
-// output columns and the rows' sums ([position][row]) in shared memory.  For each inner index k of
-// the group (ascending) the lanes find the positions of B's row k in the column list once for all
-// of the warp's rows; the lanes of one row then split that row's entries (distinct positions), so
-// every sum still runs in ascending k with separately rounded products, as in the per-row passes;
-// a warp barrier between two k orders the updates of one sum made by different lanes.  Two entries
-// are applied per step (their positions differ), which halves the dependent shared-memory chain.
+// numeric, per row: a warp per row; smem per warp: the group's sorted list (umax int32) and the
+// sums (umax doubles); the lanes take the entries of B's row k, each finding its position by a
+// binary search
+__global__ void __launch_bounds__(kNumWarps * 32) gnum_rows(int64_t n, int umax, const int64_t* __restrict__ arp,
+                                                            const int32_t* __restrict__ aci,
+                                                            const double* __restrict__ av,
+                                                            const int64_t* __restrict__ brp,
+                                                            const int32_t* __restrict__ bci,
+                                                            const double* __restrict__ bv,
+                                                            const int32_t* __restrict__ gid,
+                                                            const int64_t* __restrict__ uoff,
+                                                            const int32_t* __restrict__ ulist,
+                                                            const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                                            double* __restrict__ cv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)w * umax;
+  int32_t* cols = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem_raw) + (size_t)kNumWarps * umax) +
+                  (size_t)w * umax;
+  const int64_t row = (int64_t)blockIdx.x * kNumWarps + w;
+  if (row >= n) return;
+  const int32_t g = gid[row];
+  const int32_t* __restrict__ ul = ulist + uoff[g];
+  const int u = (int)(uoff[g + 1] - uoff[g]);
+  for (int i = lane; i < u; i += 32) {
+    cols[i] = ul[i];
+    acc[i] = 0.0;
+  }
+  __syncwarp();
+  for (int64_t t = arp[row]; t < arp[row + 1]; ++t) {
+    const int32_t k = aci[t];
+    const double a = av[t];
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+      const int32_t c = bci[q];
+      int lo = 0, hi = u - 1;  // c is in the list by construction
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cols[mid] < c) lo = mid + 1;
+        else hi = mid;
+      }
+      acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, bv[q]));
+    }
+    __syncwarp();
+  }
+  const int64_t base = crp[row];
+  for (int i = lane; i < u; i += 32) {
+    cci[base + i] = cols[i];
+    cv[base + i] = acc[i];
+  }
+}
+
+// numeric, by warp work items (groups of many rows): a warp takes `nr` rows of one group with `ns`
+// lanes per row (ns = 32 / nr rounded down, so pieces of few rows still fill the warp), the
+// group's sorted output columns and the rows' sums ([position][row]) in shared memory.  For each
+// inner index k of the group (ascending) the lanes find the positions of B's row k in the column
+// list once for all of the warp's rows; the lanes of one row then split that row's entries
+// (distinct positions), so every sum still runs in ascending k with separately rounded products, as
+// in the per-row pass; a warp barrier between two k orders the updates of one sum made by
+// different lanes.  Two entries are applied per step (their positions differ), which halves the
+// dependent shared-memory chain; the next k's row bounds are loaded two steps ahead and its first
+// 32 entries of B one step ahead.
 struct GnumItem {
   int32_t g, r0, nr, ns;  // group, first row (offset in the group's row list), rows, lanes per row
 };
-constexpr int kGnumCap = 4096;  // sums per warp item (doubles): 32 KB of shared memory
+constexpr int kGnumCap = 2048;    // target sums per warp item (doubles; 16 KB of shared memory)
 
-__global__ void __launch_bounds__(32) gnum_warp(const GnumItem* __restrict__ items,
+__global__ void __launch_bounds__(32) gnum_warp(const GnumItem* __restrict__ items, int cap,
                                                 const int64_t* __restrict__ arp, const double* __restrict__ av,
                                                 const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
                                                 const double* __restrict__ bv, const int64_t* __restrict__ gptr,
@@ -1014,8 +1124,8 @@ __global__ void __launch_bounds__(32) gnum_warp(const GnumItem* __restrict__ ite
   const int R = it.nr, S = it.ns;
   const int64_t g = it.g;
   const int u = (int)(uoff[g + 1] - uoff[g]);
-  double* acc = reinterpret_cast<double*>(smem_raw);  // u * R sums, position-major
-  int32_t* cols = reinterpret_cast<int32_t*>(acc + kGnumCap);
+  double* acc = reinterpret_cast<double*>(smem_raw);  // u * R <= cap sums, position-major
+  int32_t* cols = reinterpret_cast<int32_t*>(acc + cap);
   const int32_t* __restrict__ ul = ulist + uoff[g];
   for (int i = lane; i < u; i += 32) cols[i] = ul[i];
   for (int i = lane; i < u * R; i += 32) acc[i] = 0.0;
@@ -1025,32 +1135,70 @@ __global__ void __launch_bounds__(32) gnum_warp(const GnumItem* __restrict__ ite
   const double* __restrict__ arow = av + arp[grow[rbase + r]];
   double* accr = acc + r;
   const int64_t k0 = gptr[g], nk = gptr[g + 1] - k0;
-  __syncwarp();
-  int32_t kn = 0;
-  int64_t qn0 = 0, qn1 = 0;
-  double an = 0.0;
+  // pipeline registers: (q0, q1, a) and the first entries (cb, pvb) of the step to come, and the
+  // bounds (nq0, nq1, na) of the one after it
+  int64_t q0 = 0, q1 = 0, nq0 = 0, nq1 = 0;
+  double a = 0.0, na = 0.0, pvb = 0.0;
+  int32_t cb = 0;
   if (nk > 0) {
-    kn = gcol[k0];
-    qn0 = brp[kn];
-    qn1 = brp[kn + 1];
-    an = arow[0];
-  }
-  for (int64_t t = 0; t < nk; ++t) {
-    const int64_t q0 = qn0, q1 = qn1;
-    const double a = an;
-    if (t + 1 < nk) {
-      kn = gcol[k0 + t + 1];
-      qn0 = brp[kn];
-      qn1 = brp[kn + 1];
-      an = arow[t + 1];
+    const int32_t k = gcol[k0];
+    q0 = brp[k];
+    q1 = brp[k + 1];
+    a = arow[0];
+    if (lane < q1 - q0) {
+      cb = bci[q0 + lane];
+      pvb = bv[q0 + lane];
     }
-    for (int64_t qb = q0; qb < q1; qb += 32) {
-      const int nb = q1 - qb < 32 ? (int)(q1 - qb) : 32;
+    if (nk > 1) {
+      const int32_t k2 = gcol[k0 + 1];
+      nq0 = brp[k2];
+      nq1 = brp[k2 + 1];
+      na = arow[1];
+    }
+  }
+  __syncwarp();
+  for (int64_t t = 0; t < nk; ++t) {
+    const int64_t tq0 = q0, tq1 = q1;
+    const double ta = a;
+    int32_t c = cb;
+    double pv = pvb;
+    q0 = nq0;
+    q1 = nq1;
+    a = na;
+    if (t + 2 < nk) {
+      const int32_t k2 = gcol[k0 + t + 2];
+      nq0 = brp[k2];
+      nq1 = brp[k2 + 1];
+      na = arow[t + 2];
+    }
+    if (tq0 >= tq1 && t + 1 < nk) {  // B's row k is empty: the next step's entries now
+      cb = 0;
+      pvb = 0.0;
+      if (lane < q1 - q0) {
+        cb = bci[q0 + lane];
+        pvb = bv[q0 + lane];
+      }
+    }
+    for (int64_t qb = tq0; qb < tq1; qb += 32) {
+      const int nb = tq1 - qb < 32 ? (int)(tq1 - qb) : 32;
+      if (qb != tq0) {
+        c = 0;
+        pv = 0.0;
+        if (lane < nb) {
+          c = bci[qb + lane];
+          pv = bv[qb + lane];
+        }
+      }
+      if (qb + 32 >= tq1 && t + 1 < nk) {  // this step's last entries: load the next step's first
+        cb = 0;
+        pvb = 0.0;
+        if (lane < q1 - q0) {
+          cb = bci[q0 + lane];
+          pvb = bv[q0 + lane];
+        }
+      }
       int pos = 0;
-      double pv = 0.0;
       if (lane < nb) {
-        const int32_t c = bci[qb + lane];
-        pv = bv[qb + lane];
         int lo = 0, hi = u - 1;  // c is in the list by construction
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
@@ -1065,12 +1213,12 @@ __global__ void __launch_bounds__(32) gnum_warp(const GnumItem* __restrict__ ite
         const double v0 = __shfl_sync(kFull, pv, ja & 31), v1 = __shfl_sync(kFull, pv, jb & 31);
         if (active && jb < nb) {
           double x0 = accr[p0 * R], x1 = accr[p1 * R];
-          x0 = __dadd_rn(x0, __dmul_rn(a, v0));
-          x1 = __dadd_rn(x1, __dmul_rn(a, v1));
+          x0 = __dadd_rn(x0, __dmul_rn(ta, v0));
+          x1 = __dadd_rn(x1, __dmul_rn(ta, v1));
           accr[p0 * R] = x0;
           accr[p1 * R] = x1;
         } else if (active && ja < nb) {
-          accr[p0 * R] = __dadd_rn(accr[p0 * R], __dmul_rn(a, v0));
+          accr[p0 * R] = __dadd_rn(accr[p0 * R], __dmul_rn(ta, v0));
         }
       }
     }
@@ -1118,18 +1266,19 @@ bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
   int64_t utot = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&utot, uoff.get() + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GIAMG_CUDA(cudaStreamSynchronize(s));
-  DBuf<int32_t> ulist, cnt;
+  DBuf<int32_t> ulist, gid, cnt;
   ulist.alloc(std::max<int64_t>(utot, 1), s);
   {
     static PerDevice attr;
-    const int fsm = (int)(sizeof(NumSmem) * kNumWarps);
+    const int fsm = (int)(sizeof(FillSmem) * kNumWarps);
     attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(gsym_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)); });
     gsym_fill<<<blocks_for(G, kNumWarps), kNumWarps * 32, fsm, s>>>(G, R.gptr.get(), R.gcol.get(), B.rp.get(),
                                                                    B.ci.get(), uoff.get(), ulist.get());
     note_launch();
   }
+  gid.alloc(n, s);
   cnt.alloc(n, s);
-  { group_row_counts<<<blocks_for(G, 256, 65535), 256, 0, s>>>(G, R.rptr.get(), R.grow.get(), ucnt.get(),
+  { group_row_counts<<<blocks_for(G, 256, 65535), 256, 0, s>>>(G, R.rptr.get(), R.grow.get(), ucnt.get(), gid.get(),
                                                               cnt.get()); note_launch(); }
   GIAMG_CUDA(cudaGetLastError());
   lap("symbolic");
@@ -1141,40 +1290,67 @@ bool spgemm_grouped(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
   GIAMG_CUDA(cudaStreamSynchronize(s));
   C.ci.alloc(std::max<int64_t>(C.nnz, 1), s);
   C.v.alloc(std::max<int64_t>(C.nnz, 1), s);
-  // warp work items: each group in pieces of the largest power of two of rows (at most 32) whose
-  // sums fit kGnumCap, the remainder last
-  std::vector<int64_t> rp_h(G + 1);
-  GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
-  GIAMG_CUDA(cudaStreamSynchronize(s));
-  std::vector<GnumItem> items;
-  items.reserve((size_t)G * 2);
-  for (int64_t g = 0; g < G; ++g) {
-    const int u = std::max(uc[g], 1);
-    int rb = 32;
-    while (rb > 1 && (int64_t)rb * u > kGnumCap) rb >>= 1;
-    const int64_t nr = rp_h[g + 1] - rp_h[g];
-    for (int64_t r0 = 0; r0 < nr; r0 += rb) {
-      const int rows = (int)std::min<int64_t>(rb, nr - r0);
-      items.push_back(GnumItem{(int32_t)g, (int32_t)r0, rows, 32 / rows});
+  // the numeric pass: warp work items where the groups are large enough to share the position
+  // searches among their rows, else a warp per row (environment GIAMG_SPGEMM_NUMERIC=1 / 2 forces
+  // the per-row / warp-item pass, for measurements)
+  static const int forced = [] {
+    const char* e = getenv("GIAMG_SPGEMM_NUMERIC");
+    return e ? atoi(e) : 0;
+  }();
+  const bool by_items = forced == 2 || (forced != 1 && 2 * n >= 3 * G);  // 1.5 rows a group or more
+  if (by_items) {
+    // each group in pieces of the largest power of two of rows (at most 32) whose sums fit
+    // kGnumCap, the remainder last
+    std::vector<int64_t> rp_h(G + 1);
+    GIAMG_CUDA(cudaMemcpyAsync(rp_h.data(), R.rptr.get(), sizeof(int64_t) * (G + 1), cudaMemcpyDeviceToHost, s));
+    GIAMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<GnumItem> items;
+    items.reserve((size_t)G * 2);
+    int cap = 1;
+    for (int64_t g = 0; g < G; ++g) {
+      const int u = std::max(uc[g], 1);
+      int rb = 32;
+      while (rb > 1 && (int64_t)rb * u > kGnumCap) rb >>= 1;
+      const int64_t nr = rp_h[g + 1] - rp_h[g];
+      for (int64_t r0 = 0; r0 < nr; r0 += rb) {
+        const int rows = (int)std::min<int64_t>(rb, nr - r0);
+        items.push_back(GnumItem{(int32_t)g, (int32_t)r0, rows, 32 / rows});
+        cap = std::max(cap, rows * u);
+      }
     }
-  }
-  if (!items.empty()) {
-    DBuf<GnumItem> items_d;
-    items_d.alloc(items.size(), s);
-    GIAMG_CUDA(cudaMemcpyAsync(items_d.get(), items.data(), sizeof(GnumItem) * items.size(), cudaMemcpyHostToDevice, s));
-    const int wsm = (int)(kGnumCap * sizeof(double) + (size_t)umax * sizeof(int32_t));
+    cap = (cap + 1) & ~1;  // the column list starts on 16 bytes
+    const size_t wsm = (size_t)cap * sizeof(double) + (size_t)umax * sizeof(int32_t);
+    if (!items.empty()) {
+      DBuf<GnumItem> items_d;
+      items_d.alloc(items.size(), s);
+      GIAMG_CUDA(cudaMemcpyAsync(items_d.get(), items.data(), sizeof(GnumItem) * items.size(), cudaMemcpyHostToDevice,
+                                 s));
+      static PerDevice attr;  // the largest request: cap <= max(kGnumCap, kMaxUnique) + 1, umax <= kMaxUnique
+      attr.once([&] {
+        GIAMG_CUDA(cudaFuncSetAttribute(gnum_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((kGnumCap + kMaxUnique + 2) * sizeof(double) +
+                                              kMaxUnique * sizeof(int32_t))));
+      });
+      gnum_warp<<<(unsigned)items.size(), 32, wsm, s>>>(items_d.get(), cap, A.rp.get(), A.v.get(), B.rp.get(),
+                                                        B.ci.get(), B.v.get(), R.gptr.get(), R.gcol.get(),
+                                                        R.rptr.get(), R.grow.get(), uoff.get(), ulist.get(),
+                                                        C.rp.get(), C.ci.get(), C.v.get());
+      note_launch();
+      GIAMG_CUDA(cudaGetLastError());
+      GIAMG_CUDA(cudaStreamSynchronize(s));  // items_d is released at scope end
+    }
+  } else {
+    const size_t sm = (size_t)kNumWarps * umax * (sizeof(double) + sizeof(int32_t));
     static PerDevice attr;
     attr.once([&] {
-      GIAMG_CUDA(cudaFuncSetAttribute(gnum_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kGnumCap * sizeof(double) + kMaxUnique * sizeof(int32_t))));
+      GIAMG_CUDA(cudaFuncSetAttribute(gnum_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kNumWarps * kMaxUnique * (sizeof(double) + sizeof(int32_t)))));
     });
-    gnum_warp<<<(unsigned)items.size(), 32, wsm, s>>>(items_d.get(), A.rp.get(), A.v.get(), B.rp.get(), B.ci.get(),
-                                                      B.v.get(), R.gptr.get(), R.gcol.get(), R.rptr.get(),
-                                                      R.grow.get(), uoff.get(), ulist.get(), C.rp.get(), C.ci.get(),
-                                                      C.v.get());
+    gnum_rows<<<blocks_for(n, kNumWarps), kNumWarps * 32, sm, s>>>(n, umax, A.rp.get(), A.ci.get(), A.v.get(),
+                                                                  B.rp.get(), B.ci.get(), B.v.get(), gid.get(),
+                                                                  uoff.get(), ulist.get(), C.rp.get(), C.ci.get(),
+                                                                  C.v.get());
     note_launch();
-    GIAMG_CUDA(cudaGetLastError());
-    GIAMG_CUDA(cudaStreamSynchronize(s));  // items_d is released at scope end
   }
   GIAMG_CUDA(cudaGetLastError());
   GIAMG_CUDA(cudaStreamSynchronize(s));
@@ -1489,8 +1665,18 @@ int64_t validate_map(const DCSR& A, const int32_t* l2g, int32_t n_elem, int nloc
   DBuf<unsigned long long> bad;
   bad.alloc(1, s);
   bad.zero(s);
-  { validate_kernel<<<blocks_for((int64_t)n_elem * nloc, 128, 65535), 128, 0, s>>>(A.n, A.rp.get(), A.ci.get(), l2g, n_elem,
-                                                                                 nloc, bad.get()); note_launch(); }
+  int np2 = 1;
+  while (np2 < nloc) np2 <<= 1;
+  const size_t sm = (size_t)(np2 + nloc) * sizeof(int32_t);
+  static PerDevice attr;  // the largest element: (GIAMG_MAX_ORDER + 1)^3 nodes
+  attr.once([&] {
+    GIAMG_CUDA(cudaFuncSetAttribute(validate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((4096 + 13 * 13 * 13) * sizeof(int32_t))));
+  });
+  if (n_elem > 0) {
+    validate_kernel<<<n_elem, kValThreads, sm, s>>>(A.n, A.rp.get(), A.ci.get(), l2g, nloc, np2, bad.get());
+    note_launch();
+  }
   GIAMG_CUDA(cudaGetLastError());
   unsigned long long h = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&h, bad.get(), sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -268,6 +268,11 @@ def test_errors_are_reported_not_raised_in_c():
     with pytest.raises(g.GiamgError) as e:
         g.Solver(free.n, free.row_ptr, free.col, free.val, bad, 2)
     assert e.value.code == g.GIAMG_ERR_MAP
+    # the count reported: node pairs of one element missing from A's pattern, counted on the host
+    import scipy.sparse as sp
+    pat = sp.csr_matrix((np.ones(len(free.col)), free.col, free.row_ptr), shape=(free.n, free.n))
+    missing = sum(int(bad.shape[1] ** 2 - pat[ids][:, ids].nnz) for ids in bad)
+    assert missing > 0 and f": {missing} entries" in str(e.value), (missing, str(e.value))
     # out-of-range map entry
     bad = prob.elem_dof.copy()
     bad[0, 0] = prob.n + 7
