@@ -123,6 +123,7 @@ struct Groups {
   // group is one contiguous block; hv from the FP32 values, hv64 from the FP64 values
   bool hvon = false, hv64on = false;
   int cpmax = 0;                // widest padded row of a big group
+  int rmax = 0;                 // most rows of a big group
   DBuf<int64_t> hoff;           // start of big group j's block (values), n_big + 1 entries
   DBuf<float> hv;
   DBuf<double> hv64;

@@ -591,18 +591,21 @@ bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s) {
     GIAMG_CUDA(cudaMemcpyAsync(big.data(), R.big.get(), sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
     GIAMG_CUDA(cudaStreamSynchronize(s));
     std::vector<int64_t> hoff(nb + 1, 0);
-    int cpmax = 0;
+    int cpmax = 0, rmax = 0;
     for (int64_t j = 0; j < nb; ++j) {
       const int64_t g = big[j];
       const int cp = (int)((gp[g + 1] - gp[g] + 3) & ~(int64_t)3);
       cpmax = std::max(cpmax, cp);
+      rmax = std::max(rmax, (int)(rp_h[g + 1] - rp_h[g]));
       hoff[j + 1] = hoff[j] + (rp_h[g + 1] - rp_h[g]) * cp;
     }
-    if ((size_t)cpmax * 8 > 96 * 1024) return false;  // x of a group in shared memory (FP64)
+    // x of a group in shared memory (FP64), and (FP32 form) the sums of its rows after it
+    if ((size_t)cpmax * 8 > 96 * 1024 || (size_t)(cpmax + rmax) * 4 > 96 * 1024) return false;
     R.hoff.alloc(nb + 1, s);
     GIAMG_CUDA(cudaMemcpyAsync(R.hoff.get(), hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
     GIAMG_CUDA(cudaStreamSynchronize(s));
     R.cpmax = cpmax;
+    R.rmax = rmax;
   }
   int64_t total = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&total, R.hoff.get() + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -293,8 +293,12 @@ HYB_SELECT(float, kAddSpmv, hyb_add_f32)
 // multiple of 4 values), so the warp of a row loads it with float4 loads, 4 per lane at once,
 // from a sequential stream: one step covers a row of 344 padded values (86 float4 of 128
 // slots), two a row of 640.  Against hyb_body's 4-byte loads from rows scattered over the value
-// array this doubles the bytes a warp has in flight with the same 32 registers.  The other rows
-// run the row-pattern kernel in the same launch, as in hyb_body's kernel.
+// array this doubles the bytes a warp has in flight with the same 32 registers.  A warp leaves
+// each row's sum in shared memory and goes on to its next row; after a barrier the block's
+// threads finish all rows of the group at once (the step's reads of b, d, D^-1 and x and its
+// writes), so the group pays that dependent latency once instead of once per row (4% per launch
+// on 16^3 p = 6).  The other rows run the row-pattern kernel in the same launch, as in
+// hyb_body's kernel.
 template <typename V>
 struct Vec16;
 template <>
@@ -325,11 +329,12 @@ __device__ __forceinline__ void hyv_body(const int32_t* __restrict__ big, const 
                                          const int32_t* __restrict__ grow, const int64_t* __restrict__ hoff,
                                          const V* __restrict__ hv, const V* __restrict__ x,
                                          const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,
-                                         const V* __restrict__ dinv, V c1, V c2) {
+                                         const V* __restrict__ dinv, V c1, V c2, int cpmax) {
   using VT = typename Vec16<V>::T;
   constexpr int EV = 16 / sizeof(V), U = Vec16<V>::kU;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* xs = reinterpret_cast<V*>(smem_raw);
+  V* sums = xs + cpmax;  // after the widest padded x list: one sum per row of the group
   const int64_t j = blockIdx.x;
   const int64_t g = big[j];
   const int64_t c0 = gptr[g];
@@ -361,7 +366,12 @@ __device__ __forceinline__ void hyv_body(const int32_t* __restrict__ big, const 
     V acc = (a[0] + a[1]) + (a[2] + a[3]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane != 0) continue;
+    if (lane == 0) sums[t] = acc;
+  }
+  // the rows' epilogues together: one latency for the group instead of one per row
+  __syncthreads();
+  for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+    const V acc = sums[t];
     const int64_t row = grow[t0 + t];
     if (MODE == kSpmv) {
       y[row] = acc;
@@ -386,9 +396,9 @@ __device__ __forceinline__ void hyv_body(const int32_t* __restrict__ big, const 
            int64_t n_rest, const int32_t* __restrict__ rest, const int32_t* __restrict__ obase,               \
            const int32_t* __restrict__ toff, const int64_t* __restrict__ rp, const V* __restrict__ val,       \
            const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, V* __restrict__ d,            \
-           const V* __restrict__ dinv, V c1, V c2) {                                                          \
+           const V* __restrict__ dinv, V c1, V c2, int cpmax) {                                               \
     if ((int64_t)blockIdx.x < n_big)                                                                          \
-      hyv_body<V, MODE>(big, gptr, gcol, rptr, grow, hoff, hv, x, b, y, d, dinv, c1, c2);                    \
+      hyv_body<V, MODE>(big, gptr, gcol, rptr, grow, hoff, hv, x, b, y, d, dinv, c1, c2, cpmax);             \
     else                                                                                                      \
       pat_body<32, 2, V, MODE, true>(n_rest, rp, obase, toff, val, x, b, y, d, dinv, c1, c2, 0, 0, rest, n_big); \
   }
@@ -739,7 +749,7 @@ template <typename V, int MODE>
 void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d, const V* dinv, V c1, V c2,
                 cudaStream_t s) {
   auto k = HyvKernel<V, MODE>::get();
-  const size_t sm = (size_t)A.grp.cpmax * sizeof(V);
+  const size_t sm = (size_t)(A.grp.cpmax + A.grp.rmax) * sizeof(V);
   static PerDevice attr;
   attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)); });
   const V* hv = A.grp.hv.get();
@@ -747,7 +757,7 @@ void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
       A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
       A.grp.hoff.get(), hv, A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(), A.rp.get(), val, x,
-      b, y, d, dinv, c1, c2);
+      b, y, d, dinv, c1, c2, A.grp.cpmax);
   note_launch();
 }
 
