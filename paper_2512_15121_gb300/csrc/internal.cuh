@@ -124,6 +124,7 @@ struct Groups {
   bool hvon = false, hv64on = false;
   int cpmax = 0;                // widest padded row of a big group
   int rmax = 0;                 // most rows of a big group
+  int hwarps = 8;               // FP32 vector hybrid: warps per block (rows of a group split evenly)
   DBuf<int64_t> hoff;           // start of big group j's block (values), n_big + 1 entries
   DBuf<float> hv;
   DBuf<double> hv64;

@@ -606,6 +606,20 @@ bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s) {
     GIAMG_CUDA(cudaStreamSynchronize(s));
     R.cpmax = cpmax;
     R.rmax = rmax;
+    // warps per block of the FP32 vector hybrid: the count (4 to 8) that leaves the fewest idle
+    // warp-rows when each group's rows are dealt round-robin to the block's warps (ties: more warps)
+    int64_t best = INT64_MAX;
+    for (int w = 8; w >= 4; --w) {
+      int64_t idle = 0;
+      for (int64_t j = 0; j < nb; ++j) {
+        const int64_t r = rp_h[big[j] + 1] - rp_h[big[j]];
+        idle += (r + w - 1) / w * w - r;
+      }
+      if (idle < best) {
+        best = idle;
+        R.hwarps = w;
+      }
+    }
   }
   int64_t total = 0;
   GIAMG_CUDA(cudaMemcpyAsync(&total, R.hoff.get() + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

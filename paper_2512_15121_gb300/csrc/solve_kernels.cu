@@ -753,8 +753,10 @@ void launch_hyv(const DCSR& A, const V* val, const V* x, const V* b, V* y, V* d,
   static PerDevice attr;
   attr.once([&] { GIAMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)); });
   const V* hv = A.grp.hv.get();
-  const int64_t rest_blocks = (A.grp.n_rest * 32 + kThreads - 1) / kThreads;
-  k<<<(unsigned)(A.grp.n_big + rest_blocks), kThreads, sm, s>>>(
+  // the listed rows' blocks (pat_body: 32 lanes per row) take rows at the block size used here
+  const int threads = 32 * A.grp.hwarps;
+  const int64_t rest_blocks = (A.grp.n_rest * 32 + threads - 1) / threads;
+  k<<<(unsigned)(A.grp.n_big + rest_blocks), threads, sm, s>>>(
       A.grp.n_big, A.grp.big.get(), A.grp.gptr.get(), A.grp.gcol.get(), A.grp.rptr.get(), A.grp.grow.get(),
       A.grp.hoff.get(), hv, A.grp.n_rest, A.grp.rest.get(), A.pat.obase.get(), A.pat.toff.get(), A.rp.get(), val, x,
       b, y, d, dinv, c1, c2, A.grp.cpmax);
