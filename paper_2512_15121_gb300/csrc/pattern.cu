@@ -606,18 +606,32 @@ bool hybrid_vector_build(DCSR& A, int precision, cudaStream_t s) {
     GIAMG_CUDA(cudaStreamSynchronize(s));
     R.cpmax = cpmax;
     R.rmax = rmax;
-    // warps per block of the FP32 vector hybrid: the count (4 to 8) that leaves the fewest idle
-    // warp-rows when each group's rows are dealt round-robin to the block's warps (ties: more warps)
-    int64_t best = INT64_MAX;
-    for (int w = 8; w >= 4; --w) {
+    // warps per block of the FP32 vector hybrid: 8, unless they leave more than 5% of the warp-rows
+    // idle when each group's rows are dealt round-robin to the block's warps (measured in the
+    // solve: 16^3 p = 6, groups of 125 and 25 rows, 10% idle with 8 warps, 2% faster with 5;
+    // 12^3 p = 8, groups of 343 and 49 rows, 4.5% idle, 2% slower with 7); then the count from
+    // 4 to 7 with the fewest idle warp-rows (ties: more warps)
+    auto idle_of = [&](int w, int64_t& slots) {
       int64_t idle = 0;
+      slots = 0;
       for (int64_t j = 0; j < nb; ++j) {
         const int64_t r = rp_h[big[j] + 1] - rp_h[big[j]];
         idle += (r + w - 1) / w * w - r;
+        slots += (r + w - 1) / w * w;
       }
-      if (idle < best) {
-        best = idle;
-        R.hwarps = w;
+      return idle;
+    };
+    int64_t slots8 = 0;
+    const int64_t idle8 = idle_of(8, slots8);
+    R.hwarps = 8;
+    if (idle8 * 20 > slots8) {
+      int64_t best = idle8, slots = 0;
+      for (int w = 7; w >= 4; --w) {
+        const int64_t idle = idle_of(w, slots);
+        if (idle < best) {
+          best = idle;
+          R.hwarps = w;
+        }
       }
     }
   }
