@@ -494,6 +494,38 @@ def test_fp32_level_product(form):
         gpu.close()
 
 
+@pytest.mark.parametrize("n, p", [(4, 4), (5, 5), (4, 7)])
+def test_vector_hybrid_block_sizes_match_oracle(n, p):
+    """The FP32 vector hybrid forced on operators whose row groups set other block sizes than the
+    p = 6 forms test (5 warps): the block takes 8 warps unless they leave over 5% of the warp-rows
+    idle -- 7 warps at p = 4 (interior groups of 27 rows), 8 at p = 5 and 7 (groups of 64 / 16
+    and 216 / 36 rows; p = 8 runs the form by default at full size, test_gpu_fullsize.py): the
+    finest level's FP32 product against the product of the FP32-rounded operands row by row
+    within the accumulation bound, its FP32 residual and smoother steps against the oracle's
+    within the rounding bounds, and FP64 PCG with the oracle's iteration count against the
+    oracle's solution."""
+    prob = fegen.make(n, p, mesh="jitter", lam=10.0)
+    orc = oracle.Hierarchy.from_problem(prob, cheb_degree=2)
+    gpu = g.Solver.from_problem(prob, device=True, cheb_degree=2, row_form=5)
+    try:
+        assert gpu.kernel(0, 1)[1] == "vector"
+        rng = np.random.default_rng(13)
+        rp, ci, v, _ = orc.level(0)
+        x = rng.normal(size=len(rp) - 1)
+        y = gpu.spmv32(0, dev(x)).cpu().numpy().astype(np.float64)
+        ref, bound = fp32_product_bound(rp, ci, v, x)
+        assert np.all(np.abs(y - ref) <= bound)
+        fp32_step_checks(orc, gpu, 2, rng, levels=[0], smooth_starts=(None, "x"))
+        xo, ito, _, _, st = orc.solve(prob.b, rtol=1e-8)
+        assert st == "ok"
+        xg, it, _ = gpu.solve(dev(prob.b), rtol=1e-8, force_iters=ito, precision=0)
+        assert it == ito and np.max(np.abs(host(xg) - xo)) <= 1e-10 * np.max(np.abs(xo))
+    finally:
+        gpu.close()
+        orc.close()
+        prob.close()
+
+
 @pytest.mark.parametrize("name", ["cube4_p4", "jitter8_p2_poisson", "graded345_p8_kappa"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_graph_solve_equals_host_loop(name, precision):
